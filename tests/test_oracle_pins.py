@@ -1,0 +1,334 @@
+"""Pins of the FP64 oracle to facts other than itself (CPU only).
+
+Each test checks the oracle against something the paper or the mathematics
+fixes: closed forms, brute force, a textbook special case (the SVD), theorem
+invariants, values printed in the paper's tables, finite differences, and the
+definitions of the BF16 / FP8-e4m3 formats."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+
+def rand_unit(dims, seed):
+    return [v.numpy().astype(np.float64) for v in W.unit_gaussian_vectors(dims, seed)]
+
+
+# ------------------------------------------------------------- eq. (3.3)
+@pytest.mark.parametrize("dims", [(3, 4, 5), (2, 3, 4, 5), (2, 3, 2, 3, 2), (4, 3)])
+def test_blocks_rank_one_closed_form(dims):
+    """For T = a1 o ... o ad:  A_{m,n} = (prod_{k!=m,n} <a_k,u_k>) a_m a_n^T."""
+    rng = np.random.default_rng(1)
+    a = [rng.standard_normal(n) for n in dims]
+    T = W.outer([torch.from_numpy(v) for v in a]).numpy()          # float64
+    u = rand_unit(dims, 2)
+    H = oracle.unpack_blocks(oracle.blocks(T, u), list(dims))
+    d = len(dims)
+    for (m, n), B in H.items():
+        c = np.prod([a[k] @ u[k] for k in range(d) if k not in (m, n)])
+        np.testing.assert_allclose(B, c * np.outer(a[m], a[n]), rtol=1e-12, atol=1e-14)
+
+
+def test_blocks_integer_brute_force():
+    """Integer tensor and integer vectors: FP64 sums are exact, so the blocks
+    must equal a pure-Python brute-force sum bit for bit."""
+    dims = (3, 2, 4, 3)
+    rng = np.random.default_rng(3)
+    T = rng.integers(-5, 6, size=dims).astype(np.float32)
+    u = [rng.integers(-3, 4, size=n).astype(np.float64) for n in dims]
+    H = oracle.unpack_blocks(oracle.blocks(T, u), list(dims))
+    for (m, n), B in H.items():
+        ref = np.zeros((dims[m], dims[n]))
+        for idx in itertools.product(*[range(s) for s in dims]):
+            p = float(T[idx])
+            for k in range(4):
+                if k not in (m, n):
+                    p *= u[k][idx[k]]
+            ref[idx[m], idx[n]] += p
+        assert np.array_equal(B, ref)
+
+
+def test_blocks_match_einsum_and_entries():
+    dims = (4, 5, 3, 2)
+    T = W.gaussian_tensor(dims, 5).numpy()
+    u = rand_unit(dims, 6)
+    Hp = oracle.blocks(T, u)
+    H = oracle.unpack_blocks(Hp, list(dims))
+    letters = "abcd"
+    for (m, n), B in H.items():
+        ops, subs = [T.astype(np.float64)], [letters]
+        for k in range(4):
+            if k not in (m, n):
+                ops.append(u[k])
+                subs.append(letters[k])
+        ref = np.einsum(",".join(subs) + "->" + letters[m] + letters[n], *ops)
+        np.testing.assert_allclose(B, ref, rtol=1e-12, atol=1e-13)
+        for (i, j) in [(0, 0), (dims[m] - 1, dims[n] - 1), (1, 0)]:
+            for fast in (True, False):
+                assert abs(oracle.block_entry(T, u, m, n, i, j, fast=fast) - B[i, j]) < 1e-12
+
+
+def test_kkt_vectors_match_blocks():
+    """g_n from the tensor directly equals A_{n,m} u_m for every m != n."""
+    dims = (5, 4, 6)
+    T = W.gaussian_tensor(dims, 7).numpy()
+    u = rand_unit(dims, 8)
+    g, full = oracle.kkt_vectors(T, u)
+    Hf = oracle.full_block_matrix(oracle.blocks(T, u), list(dims))
+    off = oracle.mode_offsets(dims)
+    for n in range(3):
+        for m in range(3):
+            if m == n:
+                continue
+            gnm = Hf[off[n]:off[n + 1], off[m]:off[m + 1]] @ u[m]
+            np.testing.assert_allclose(gnm, g[n], rtol=1e-12, atol=1e-13)
+        assert abs(full - g[n] @ u[n]) < 1e-12
+
+
+def test_ttv_definition():
+    dims = (3, 4, 5)
+    T = W.gaussian_tensor(dims, 9).numpy()
+    v = np.arange(4, dtype=np.float64)
+    np.testing.assert_allclose(oracle.ttv(T, 1, v), np.einsum("abc,b->ac", T.astype(np.float64), v),
+                               rtol=1e-12)
+
+
+# ------------------------------------------------------------- Theorem 1
+@pytest.mark.parametrize("dims", [(4, 5, 3), (3, 4, 2, 3)])
+def test_spectrum_flip_theorem1_p1(dims):
+    """Thm 1 (P1): negating block 1 of x negates the spectrum of J(x)."""
+    T = W.gaussian_tensor(dims, 11).numpy()
+    u = rand_unit(dims, 12)
+    uh = [-u[0]] + u[1:]
+    J = oracle.nepv_matrix(oracle.blocks(T, u), list(dims))
+    Jh = oracle.nepv_matrix(oracle.blocks(T, uh), list(dims))
+    w = np.sort(np.linalg.eigvalsh(J))
+    wh = np.sort(np.linalg.eigvalsh(Jh))
+    np.testing.assert_allclose(wh, -w[::-1], atol=1e-12)
+
+
+# ------------------------------------------------------------- d = 2: SVD
+def test_order2_is_top_singular_triplet():
+    """d = 2: J is [[0,A],[A^T,0]] and the best rank-one approximation is the
+    top singular triplet (Eckart-Young-Mirsky)."""
+    A = W.gaussian_tensor((7, 5), 13).numpy()
+    U, S, Vt = np.linalg.svd(A.astype(np.float64))
+    res = oracle.hoscf(A, rand_unit((7, 5), 14), tol=1e-12, max_iter=10)
+    assert res.converged and res.iters == 1
+    assert abs(res.sigma - S[0]) < 1e-12 * S[0]
+    assert abs(abs(res.u[0] @ U[:, 0]) - 1) < 1e-12
+    assert abs(abs(res.u[1] @ Vt[0]) - 1) < 1e-12
+
+
+# ------------------------------------------------------------- planted
+@pytest.mark.parametrize("dims", [(6, 7, 8), (5, 4, 6, 3), (3, 4, 3, 2, 3)])
+def test_planted_rank_one_exact_recovery(dims):
+    f = [v / np.linalg.norm(v) for v in rand_unit(dims, 21)]      # unit in FP64
+    T = 3.5 * W.outer([torch.from_numpy(v) for v in f]).numpy()  # exact rank one
+    res = oracle.hoscf(T, rand_unit(dims, 22), tol=1e-13, max_iter=100)
+    assert res.converged
+    assert abs(res.sigma - 3.5) < 1e-12 * 3.5
+    for n in range(len(dims)):
+        assert abs(abs(res.u[n] @ f[n]) - 1) < 1e-12
+
+
+def test_kkt_and_theorems_at_convergence():
+    """KKT (2.4) from the tensor itself; Thm 3 (largest magnitude);
+    Thm 1 (P2) equal block norms; Lemma 2 remark: sigma is the top singular
+    value of every block, with singular vectors (u_m, u_n)."""
+    dims = (9, 8, 7)
+    T, _ = W.planted_cp(dims, [4.0], seed=31, noise_abs=1.0)
+    T = T.numpy()
+    res = oracle.hoscf(T, rand_unit(dims, 32), tol=1e-12, max_iter=500)
+    assert res.converged
+    g, full = oracle.kkt_vectors(T, res.u)
+    assert abs(full - res.sigma) < 1e-10 * res.sigma
+    for n in range(3):
+        assert np.linalg.norm(g[n] - res.sigma * res.u[n]) < 1e-10 * res.sigma
+    Hp = oracle.blocks(T, res.u)
+    J = oracle.nepv_matrix(Hp, list(dims))
+    w, V = np.linalg.eigh(J)
+    k = np.argmax(np.abs(w))
+    assert abs(w[k] - res.sigma) < 1e-10 * res.sigma
+    norms = [np.linalg.norm(b) for b in oracle.split(V[:, k], dims)]
+    np.testing.assert_allclose(norms, norms[0], rtol=1e-8)
+    for (m, n), B in oracle.unpack_blocks(Hp, dims).items():
+        U, S, Vt = np.linalg.svd(B)
+        assert abs(S[0] - res.sigma) < 1e-10 * res.sigma
+        assert abs(abs(U[:, 0] @ res.u[m]) - 1) < 1e-10
+        assert abs(abs(Vt[0] @ res.u[n]) - 1) < 1e-10
+
+
+def test_brute_force_2x2x2():
+    """On 2x2x2 tensors the best of several HOSCF starts equals the maximum of
+    |T(u1,u2,u3)| over a fine grid of unit vectors (cos t, sin t), refined."""
+    from scipy.optimize import minimize
+    th = np.linspace(0, np.pi, 181, endpoint=False)
+    C = np.stack([np.cos(th), np.sin(th)], 1)
+    for seed in range(3):
+        T = W.gaussian_tensor((2, 2, 2), 40 + seed).numpy().astype(np.float64)
+        F = np.abs(np.einsum("abc,ia,jb,kc->ijk", T, C, C, C))
+        i, j, k = np.unravel_index(np.argmax(F), F.shape)
+
+        def f(t):
+            v = [np.array([np.cos(x), np.sin(x)]) for x in t]
+            return -abs(np.einsum("abc,a,b,c->", T, *v))
+        best = -minimize(f, [th[i], th[j], th[k]], method="Nelder-Mead",
+                         options=dict(xatol=1e-12, fatol=1e-14, maxiter=4000)).fun
+        sig = max(oracle.hoscf(T, rand_unit((2, 2, 2), s), tol=1e-13, max_iter=500).sigma
+                  for s in range(8))
+        assert abs(sig - best) < 1e-9 * best
+
+
+def test_hopm_cross_check():
+    dims = (8, 6, 7)
+    T, _ = W.planted_cp(dims, [5.0, 1.0], seed=51, noise_abs=0.5)
+    T = T.numpy()
+    u0 = rand_unit(dims, 52)
+    s1 = oracle.hoscf(T, u0, tol=1e-12, max_iter=500)
+    s2, _ = oracle.hopm(T, u0, tol=1e-12)
+    assert abs(s1.sigma - s2) < 1e-10 * s2
+
+
+# ------------------------------------------------------------- Tables 1-3
+@pytest.mark.parametrize("name", ["EXP", "ARCSIN"])
+def test_example2_table2_rho_and_table3_iterations(name):
+    ref = GOLD["table2_rho"][name]
+    it_ref = GOLD["table3_iterations"][name]
+    T = W.example2(name).numpy()
+    nrm = np.linalg.norm(T.astype(np.float64))
+    rho, its, its_i = [], [], []
+    for s in range(6):
+        u0 = [v.numpy() for v in W.uniform01_vectors(T.shape, s)]
+        r = oracle.hoscf(T, u0, tol=1e-4, max_iter=500)
+        ri = oracle.hoscf(T, u0, tol=1e-4, max_iter=500, variant="ihoscf")
+        rho.append(r.sigma / nrm)
+        its.append(r.iters)
+        its_i.append(ri.iters)
+        assert abs(ri.sigma - r.sigma) < 1e-4 * r.sigma
+    assert abs(np.mean(rho) - ref["rho"]) <= ref["pm"] + 0.005     # two printed digits
+    m, sd = it_ref["hoscf"]
+    assert abs(np.mean(its) - m) <= 2 * sd
+    assert np.mean(its_i) < np.mean(its)                            # iHOSCF needs fewer
+
+
+def test_example1_table1_mean_lambda():
+    """Loose statistical check of Table 1 (HOSCF column): Gaussian 10x10x10."""
+    m, sd = GOLD["table1_lambda"]["3"]
+    lam = []
+    for s in range(12):
+        T = W.gaussian_tensor((10, 10, 10), 600 + s).numpy()
+        u0 = [v.numpy() for v in W.uniform01_vectors((10, 10, 10), 700 + s)]
+        lam.append(oracle.hoscf(T, u0, tol=1e-4, max_iter=500).sigma)
+    assert abs(np.mean(lam) - m) < 2 * sd
+
+
+# ------------------------------------------------------------- final fix / gauge
+def test_final_fix_and_gauge_keep_the_rank_one_term():
+    dims = (4, 3, 5)
+    u = rand_unit(dims, 61)
+    s, uf = oracle.gauge(*oracle.final_fix(-2.0, u))
+    assert s == 2.0
+    for n in range(1, 3):
+        assert uf[n][np.argmax(np.abs(uf[n]))] > 0
+    a = -2.0 * W.outer([torch.from_numpy(v) for v in u]).numpy()
+    b = s * W.outer([torch.from_numpy(v) for v in uf]).numpy()
+    np.testing.assert_allclose(a, b, atol=1e-15)
+
+
+# ------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("dims", [(5, 6, 7), (3, 4, 3, 4)])
+def test_adjoint_matches_central_differences(dims):
+    T, _ = W.planted_cp(dims, [3.0], seed=71, noise_abs=0.3)
+    T = T.numpy().astype(np.float64)
+    res = oracle.hoscf(T, rand_unit(dims, 72), tol=1e-14, max_iter=500)
+    rng = np.random.default_rng(73)
+    w = [rng.standard_normal(n) for n in dims]
+    c = 0.7
+    G, a, _ = oracle.adjoint(T, res.u, res.sigma, c, w)
+    for n in range(len(dims)):
+        assert abs(a[n] @ res.u[n]) < 1e-10
+    D = rng.standard_normal(T.shape)
+
+    def L(Tp):
+        r = oracle.hoscf(Tp, res.u, tol=1e-14, max_iter=500)
+        return c * r.sigma + sum(wn @ un for wn, un in zip(w, r.u))
+    h = 1e-5
+    fd = (L(T + h * D) - L(T - h * D)) / (2 * h)
+    an = float(np.sum(G * D))
+    assert abs(fd - an) < 1e-6 * max(1.0, abs(an))
+
+
+# ------------------------------------------------------------- formats
+def test_bf16_rounding_definition():
+    vals = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8), 1 + 2 ** -8 + 2 ** -20,
+                     3.0e38, 1e-40, 0.0, -0.0], dtype=np.float32)
+    q = oracle.quantize_bf16(vals)
+    assert [hex(v) for v in q[:5]] == ["0x3f80", "0x3f80", "0x3f82", "0xbf80", "0x3f81"]
+    assert q[5] == 0x7F80 or q[5] == 0x7F62
+    assert oracle.dequantize_bf16(q[7:9]).tolist() == [0.0, 0.0]
+    x = W.gaussian_tensor((4096,), 81).numpy() * 37
+    ref = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(oracle.quantize_bf16(x), ref)
+
+
+def test_e4m3_definition():
+    tab = oracle.e4m3_table()
+    assert tab[0x7E] == 448.0 and tab[0x38] == 1.0 and tab[0x08] == 2.0 ** -6
+    assert tab[0x01] == 2.0 ** -9 and np.isnan(tab[0x7F]) and tab[0xB8] == -1.0
+    y = np.array([1.0625, 1.1875, 500.0, -1000.0, 2.0 ** -10, 3 * 2.0 ** -10, 0.0, 17.0])
+    codes = oracle._e4m3_round(y)
+    # 1.0625 ties between 1.0 (0x38) and 1.125 (0x39) -> even 0x38; 1.1875 -> 0x3A
+    assert codes.tolist() == [0x38, 0x3A, 0x7E, 0xFE, 0x00, 0x02, 0x00, 0x58]
+    x = W.gaussian_tensor((8192,), 82).numpy() * 3
+    codes = oracle._e4m3_round(x.astype(np.float64))
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(codes, ref)
+
+
+def test_e4m3_scaled_roundtrip_error_bound():
+    x = W.gaussian_tensor((1000,), 83).numpy()
+    codes, scales = oracle.quantize_e4m3_scaled(x)
+    assert scales.shape == (8,)
+    xq = oracle.dequantize_e4m3_scaled(codes, scales)
+    amax = np.repeat(scales * 448.0, 128)[:1000]
+    # e4m3 keeps 3 mantissa bits: relative error <= 2^-4 for normals, and the
+    # subnormal spacing 2^-9 * scale bounds the rest
+    err = np.abs(xq - x)
+    assert np.all(err <= np.maximum(np.abs(x) * 2.0 ** -4, 2.0 ** -10 * amax / 448.0 * 1.0001))
+
+
+# ------------------------------------------------------------- planted mistakes
+def test_planted_mistakes_are_caught(monkeypatch):
+    """A dropped 1/(d-1), a transposed block and a wrong gauge sign each break
+    one of the pins above."""
+    dims = (6, 5, 4)
+    T, _ = W.planted_cp(dims, [2.0], seed=91)
+    T = T.numpy().astype(np.float64)
+    u0 = rand_unit(dims, 92)
+    good = oracle.nepv_matrix
+    monkeypatch.setattr(oracle, "nepv_matrix", lambda Hp, d: good(Hp, d) * (len(d) - 1))
+    r = oracle.hoscf(T, u0, tol=1e-12, max_iter=50)
+    lam = oracle.largest_magnitude_eigpair(oracle.nepv_matrix(oracle.blocks(T, r.u), dims))[0]
+    assert abs(lam - r.sigma) > 0.5            # Thm 3 check would fail
+    monkeypatch.setattr(oracle, "nepv_matrix", good)
+
+    A = W.gaussian_tensor((5, 5), 93).numpy().astype(np.float64)
+    U, S, Vt = np.linalg.svd(A)
+    gfull = oracle.full_block_matrix
+    monkeypatch.setattr(oracle, "full_block_matrix",
+                        lambda Hp, d: gfull(Hp.reshape(5, 5).T.ravel(), d))
+    r = oracle.hoscf(A, rand_unit((5, 5), 94), tol=1e-12, max_iter=5)
+    assert abs(abs(r.u[0] @ U[:, 0]) - 1) > 1e-3   # SVD pin would fail
+    monkeypatch.setattr(oracle, "full_block_matrix", gfull)
+
+    s, uf = oracle.final_fix(-1.0, rand_unit(dims, 95))
+    assert s > 0 and abs(uf[0][0]) > 0
