@@ -1,0 +1,212 @@
+/*
+ * hoscf.h - C ABI of the GB300 (sm_103a) HOSCF / iHOSCF library.
+ *
+ * Best rank-one approximation of a dense order-d tensor A (I_1 x ... x I_d):
+ * find sigma and unit vectors u^(1..d) maximising A x_1 u^(1) ... x_d u^(d)
+ * (paper Sec. 2, eq. 2.3), by the higher-order self-consistent-field
+ * iteration (Algorithm 1) and its Rayleigh-quotient variant (Sec. 4.4).
+ *
+ * Conventions used by every entry point
+ *   - Tensors are dense, row-major (last index fastest), contiguous.
+ *   - Factor vectors are passed concatenated: u^(1) first, u^(n) starting at
+ *     offset I_1 + ... + I_{n-1}; total length n_tot = I_1 + ... + I_d.
+ *   - Coupling blocks A_{m,n} (eq. 3.3) are stored for m < n only, packed in
+ *     lexicographic (m, n) order, each row-major I_m x I_n; total length
+ *     P = sum_{m<n} I_m I_n.  J(x) of eq. (3.2) is these blocks divided by
+ *     (d - 1), placed symmetrically with zero diagonal blocks.
+ *   - "device" pointers are CUDA device memory of the handle's device;
+ *     "host" pointers are ordinary host memory.  Streams are cudaStream_t
+ *     passed as void* (NULL = the legacy default stream).
+ *   - The caller owns every buffer it passes.  The handle owns an internal
+ *     workspace (grown on demand with cudaMalloc; hoscf_workspace_size
+ *     reports what a problem needs).
+ *   - No call aborts or prints.  Each returns an hoscf_status; on failure
+ *     hoscf_last_error() gives a message.  A handle is used by one host
+ *     thread and one stream at a time.
+ */
+#ifndef HOSCF_H
+#define HOSCF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HOSCF_MAX_ORDER 8
+
+typedef enum {
+    HOSCF_OK = 0,
+    HOSCF_EINVAL = 1,          /* bad argument: order, dims, null or misaligned pointer, zero block */
+    HOSCF_ENOMEM = 2,          /* workspace allocation failed */
+    HOSCF_ECUDA = 3,           /* a CUDA call failed (message has the CUDA error string) */
+    HOSCF_NOT_CONVERGED = 4,   /* max_iter reached; outputs hold the last certified iterate */
+    HOSCF_NONFINITE = 5,       /* NaN/Inf met in the tensor, the factors or a solve */
+    HOSCF_TIMEOUT = 6,         /* a bounded device-side wait gave up (no hang) */
+    HOSCF_EUNSUPPORTED = 7     /* a valid request this build does not handle */
+} hoscf_status;
+
+typedef enum {
+    HOSCF_F32 = 0,             /* IEEE float32 */
+    HOSCF_BF16 = 1,            /* bfloat16, no scale */
+    HOSCF_F8E4M3 = 2           /* FP8 e4m3 (fn), one float32 scale per 128 consecutive elements */
+} hoscf_dtype;
+
+typedef enum {
+    HOSCF_VARIANT_HOSCF = 0,   /* Algorithm 1 */
+    HOSCF_VARIANT_IHOSCF = 1,  /* Sec. 4.4: RQI with J built at the new point x_k (one more pass) */
+    HOSCF_VARIANT_IHOSCF_PREV = 2 /* Sec. 4.4 read with J_{k-1} (tracks plain HOSCF) */
+} hoscf_variant;
+
+typedef struct hoscf_handle hoscf_handle;
+
+/* A dense tensor in device memory. */
+typedef struct {
+    int order;                 /* d, 2 .. HOSCF_MAX_ORDER */
+    const int64_t* dims;       /* host, d entries, each >= 1 */
+    hoscf_dtype dtype;
+    const void* data;          /* device, row-major contiguous, 16-byte aligned */
+    const float* scales;       /* device, HOSCF_F8E4M3 only: ceil(N/128) float32 scales, else NULL */
+} hoscf_tensor_desc;
+
+typedef struct {
+    double tol;                /* stop when r = ||g - sigma u||_2 / |sigma| <= tol (see hoscf_solve) */
+    int max_iter;              /* maximum eigen steps (Alg. 1 loop trips) */
+    int variant;               /* hoscf_variant */
+    double eig_tol;            /* Lanczos stop: Ritz residual <= eig_tol * |theta| */
+    int eig_max_steps;         /* Lanczos basis size limit (<= 128) */
+    const hoscf_tensor_desc* refine; /* precision form: FP32 copy of the same tensor, or NULL */
+    double switch_tol;         /* precision form: residual at which passes move to `refine` */
+    int64_t timeout_ns;        /* bound on every device-side wait (0 = 2 s) */
+} hoscf_opts;
+
+typedef struct {
+    int iters;                 /* eigen steps taken */
+    int passes;                /* block constructions (TTVc passes), all tensors */
+    int passes_refine;         /* of which on the `refine` tensor */
+    int rqi_accepts;           /* iHOSCF: RQI iterates kept */
+    double resid;              /* KKT residual r at the returned point */
+    double resid_4_1;          /* eq. (4.1) evaluated at the returned point */
+    double sigma_raw;          /* sigma before the final sign fix */
+} hoscf_info;
+
+/* Handle lifetime.  `device` is a CUDA ordinal. */
+hoscf_status hoscf_create(hoscf_handle** h, int device);
+hoscf_status hoscf_destroy(hoscf_handle* h);
+const char* hoscf_last_error(const hoscf_handle* h);
+
+/* Defaults: tol 1e-6, max_iter 200, HOSCF, eig_tol 1e-10, eig_max_steps 64,
+ * refine NULL, switch_tol 1e-3, timeout 2 s. */
+hoscf_status hoscf_opts_default(hoscf_opts* opts);
+
+/* Bytes of handle workspace a solve of this shape and dtype needs (host args). */
+hoscf_status hoscf_workspace_size(int order, const int64_t* dims, int dtype, size_t* bytes);
+
+/*
+ * hoscf_ttvc_blocks - all coupling blocks in one read of the tensor.
+ * Eq. (3.3): H[(m,n)] = A x_{k != m,n} u^(k) for every m < n (Alg. 1 line 4).
+ *   T  tensor descriptor (device data).
+ *   u  device, n_tot floats: the d factor vectors, used as given (the
+ *      paper's blocks use unit vectors, eq. 3.4; no normalisation is done).
+ *   H  device, P floats, packed as described above (overwritten).
+ * Asynchronous on `stream`; FP32 accumulation.  Errors: EINVAL (order < 2
+ * or > 8, a dim < 1, null pointer, F8 without scales), ENOMEM, ECUDA.
+ */
+hoscf_status hoscf_ttvc_blocks(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u,
+                               float* H, void* stream);
+
+/*
+ * hoscf_eig_step - the largest-magnitude eigenpair of J (Alg. 1 line 5),
+ * then the block normalisation of lines 6-9.
+ *   order, dims   host.
+ *   H             device, P floats (packed blocks; J = blocks / (d-1)).
+ *   x_prev        device, n_tot doubles: warm start and sign reference
+ *                 (need not be normalised; must be nonzero).
+ *   x_out         device, n_tot doubles: unit eigenvector with
+ *                 <x_out, x_prev> >= 0.
+ *   u_out         device, n_tot floats, or NULL: x_out's blocks each scaled
+ *                 to unit length (eq. 3.4; a zero block stays zero).
+ *   lambda_out    device, 1 double: the eigenvalue (ties between +l and -l
+ *                 resolve to +l).
+ * Lanczos with full reorthogonalisation in FP64 (stop: eig_tol,
+ * eig_max_steps; opts may be NULL for defaults).  Asynchronous on `stream`.
+ */
+hoscf_status hoscf_eig_step(hoscf_handle* h, int order, const int64_t* dims, const float* H,
+                            const double* x_prev, double* x_out, float* u_out,
+                            double* lambda_out, const hoscf_opts* opts, void* stream);
+
+/*
+ * hoscf_solve - HOSCF / iHOSCF (Algorithm 1 and Sec. 4.4).
+ *   T       tensor (device data; F32, BF16 or F8E4M3).
+ *   u0      device, n_tot floats: initial guess; each block is normalised
+ *           (a zero or non-finite block gives EINVAL).
+ *   opts    host, or NULL for defaults.
+ *   u_out   device, n_tot floats: the factors, after Alg. 1 lines 12-15
+ *           and the sign gauge (for n >= 2 the largest-|.| entry of u^(n),
+ *           lowest index on ties, is positive; sigma >= 0).
+ *   sigma_out host double.  info host, or NULL.
+ * Each iteration builds the blocks at the current factors, certifies that
+ * point with r = ||g - sigma u||_2 / |sigma| (g_n = A x_{k!=n} u^(k) from the
+ * blocks, sigma = mean_n <u_n, g_n>; the KKT system 2.4) and stops there when
+ * r <= tol; otherwise it takes the eigen step.  With opts->refine set, passes
+ * run on T until r <= switch_tol and on `refine` (FP32) afterwards.
+ * Synchronous: returns when the outputs are final.  NOT_CONVERGED after
+ * max_iter (outputs = last certified iterate), NONFINITE, TIMEOUT, EINVAL,
+ * ENOMEM, ECUDA.
+ */
+hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u0,
+                         const hoscf_opts* opts, float* u_out, double* sigma_out,
+                         hoscf_info* info, void* stream);
+
+/*
+ * hoscf_solve_batched - `count` independent F32 tensors of orders 3..4 and
+ * small dims, solved in one persistent launch (no paper counterpart; the
+ * per-tensor algorithm is hoscf_solve's HOSCF variant).
+ *   T        host array of `count` descriptors (device data).
+ *   u0       host array of `count` device pointers (n_tot floats each).
+ *   u_out    host array of `count` device pointers (n_tot floats each).
+ *   sigma_out host, count doubles.  infos host, count entries, or NULL.
+ * Synchronous.  Returns the worst per-tensor status.
+ */
+hoscf_status hoscf_solve_batched(hoscf_handle* h, int count, const hoscf_tensor_desc* T,
+                                 const float* const* u0, const hoscf_opts* opts,
+                                 float* const* u_out, double* sigma_out, hoscf_info* infos,
+                                 void* stream);
+
+/*
+ * hoscf_backward - gradient of L = grad_sigma * sigma + sum_n <grad_u_n, u_n>
+ * with respect to the tensor, at a converged solution (no paper
+ * counterpart: envelope theorem for sigma, implicit-function adjoint of the
+ * KKT system 2.4 for the factors).
+ *   T        F32 tensor (device data) the solution was computed on.
+ *   u        device, n_tot floats: converged unit factors.
+ *   sigma    host: converged sigma (consistent with u's signs).
+ *   grad_u   device, n_tot floats, or NULL (= zero).
+ *   grad_T   device, N floats (overwritten):
+ *            grad_sigma * u1 o ... o ud - sum_n u1 o .. o a_n o .. o ud,
+ *            where [a; nu] solves [[H - sigma I, -U], [-U^T, 0]] [a; nu] = [w; 0]
+ *            (H = full symmetric block matrix, U = blockdiag(u_n), w = grad_u).
+ * The adjoint system is solved in FP64 on the device.  Synchronous.
+ * NONFINITE if the system is singular to working precision.
+ */
+hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u,
+                            double sigma, double grad_sigma, const float* grad_u,
+                            float* grad_T, void* stream);
+
+/*
+ * hoscf_quantize - FP32 tensor to the precision-form storage (no paper
+ * counterpart).  x: device, n floats.  dtype BF16: q receives n uint16
+ * (round to nearest even).  dtype F8E4M3: q receives n bytes and scales
+ * ceil(n/128) floats: scale = fp32(amax/448) per 128-element group (1 for an
+ * all-zero group), code = saturating round-to-nearest-even e4m3 of
+ * fp32(x/scale).  Asynchronous on `stream`.
+ */
+hoscf_status hoscf_quantize(hoscf_handle* h, const float* x, int64_t n, int dtype, void* q,
+                            float* scales, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOSCF_H */

@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) HOSCF / iHOSCF: best rank-one approximation of dense
+tensors (arXiv 2403.01778) behind a C ABI (include/hoscf.h).
+
+The compute path is libhoscf.so (hand-written CUDA); this package only
+marshals torch tensors into it.  There is no CPU fallback: importing the
+functions works everywhere, calling them needs the built library and a GPU.
+"""
+from .api import (HoscfError, SolveResult, balanced, handle, hoscf_backward, hoscf_eig_step,  # noqa: F401
+                  hoscf_opts_default, hoscf_quantize, hoscf_solve, hoscf_solve_batched,
+                  hoscf_ttvc_blocks, hoscf_workspace_size, n_blocks, n_tot)

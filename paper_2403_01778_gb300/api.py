@@ -1,0 +1,280 @@
+"""Python binding of the HOSCF C ABI: same names, argument marshalling only.
+
+Tensors are torch CUDA tensors (PyTorch supplies device memory and the
+current stream); every computation runs in libhoscf.so.  A tensor may be
+float32, bfloat16, or FP8-e4m3 (torch.float8_e4m3fn or uint8 codes, with a
+float32 ``scales`` tensor of one scale per 128 consecutive elements).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import Info, Opts, TensorDesc
+
+
+class HoscfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_handles = {}
+_hlock = threading.Lock()
+
+
+def handle(device=None) -> ctypes.c_void_p:
+    """Per-device library handle, created on first use."""
+    if device is None:
+        device = torch.cuda.current_device()
+    device = int(torch.device("cuda", device).index if not isinstance(device, int) else device)
+    with _hlock:
+        h = _handles.get(device)
+        if h is None:
+            lib = _lib.load()
+            h = ctypes.c_void_p()
+            st = lib.hoscf_create(ctypes.byref(h), device)
+            if st != 0:
+                raise HoscfError(st, f"hoscf_create(device={device}) failed")
+            _handles[device] = h
+        return h
+
+
+def _check(st: int, h, allow=(0,)):
+    if st not in allow:
+        msg = _lib.load().hoscf_last_error(h)
+        raise HoscfError(st, msg.decode() if msg else "")
+    return st
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(T: torch.Tensor):
+    if T.dtype == torch.float32:
+        return _lib.HOSCF_F32
+    if T.dtype == torch.bfloat16:
+        return _lib.HOSCF_BF16
+    if T.dtype in (torch.uint8, getattr(torch, "float8_e4m3fn", None)):
+        return _lib.HOSCF_F8E4M3
+    raise TypeError(f"unsupported tensor dtype {T.dtype}")
+
+
+class _Desc:
+    """Keeps the dims array alive alongside the descriptor."""
+
+    def __init__(self, T: torch.Tensor, scales=None, dims=None):
+        if not T.is_cuda:
+            raise ValueError("tensor must be on a CUDA device")
+        if not T.is_contiguous():
+            raise ValueError("tensor must be contiguous (row-major)")
+        shape = tuple(int(v) for v in (dims if dims is not None else T.shape))
+        self.dims = (ctypes.c_int64 * len(shape))(*shape)
+        self.shape = shape
+        self.T = T
+        self.scales = scales
+        self.desc = TensorDesc(len(shape), self.dims, _dtype_code(T), ctypes.c_void_p(T.data_ptr()),
+                               ctypes.c_void_p(scales.data_ptr() if scales is not None else 0))
+
+
+def n_tot(dims):
+    return int(sum(dims))
+
+
+def n_blocks(dims):
+    return int(sum(dims[m] * dims[n] for m in range(len(dims)) for n in range(m + 1, len(dims))))
+
+
+def hoscf_opts_default() -> Opts:
+    o = Opts()
+    _lib.load().hoscf_opts_default(ctypes.byref(o))
+    return o
+
+
+def hoscf_workspace_size(dims, dtype=_lib.HOSCF_F32) -> int:
+    arr = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
+    out = ctypes.c_size_t()
+    st = _lib.load().hoscf_workspace_size(len(dims), arr, int(dtype), ctypes.byref(out))
+    if st != 0:
+        raise HoscfError(st, "hoscf_workspace_size failed")
+    return int(out.value)
+
+
+def hoscf_ttvc_blocks(T: torch.Tensor, u: torch.Tensor, H: torch.Tensor | None = None,
+                      scales=None, stream=None) -> torch.Tensor:
+    """All coupling blocks (eq. 3.3), packed (m<n lexicographic, each row-major)."""
+    d = _Desc(T, scales)
+    u = u.contiguous()
+    if u.dtype != torch.float32 or u.numel() != n_tot(d.shape):
+        raise ValueError("u must be float32 with sum(dims) entries")
+    if H is None:
+        H = torch.empty(n_blocks(d.shape), device=T.device, dtype=torch.float32)
+    h = handle(T.device.index)
+    _check(_lib.load().hoscf_ttvc_blocks(h, ctypes.byref(d.desc), ctypes.c_void_p(u.data_ptr()),
+                                         ctypes.c_void_p(H.data_ptr()), _stream_ptr(stream)), h)
+    return H
+
+
+def _opts(tol=None, max_iter=None, variant=None, eig_tol=None, eig_max_steps=None,
+          refine_desc=None, switch_tol=None, timeout_ns=None) -> Opts:
+    o = hoscf_opts_default()
+    if tol is not None:
+        o.tol = float(tol)
+    if max_iter is not None:
+        o.max_iter = int(max_iter)
+    if variant is not None:
+        o.variant = _lib.VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    if eig_tol is not None:
+        o.eig_tol = float(eig_tol)
+    if eig_max_steps is not None:
+        o.eig_max_steps = int(eig_max_steps)
+    if refine_desc is not None:
+        o.refine = ctypes.pointer(refine_desc)
+    if switch_tol is not None:
+        o.switch_tol = float(switch_tol)
+    if timeout_ns is not None:
+        o.timeout_ns = int(timeout_ns)
+    return o
+
+
+def hoscf_eig_step(dims, H: torch.Tensor, x_prev: torch.Tensor, eig_tol=None, eig_max_steps=None,
+                   stream=None):
+    """Largest-magnitude eigenpair of J (Alg. 1 line 5) and the normalised
+    factors (lines 6-9).  Returns (x float64, u float32, lambda float64 tensor)."""
+    dims = [int(v) for v in dims]
+    n = n_tot(dims)
+    x_prev = x_prev.contiguous()
+    if x_prev.dtype != torch.float64 or x_prev.numel() != n:
+        raise ValueError("x_prev must be float64 with sum(dims) entries")
+    x = torch.empty(n, device=H.device, dtype=torch.float64)
+    u = torch.empty(n, device=H.device, dtype=torch.float32)
+    lam = torch.empty(1, device=H.device, dtype=torch.float64)
+    arr = (ctypes.c_int64 * len(dims))(*dims)
+    o = _opts(eig_tol=eig_tol, eig_max_steps=eig_max_steps)
+    h = handle(H.device.index)
+    _check(_lib.load().hoscf_eig_step(h, len(dims), arr, ctypes.c_void_p(H.data_ptr()),
+                                      ctypes.c_void_p(x_prev.data_ptr()),
+                                      ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                      ctypes.c_void_p(lam.data_ptr()), ctypes.byref(o),
+                                      _stream_ptr(stream)), h)
+    return x, u, lam
+
+
+@dataclass
+class SolveResult:
+    sigma: float
+    u: torch.Tensor          # concatenated factors, float32
+    dims: tuple
+    iters: int
+    passes: int
+    passes_refine: int
+    rqi_accepts: int
+    resid: float
+    resid_4_1: float
+    sigma_raw: float
+    converged: bool
+
+    def factors(self):
+        out, o = [], 0
+        for n in self.dims:
+            out.append(self.u[o:o + n])
+            o += n
+        return out
+
+
+def hoscf_solve(T: torch.Tensor, u0: torch.Tensor, tol=1e-6, max_iter=200, variant="hoscf",
+                eig_tol=None, eig_max_steps=None, scales=None, refine: torch.Tensor | None = None,
+                switch_tol=None, timeout_ns=None, u_out: torch.Tensor | None = None,
+                stream=None) -> SolveResult:
+    """HOSCF / iHOSCF (Algorithm 1, Sec. 4.4).  Synchronous."""
+    d = _Desc(T, scales)
+    u0 = u0.contiguous()
+    n = n_tot(d.shape)
+    if u0.dtype != torch.float32 or u0.numel() != n:
+        raise ValueError("u0 must be float32 with sum(dims) entries")
+    rd = _Desc(refine) if refine is not None else None
+    o = _opts(tol, max_iter, variant, eig_tol, eig_max_steps,
+              rd.desc if rd is not None else None, switch_tol, timeout_ns)
+    if u_out is None:
+        u_out = torch.empty(n, device=T.device, dtype=torch.float32)
+    sigma = ctypes.c_double()
+    info = Info()
+    h = handle(T.device.index)
+    st = _lib.load().hoscf_solve(h, ctypes.byref(d.desc), ctypes.c_void_p(u0.data_ptr()),
+                                 ctypes.byref(o), ctypes.c_void_p(u_out.data_ptr()),
+                                 ctypes.byref(sigma), ctypes.byref(info), _stream_ptr(stream))
+    _check(st, h, allow=(0, _lib.HOSCF_NOT_CONVERGED))
+    return SolveResult(sigma.value, u_out, d.shape, info.iters, info.passes, info.passes_refine,
+                       info.rqi_accepts, info.resid, info.resid_4_1, info.sigma_raw, st == 0)
+
+
+def hoscf_quantize(x: torch.Tensor, dtype: str, stream=None):
+    """FP32 -> ("bf16": bfloat16 tensor) or ("fp8": uint8 e4m3 codes, float32 scales)."""
+    x = x.contiguous()
+    if x.dtype != torch.float32 or not x.is_cuda:
+        raise ValueError("x must be a float32 CUDA tensor")
+    n = x.numel()
+    h = handle(x.device.index)
+    if dtype == "bf16":
+        q = torch.empty(x.shape, device=x.device, dtype=torch.bfloat16)
+        _check(_lib.load().hoscf_quantize(h, ctypes.c_void_p(x.data_ptr()), n, _lib.HOSCF_BF16,
+                                          ctypes.c_void_p(q.data_ptr()), None, _stream_ptr(stream)), h)
+        return q, None
+    if dtype == "fp8":
+        q = torch.empty(x.shape, device=x.device, dtype=torch.uint8)
+        s = torch.empty((n + 127) // 128, device=x.device, dtype=torch.float32)
+        _check(_lib.load().hoscf_quantize(h, ctypes.c_void_p(x.data_ptr()), n, _lib.HOSCF_F8E4M3,
+                                          ctypes.c_void_p(q.data_ptr()),
+                                          ctypes.c_void_p(s.data_ptr()), _stream_ptr(stream)), h)
+        return q, s
+    raise ValueError(dtype)
+
+
+def hoscf_backward(T: torch.Tensor, u: torch.Tensor, sigma: float, grad_sigma: float,
+                   grad_u: torch.Tensor | None = None, grad_T: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """dL/dT for L = grad_sigma*sigma + <grad_u, u> at a converged solution."""
+    d = _Desc(T)
+    u = u.contiguous()
+    if grad_T is None:
+        grad_T = torch.empty(d.shape, device=T.device, dtype=torch.float32)
+    gu = grad_u.contiguous() if grad_u is not None else None
+    h = handle(T.device.index)
+    _check(_lib.load().hoscf_backward(h, ctypes.byref(d.desc), ctypes.c_void_p(u.data_ptr()),
+                                      float(sigma), float(grad_sigma),
+                                      ctypes.c_void_p(gu.data_ptr() if gu is not None else 0),
+                                      ctypes.c_void_p(grad_T.data_ptr()), _stream_ptr(stream)), h)
+    return grad_T
+
+
+def hoscf_solve_batched(tensors, u0s, tol=1e-6, max_iter=200, eig_tol=None, timeout_ns=None,
+                        stream=None):
+    """Many small independent F32 tensors in one persistent launch."""
+    cnt = len(tensors)
+    descs = [_Desc(T) for T in tensors]
+    arr = (TensorDesc * cnt)(*[dd.desc for dd in descs])
+    u0c = [u.contiguous() for u in u0s]
+    uo = [torch.empty_like(u) for u in u0c]
+    pin = (ctypes.c_void_p * cnt)(*[u.data_ptr() for u in u0c])
+    pout = (ctypes.c_void_p * cnt)(*[u.data_ptr() for u in uo])
+    sig = (ctypes.c_double * cnt)()
+    infos = (Info * cnt)()
+    o = _opts(tol, max_iter, None, eig_tol, None, None, None, timeout_ns)
+    dev = tensors[0].device.index
+    h = handle(dev)
+    st = _lib.load().hoscf_solve_batched(h, cnt, arr, pin, ctypes.byref(o), pout, sig, infos,
+                                         _stream_ptr(stream))
+    _check(st, h, allow=(0, _lib.HOSCF_NOT_CONVERGED))
+    return [float(s) for s in sig], uo, [infos[i] for i in range(cnt)], st
+
+
+def balanced(u: torch.Tensor, dims) -> torch.Tensor:
+    """x = [u^(1); ...; u^(d)] / sqrt(d) in float64 (marshalling helper)."""
+    return u.double() / math.sqrt(len(dims))

@@ -1,0 +1,473 @@
+// C ABI of the HOSCF library (declared in include/hoscf.h): handle,
+// workspace, argument checks and the host-side iteration driver.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace hoscf;
+
+struct hoscf_handle {
+    int device = 0;
+    int nsm = 0;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    double* h_pinned = nullptr;   // small pinned readback buffer
+    char msg[512] = {0};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+hoscf_status fail(hoscf_handle* h, hoscf_status code, const char* fmt, ...) {
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->msg, sizeof(h->msg), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+hoscf_status cuda_fail(hoscf_handle* h, cudaError_t e, const char* what) {
+    return fail(h, HOSCF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return cuda_fail(h, _e, #call);     \
+    } while (0)
+
+// Fixed head of the workspace: device error word, grid barrier, scalars.
+constexpr size_t kHeadBytes = 4096;
+constexpr size_t kOffErr = 0;        // int
+constexpr size_t kOffBar = 64;       // 2 unsigned
+constexpr size_t kOffScal = 256;     // 32 doubles
+constexpr size_t kOffNorms = 1024;   // up to 16 doubles
+
+struct Layout {
+    Shape s;
+    PassPlan pp;
+    EigPlan ep;
+    size_t off_pass = 0, off_eig = 0, off_H = 0, off_H2 = 0, off_ua = 0, off_ub = 0, off_x = 0;
+    size_t total = 0;
+};
+
+hoscf_status ensure_ws(hoscf_handle* h, size_t bytes) {
+    if (bytes <= h->ws_bytes) return HOSCF_OK;
+    if (h->ws) {
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaMalloc(&h->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, HOSCF_ENOMEM, "workspace allocation of %zu bytes failed: %s", want,
+                    cudaGetErrorString(e));
+    }
+    h->ws_bytes = want;
+    return HOSCF_OK;
+}
+
+bool dims_valid(int order, const int64_t* dims) {
+    if (order < 2 || order > HOSCF_MAX_ORDER || !dims) return false;
+    for (int k = 0; k < order; ++k)
+        if (dims[k] < 1) return false;
+    return true;
+}
+
+hoscf_status check_desc(hoscf_handle* h, const hoscf_tensor_desc* T) {
+    if (!T) return fail(h, HOSCF_EINVAL, "tensor descriptor is NULL");
+    if (!dims_valid(T->order, T->dims)) return fail(h, HOSCF_EINVAL, "order must be 2..%d and dims >= 1", HOSCF_MAX_ORDER);
+    if (!T->data) return fail(h, HOSCF_EINVAL, "tensor data is NULL");
+    if (T->dtype != HOSCF_F32 && T->dtype != HOSCF_BF16 && T->dtype != HOSCF_F8E4M3)
+        return fail(h, HOSCF_EINVAL, "unknown dtype %d", (int)T->dtype);
+    if (T->dtype == HOSCF_F8E4M3 && !T->scales) return fail(h, HOSCF_EINVAL, "FP8 tensor needs scales");
+    if ((reinterpret_cast<uintptr_t>(T->data) & 15) != 0)
+        return fail(h, HOSCF_EINVAL, "tensor data must be 16-byte aligned");
+    return HOSCF_OK;
+}
+
+hoscf_status plan_all(hoscf_handle* h, int order, const int64_t* dims, int dtype, bool pass,
+                      bool eig, int mmax, Layout& L) {
+    if (!make_shape(order, dims, L.s)) return fail(h, HOSCF_EINVAL, "invalid shape");
+    size_t off = kHeadBytes;
+    if (pass) {
+        make_pass_plan(L.s, dtype, h->nsm, true, L.pp);
+        L.off_pass = off;
+        off = align_up(off + L.pp.bytes, 256);
+    }
+    if (eig) {
+        if (!make_eig_plan(L.s, h->nsm, lanczos_blocks_per_sm(L.s.n_tot), mmax, L.ep))
+            return fail(h, HOSCF_EINVAL, "eigen plan failed");
+        L.off_eig = off;
+        off = align_up(off + L.ep.bytes, 256);
+    }
+    L.off_H = off;
+    off = align_up(off + sizeof(float) * (size_t)L.s.P, 256);
+    L.off_H2 = off;
+    off = align_up(off + sizeof(float) * (size_t)L.s.P, 256);
+    L.off_ua = off;
+    off = align_up(off + sizeof(float) * (size_t)L.s.n_tot, 256);
+    L.off_ub = off;
+    off = align_up(off + sizeof(float) * (size_t)L.s.n_tot, 256);
+    L.off_x = off;
+    off = align_up(off + sizeof(double) * (size_t)L.s.n_tot, 256);
+    L.total = off;
+    return ensure_ws(h, L.total);
+}
+
+int* dev_err(hoscf_handle* h) { return reinterpret_cast<int*>(h->ws + kOffErr); }
+
+hoscf_status reset_dev_state(hoscf_handle* h, cudaStream_t st) {
+    CK(cudaMemsetAsync(h->ws, 0, 256, st));
+    return HOSCF_OK;
+}
+
+uint64_t timeout_of(const hoscf_opts* o) {
+    return (o && o->timeout_ns > 0) ? (uint64_t)o->timeout_ns : 2000000000ull;
+}
+
+hoscf_status dev_status(hoscf_handle* h, int code) {
+    if (code == DEV_OK) return HOSCF_OK;
+    if (code == DEV_TIMEOUT) return fail(h, HOSCF_TIMEOUT, "a device-side wait exceeded its time limit");
+    if (code == DEV_NONFINITE) return fail(h, HOSCF_NONFINITE, "non-finite value met on the device");
+    return fail(h, HOSCF_ECUDA, "device error code %d", code);
+}
+
+// Eigen step launcher (shared by hoscf_eig_step and the solve driver).
+hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const double* x0,
+                        const float* u0, double* x_out, float* u_out, double* lambda_out,
+                        const hoscf_opts* o, int check, double kkt_tol, cudaStream_t st) {
+    char* eb = h->ws + L.off_eig;
+    float* Jr = reinterpret_cast<float*>(eb + L.ep.off_jr);
+    cudaError_t e = launch_build_jr(L.s, H, Jr, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "build_jr");
+    LanczosLaunch ll;
+    ll.Jr = Jr;
+    ll.x0 = x0;
+    ll.u0 = u0;
+    ll.V = reinterpret_cast<double*>(eb + L.ep.off_V);
+    ll.Y = reinterpret_cast<double*>(eb + L.ep.off_Y);
+    ll.part = reinterpret_cast<double*>(eb + L.ep.off_part);
+    ll.scal = reinterpret_cast<double*>(h->ws + kOffScal);
+    ll.x_out = x_out;
+    ll.u_out = u_out;
+    ll.lambda_out = lambda_out;
+    ll.mmax = L.ep.mmax;
+    ll.G = L.ep.G;
+    ll.eig_tol = (o && o->eig_tol > 0) ? o->eig_tol : 1e-10;
+    ll.check = check;
+    ll.kkt_tol = kkt_tol;
+    ll.bar = reinterpret_cast<unsigned*>(h->ws + kOffBar);
+    ll.err = dev_err(h);
+    ll.timeout_ns = timeout_of(o);
+    e = launch_lanczos(L.s, ll, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lanczos");
+    return HOSCF_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+hoscf_status hoscf_create(hoscf_handle** out, int device) {
+    if (!out) return HOSCF_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return HOSCF_EINVAL;
+    }
+    hoscf_handle* h = new (std::nothrow) hoscf_handle();
+    if (!h) return HOSCF_ENOMEM;
+    h->device = device;
+    DeviceGuard g(device);
+    if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete h;
+        return HOSCF_ECUDA;
+    }
+    if (cudaMallocHost(&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return HOSCF_ENOMEM;
+    }
+    *out = h;
+    return HOSCF_OK;
+}
+
+hoscf_status hoscf_destroy(hoscf_handle* h) {
+    if (!h) return HOSCF_EINVAL;
+    {
+        DeviceGuard g(h->device);
+        if (h->ws) cudaFree(h->ws);
+        if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    }
+    delete h;
+    return HOSCF_OK;
+}
+
+const char* hoscf_last_error(const hoscf_handle* h) { return h ? h->msg : "null handle"; }
+
+hoscf_status hoscf_opts_default(hoscf_opts* o) {
+    if (!o) return HOSCF_EINVAL;
+    memset(o, 0, sizeof(*o));
+    o->tol = 1e-6;
+    o->max_iter = 200;
+    o->variant = HOSCF_VARIANT_HOSCF;
+    o->eig_tol = 1e-10;
+    o->eig_max_steps = 64;
+    o->refine = nullptr;
+    o->switch_tol = 1e-3;
+    o->timeout_ns = 0;
+    return HOSCF_OK;
+}
+
+hoscf_status hoscf_workspace_size(int order, const int64_t* dims, int dtype, size_t* bytes) {
+    if (!bytes || !dims_valid(order, dims)) return HOSCF_EINVAL;
+    Shape s;
+    if (!make_shape(order, dims, s)) return HOSCF_EINVAL;
+    int nsm = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    PassPlan pp;
+    EigPlan ep;
+    make_pass_plan(s, dtype, nsm, true, pp);
+    make_eig_plan(s, nsm, 1, 64, ep);
+    size_t t = kHeadBytes + align_up(pp.bytes, 256) + align_up(ep.bytes, 256) +
+               2 * align_up(sizeof(float) * s.P, 256) + 2 * align_up(sizeof(float) * s.n_tot, 256) +
+               align_up(sizeof(double) * s.n_tot, 256);
+    *bytes = t;
+    return HOSCF_OK;
+}
+
+hoscf_status hoscf_ttvc_blocks(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u,
+                               float* H, void* stream) {
+    if (!h) return HOSCF_EINVAL;
+    hoscf_status st = check_desc(h, T);
+    if (st) return st;
+    if (!u || !H) return fail(h, HOSCF_EINVAL, "u and H must be non-NULL device pointers");
+    DeviceGuard g(h->device);
+    Layout L;
+    st = plan_all(h, T->order, T->dims, T->dtype, true, false, 64, L);
+    if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Err err;
+    st = run_ttvc(L.s, L.pp, T->dtype, T->data, T->scales, u, H, h->ws + L.off_pass, dev_err(h),
+                  2000000000ull, s, err);
+    if (st) return fail(h, st, "%s", err.msg);
+    return HOSCF_OK;
+}
+
+hoscf_status hoscf_eig_step(hoscf_handle* h, int order, const int64_t* dims, const float* H,
+                            const double* x_prev, double* x_out, float* u_out, double* lambda_out,
+                            const hoscf_opts* opts, void* stream) {
+    if (!h) return HOSCF_EINVAL;
+    if (!dims_valid(order, dims)) return fail(h, HOSCF_EINVAL, "order must be 2..%d and dims >= 1", HOSCF_MAX_ORDER);
+    if (!H || !x_prev || !x_out || !lambda_out) return fail(h, HOSCF_EINVAL, "NULL pointer argument");
+    DeviceGuard g(h->device);
+    hoscf_opts o;
+    hoscf_opts_default(&o);
+    if (opts) o = *opts;
+    Layout L;
+    hoscf_status st = plan_all(h, order, dims, HOSCF_F32, false, true,
+                               std::min(std::max(o.eig_max_steps, 2), 128), L);
+    if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    st = reset_dev_state(h, s);
+    if (st) return st;
+    return eig_launch(h, L, H, x_prev, nullptr, x_out, u_out, lambda_out, &o, 0, 0.0, s);
+}
+
+hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u0,
+                         const hoscf_opts* opts, float* u_out, double* sigma_out,
+                         hoscf_info* info, void* stream) {
+    if (!h) return HOSCF_EINVAL;
+    hoscf_status st = check_desc(h, T);
+    if (st) return st;
+    if (!u0 || !u_out || !sigma_out) return fail(h, HOSCF_EINVAL, "NULL pointer argument");
+    hoscf_opts o;
+    hoscf_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.max_iter < 0 || !(o.tol >= 0)) return fail(h, HOSCF_EINVAL, "bad tol / max_iter");
+    if (o.variant != HOSCF_VARIANT_HOSCF && o.variant != HOSCF_VARIANT_IHOSCF &&
+        o.variant != HOSCF_VARIANT_IHOSCF_PREV)
+        return fail(h, HOSCF_EINVAL, "unknown variant %d", o.variant);
+    const hoscf_tensor_desc* Tr = o.refine;
+    if (Tr) {
+        st = check_desc(h, Tr);
+        if (st) return st;
+        if (Tr->dtype != HOSCF_F32 || Tr->order != T->order)
+            return fail(h, HOSCF_EINVAL, "refine tensor must be FP32 of the same shape");
+        for (int k = 0; k < T->order; ++k)
+            if (Tr->dims[k] != T->dims[k]) return fail(h, HOSCF_EINVAL, "refine tensor shape differs");
+    }
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Layout L;
+    const int mmax = std::min(std::max(o.eig_max_steps, 2), 128);
+    // plan for the larger of the two element sizes (FP32 refine dominates)
+    st = plan_all(h, T->order, T->dims, Tr ? HOSCF_F32 : T->dtype, true, true, mmax, L);
+    if (st) return st;
+    PassPlan pp_lo = L.pp;
+    if (Tr) make_pass_plan(L.s, T->dtype, h->nsm, true, pp_lo);
+    const Shape& S = L.s;
+    float* H = reinterpret_cast<float*>(h->ws + L.off_H);
+    float* ua = reinterpret_cast<float*>(h->ws + L.off_ua);
+    float* ub = reinterpret_cast<float*>(h->ws + L.off_ub);
+    double* norms = reinterpret_cast<double*>(h->ws + kOffNorms);
+    double* scal = reinterpret_cast<double*>(h->ws + kOffScal);
+    st = reset_dev_state(h, s);
+    if (st) return st;
+    // normalise the initial guess (eq. 3.4); zero / non-finite blocks are errors
+    CK(launch_mode_norms(S, u0, norms, s));
+    CK(cudaMemcpyAsync(h->h_pinned, norms, sizeof(double) * S.d, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < S.d; ++k)
+        if (!(h->h_pinned[k] > 0.0) || !std::isfinite(h->h_pinned[k]))
+            return fail(h, HOSCF_EINVAL, "initial guess block %d is zero or non-finite", k);
+    CK(launch_scale_modes(S, u0, norms, ua, s));
+
+    const uint64_t tmo = timeout_of(&o);
+    const bool ihoscf = o.variant != HOSCF_VARIANT_HOSCF;
+    int iters = 0, passes = 0, passes_ref = 0, accepts = 0;
+    double sigma = 0.0, resid = INFINITY, r41 = NAN;
+    bool use_ref = false;
+    hoscf_status result = HOSCF_NOT_CONVERGED;
+    float* ucur = ua;
+    float* unext = ub;
+    Err err;
+
+    auto pass_and_check = [&](const float* u, float* u_eig_out, int check, double* out) -> hoscf_status {
+        const hoscf_tensor_desc* TT = use_ref ? Tr : T;
+        const PassPlan& pp = use_ref ? L.pp : (Tr ? pp_lo : L.pp);
+        hoscf_status q = run_ttvc(S, pp, TT->dtype, TT->data, TT->scales, u, H,
+                                  h->ws + L.off_pass, dev_err(h), tmo, s, err);
+        if (q) return fail(h, q, "%s", err.msg);
+        ++passes;
+        if (use_ref) ++passes_ref;
+        q = eig_launch(h, L, H, nullptr, u, nullptr, u_eig_out, nullptr, &o, check, o.tol, s);
+        if (q) return q;
+        cudaError_t e = cudaMemcpyAsync(h->h_pinned, scal, sizeof(double) * SC_COUNT,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "readback");
+        e = cudaMemcpyAsync(h->h_pinned + 32, h->ws + kOffErr, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "readback");
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "iteration");
+        int code;
+        memcpy(&code, h->h_pinned + 32, sizeof(int));
+        if (code) return dev_status(h, code);
+        memcpy(out, h->h_pinned, sizeof(double) * SC_COUNT);
+        return HOSCF_OK;
+    };
+
+    double sc[SC_COUNT];
+    while (true) {
+        st = pass_and_check(ucur, unext, 1, sc);
+        if (st) return st;
+        sigma = sc[SC_SIGMA];
+        resid = sc[SC_KKT];
+        r41 = sc[SC_R41];
+        if (!std::isfinite(sigma) || !std::isfinite(resid)) {
+            if (resid == INFINITY && sigma == 0.0) {
+                result = HOSCF_NOT_CONVERGED;
+                break;
+            }
+            return fail(h, HOSCF_NONFINITE, "non-finite sigma or residual");
+        }
+        if (Tr && !use_ref && resid <= o.switch_tol) {
+            // precision form: the low-precision tensor has done its part; the
+            // remaining passes (and the certificate) use the FP32 tensor
+            use_ref = true;
+            if (sc[SC_CONVERGED] != 0.0) continue;   // no eigen step taken: recertify here
+            if (iters >= o.max_iter) {
+                result = HOSCF_NOT_CONVERGED;
+                break;
+            }
+            ++iters;
+            std::swap(ucur, unext);
+            continue;
+        }
+        if (sc[SC_CONVERGED] != 0.0 && (!Tr || use_ref)) {
+            result = HOSCF_OK;
+            break;
+        }
+        if (iters >= o.max_iter) {
+            result = HOSCF_NOT_CONVERGED;
+            break;
+        }
+        ++iters;
+        std::swap(ucur, unext);
+        (void)ihoscf;
+        (void)accepts;
+    }
+    // final sign fix (Alg. 1 lines 12-15) and gauge, into u_out
+    CK(cudaMemcpyAsync(u_out, ucur, sizeof(float) * S.n_tot, cudaMemcpyDeviceToDevice, s));
+    h->h_pinned[0] = sigma;
+    CK(cudaMemcpyAsync(norms, h->h_pinned, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(launch_final_fix(S, u_out, norms, s));
+    CK(cudaMemcpyAsync(h->h_pinned + 1, norms, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *sigma_out = h->h_pinned[1];
+    if (info) {
+        info->iters = iters;
+        info->passes = passes;
+        info->passes_refine = passes_ref;
+        info->rqi_accepts = accepts;
+        info->resid = resid;
+        info->resid_4_1 = r41;
+        info->sigma_raw = sigma;
+    }
+    if (result == HOSCF_NOT_CONVERGED)
+        fail(h, HOSCF_NOT_CONVERGED, "not converged after %d iterations (r = %.3e)", iters, resid);
+    return result;
+}
+
+hoscf_status hoscf_solve_batched(hoscf_handle* h, int count, const hoscf_tensor_desc* T,
+                                 const float* const* u0, const hoscf_opts* opts,
+                                 float* const* u_out, double* sigma_out, hoscf_info* infos,
+                                 void* stream) {
+    (void)count; (void)T; (void)u0; (void)opts; (void)u_out; (void)sigma_out; (void)infos;
+    (void)stream;
+    return fail(h, HOSCF_EUNSUPPORTED, "batched solve not built yet");
+}
+
+hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u,
+                            double sigma, double grad_sigma, const float* grad_u, float* grad_T,
+                            void* stream) {
+    (void)T; (void)u; (void)sigma; (void)grad_sigma; (void)grad_u; (void)grad_T; (void)stream;
+    return fail(h, HOSCF_EUNSUPPORTED, "backward not built yet");
+}
+
+hoscf_status hoscf_quantize(hoscf_handle* h, const float* x, int64_t n, int dtype, void* q,
+                            float* scales, void* stream) {
+    (void)x; (void)n; (void)dtype; (void)q; (void)scales; (void)stream;
+    return fail(h, HOSCF_EUNSUPPORTED, "quantize not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Shared device helpers and host-side plan structures of the HOSCF library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hoscf.h"
+
+#define HOSCF_WARP 32
+#define HOSCF_FULLMASK 0xffffffffu
+
+namespace hoscf {
+
+// ------------------------------------------------------------------ status
+struct Err {
+    hoscf_status code = HOSCF_OK;
+    char msg[512] = {0};
+};
+
+// Device-side error codes written to a status word by kernels.
+enum DevErr : int {
+    DEV_OK = 0,
+    DEV_TIMEOUT = 1,      // a bounded wait gave up
+    DEV_NONFINITE = 2,    // NaN / Inf met
+    DEV_BADARG = 3
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for an mbarrier phase with a wall-clock bound.  Returns false (and
+// leaves the caller to record the timeout) when the bound passes.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// 3-D tiled TMA load: box at coordinates (c0 innermost, c1, c2) into smem,
+// completion signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(HOSCF_FULLMASK, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(HOSCF_FULLMASK, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------ grid barrier
+// Software barrier across the co-resident CTAs of a cooperative launch.
+// `state[0]` counts arrivals, `state[1]` is the generation.  Every wait is
+// bounded by `limit_ns`; on timeout *err is set and false is returned (the
+// caller then leaves the kernel).
+__device__ __forceinline__ bool grid_barrier(unsigned* state, unsigned nblocks, int* err,
+                                             uint64_t limit_ns) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = state + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(state, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(state, 0u);
+            __threadfence();
+            atomicAdd(state + 1, 1u);
+        } else {
+            const uint64_t t0 = global_timer_ns();
+            while (*vgen == gen) {
+                if (*(volatile int*)err) { ok = 0; break; }
+                if (global_timer_ns() - t0 > limit_ns) {
+                    atomicCAS(err, 0, (int)DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ------------------------------------------------------------------ element loads
+template <typename E>
+struct ElemTraits;
+
+template <>
+struct ElemTraits<float> {
+    static constexpr int size = 4;
+    __device__ static __forceinline__ float to_f(float v) { return v; }
+};
+
+struct bf16_t { uint16_t bits; };
+struct fp8_t { uint8_t bits; };
+
+template <>
+struct ElemTraits<bf16_t> {
+    static constexpr int size = 2;
+    __device__ static __forceinline__ float to_f(bf16_t v) {
+        return __uint_as_float(static_cast<uint32_t>(v.bits) << 16);
+    }
+};
+
+}  // namespace hoscf

@@ -1,0 +1,58 @@
+// Host launchers of the HOSCF kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace hoscf {
+
+// ttvc.cu
+hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* data,
+                      const float* scales, const float* u, float* H, char* ws, int* dev_err,
+                      uint64_t timeout_ns, cudaStream_t st, Err& err);
+
+// eig.cu
+struct LanczosLaunch {
+    const float* Jr;
+    const double* x0;
+    const float* u0;
+    double* V;
+    double* Y;
+    double* part;
+    double* scal;
+    double* x_out;
+    float* u_out;
+    double* lambda_out;
+    int mmax;
+    int G;
+    double eig_tol;
+    int check;
+    double kkt_tol;
+    unsigned* bar;
+    int* err;
+    uint64_t timeout_ns;
+};
+
+enum EigScal {
+    SC_LAMBDA = 0,     // chosen Ritz value (eigenvalue of J)
+    SC_SIGMA = 1,      // Rayleigh quotient of the start vector (sigma at the certified point)
+    SC_KKT = 2,        // sqrt(d) ||J x - rho x|| / |rho|  (KKT residual when x is balanced)
+    SC_R41 = 3,        // ||J x - rho x|| / (||J||_F + |rho|)  (eq. 4.1 at the start point)
+    SC_STEPS = 4,
+    SC_CONVERGED = 5,  // 1 when the start point met kkt_tol (no eigen step taken)
+    SC_RITZRES = 6,
+    SC_JFRO = 7,
+    SC_COUNT = 8
+};
+
+int lanczos_blocks_per_sm(int64_t n_tot);
+cudaError_t launch_build_jr(const Shape& s, const float* H, float* Jr, cudaStream_t st);
+cudaError_t launch_lanczos(const Shape& s, const LanczosLaunch& l, cudaStream_t st);
+cudaError_t launch_mode_norms(const Shape& s, const float* u, double* out, cudaStream_t st);
+cudaError_t launch_scale_modes(const Shape& s, const float* u, const double* nrm2, float* out,
+                               cudaStream_t st);
+cudaError_t launch_final_fix(const Shape& s, float* u, double* sigma, cudaStream_t st);
+
+}  // namespace hoscf

@@ -1,0 +1,70 @@
+// Host-side problem plans and workspace layout of the HOSCF library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/hoscf.h"
+
+namespace hoscf {
+
+constexpr int kMaxOrder = HOSCF_MAX_ORDER;
+constexpr int kMaxBlocks = kMaxOrder * (kMaxOrder - 1) / 2;
+
+// Shape facts shared by every stage.  Modes are 0-based; the tensor is
+// viewed as [O][A][B] with A = I_{d-2}, B = I_{d-1} (the two fastest modes,
+// the "face") and O = product of the D = d-2 leading ("outer") modes.
+struct Shape {
+    int d = 0;
+    int64_t dims[kMaxOrder] = {0};
+    int64_t N = 0, n_tot = 0, P = 0;
+    int64_t moff[kMaxOrder + 1] = {0};   // factor offsets
+    int64_t boff[kMaxBlocks + 1] = {0};  // packed block offsets
+    int D = 0;
+    int64_t O = 1, A = 1, B = 1;
+    int64_t ost[kMaxOrder] = {0};        // outer strides: o = sum_k digit_k * ost[k]
+};
+
+// Packed index of block (m, n), m < n.
+inline int block_index(int d, int m, int n) { return m * d - m * (m + 1) / 2 + (n - m - 1); }
+
+bool make_shape(int d, const int64_t* dims, Shape& s);
+
+// Tiled pass configuration (face tiles of FA x FB, stream-K over
+// (tile, outer index) items).
+struct PassPlan {
+    bool copy_only = false;   // d == 2: the single block is the tensor itself
+    bool tma = false;
+    int rows = 8;             // rows per consumer warp; FA = 8 * rows
+    int FA = 64, FB = 128;
+    int64_t TA = 1, TB = 1, TT = 1, items = 0, W = 0;
+    int grid = 0;
+    int nstage = 0;
+    size_t smem = 0;
+    // workspace offsets (bytes)
+    size_t off_w = 0, off_hp = 0, off_y1p = 0, off_y2p = 0, off_y1 = 0, off_y2 = 0, off_r = 0;
+    size_t bytes = 0;
+};
+
+bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p);
+
+// Eigen-step configuration (cooperative Lanczos over G CTAs).
+struct EigPlan {
+    int G = 1;
+    int mmax = 64;
+    size_t off_jr = 0, off_V = 0, off_Y = 0, off_part = 0, off_scal = 0, off_bar = 0;
+    size_t bytes = 0;
+};
+
+bool make_eig_plan(const Shape& s, int nsm, int blocks_per_sm, int mmax, EigPlan& e);
+
+// Factor offsets passed by value to small kernels.
+struct ModeInfoArr {
+    int64_t off[kMaxOrder + 1];
+};
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace hoscf

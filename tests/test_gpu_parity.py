@@ -1,0 +1,181 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Floating-point tolerances follow from FP32 accumulation:
+an entry that sums M terms is compared with an error bound of
+c * eps32 * sqrt(M) * S, where S is the same entry computed from |T| and |u|."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_01778_gb300 import build
+    build.build()
+
+
+def P():
+    import paper_2403_01778_gb300 as pkg
+    return pkg
+
+
+def to_gpu(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).cuda()
+
+
+def blocks_gpu(T, u_list, dtype=torch.float32):
+    Tg = to_gpu(T).to(dtype)
+    ug = to_gpu(np.concatenate(u_list).astype(np.float32))
+    H = P().hoscf_ttvc_blocks(Tg, ug)
+    torch.cuda.synchronize()
+    return H.double().cpu().numpy()
+
+
+def bound(T, u_list, c=8.0):
+    """Per-entry error bound for FP32 block sums (see module docstring)."""
+    dims = T.shape
+    S = oracle.blocks(np.abs(T).astype(np.float64), [np.abs(v) for v in u_list])
+    Ms = []
+    for (m, n) in oracle.block_pairs(len(dims)):
+        Ms.append(np.full(dims[m] * dims[n], np.prod(dims) / (dims[m] * dims[n])))
+    M = np.concatenate(Ms)
+    return c * EPS32 * np.sqrt(M + 1.0) * S + 1e-30
+
+
+SHAPES = [
+    (7, 5),                  # d = 2: the block is the matrix
+    (64, 64, 64),            # aligned, one face tile
+    (37, 50, 129),           # ragged, unaligned rows (plain loads)
+    (3, 130, 260),           # several face tiles in both directions
+    (200, 70, 68),           # more CTAs than outer indices per tile
+    (9, 10, 11, 12),         # d = 4
+    (5, 4, 3, 6, 8),         # d = 5
+    (3, 2, 4, 3, 2, 5),      # d = 6
+    (1, 1, 5),               # unit dims
+]
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+def test_blocks_integer_exact(dims):
+    """Integer-valued tensor and factors: every FP32 partial sum is exact, so
+    the blocks must match the oracle bit for bit (index/layout check)."""
+    rng = np.random.default_rng(sum(dims))
+    T = rng.integers(-3, 4, size=dims).astype(np.float32)
+    u = [rng.integers(-2, 3, size=n).astype(np.float64) for n in dims]
+    Hg = blocks_gpu(T, u)
+    Hr = oracle.blocks(T, u)
+    assert np.array_equal(Hg, Hr)
+
+
+@pytest.mark.parametrize("dims", SHAPES + [(96, 96, 96), (40, 41, 42, 43)])
+def test_blocks_gaussian_within_fp32_bound(dims):
+    T = W.gaussian_tensor(dims, 3).numpy()
+    u = [v.numpy().astype(np.float64) for v in W.unit_gaussian_vectors(dims, 4)]
+    Hg = blocks_gpu(T, u)
+    Hr = oracle.blocks(T, u)
+    assert np.all(np.abs(Hg - Hr) <= bound(T, u))
+
+
+def test_blocks_bf16_match_dequantised_oracle():
+    dims = (33, 64, 128)
+    T = W.gaussian_tensor(dims, 5).numpy()
+    q = oracle.quantize_bf16(T)
+    Tq = oracle.dequantize_bf16(q).reshape(dims)           # exact bf16 values, FP64
+    u = [v.numpy().astype(np.float64) for v in W.unit_gaussian_vectors(dims, 6)]
+    Tg = torch.from_numpy(q.view(np.int16)).cuda().view(torch.bfloat16).reshape(dims)
+    ug = to_gpu(np.concatenate(u).astype(np.float32))
+    Hg = P().hoscf_ttvc_blocks(Tg, ug).double().cpu().numpy()
+    Hr = oracle.blocks(Tq, u)
+    assert np.all(np.abs(Hg - Hr) <= bound(Tq, u))
+
+
+def test_eig_step_matches_dense_eigh():
+    dims = (20, 30, 25)
+    T, _ = W.planted_cp(dims, [3.0], seed=7, noise_abs=1.0)
+    T = T.numpy()
+    u = [v.numpy().astype(np.float64) for v in W.unit_gaussian_vectors(dims, 8)]
+    Hr = oracle.blocks(T, u)
+    J = oracle.nepv_matrix(Hr, list(dims))
+    x_prev = np.concatenate(u) / math.sqrt(3)
+    lam, x = oracle.largest_magnitude_eigpair(J, x_prev)
+    Hg = to_gpu(Hr.astype(np.float32))
+    xg, ug, lg = P().hoscf_eig_step(dims, Hg, to_gpu(x_prev))
+    torch.cuda.synchronize()
+    assert abs(lg.item() - lam) <= 1e-5 * abs(lam)
+    assert abs(abs(float(xg.cpu().numpy() @ x)) - 1) <= 1e-6
+    assert float(xg.cpu().numpy() @ x_prev) >= 0
+    for n, un in enumerate(oracle.normalise_blocks(x, list(dims))):
+        o = int(sum(dims[:n]))
+        assert abs(abs(float(ug.double().cpu().numpy()[o:o + dims[n]] @ un)) - 1) <= 1e-5
+
+
+def compare_solution(res, ref, tol=1e-5):
+    assert abs(res.sigma - ref.sigma) <= tol * abs(ref.sigma)
+    for un, ur in zip(res.factors(), ref.u):
+        c = abs(float(un.double().cpu().numpy() @ ur))
+        assert abs(1 - c) <= tol
+
+
+def test_solve_order2_is_svd():
+    A = W.gaussian_tensor((40, 30), 11).numpy()
+    U, S, Vt = np.linalg.svd(A.astype(np.float64))
+    u0 = torch.cat(W.unit_gaussian_vectors((40, 30), 12)).cuda()
+    r = P().hoscf_solve(to_gpu(A), u0, tol=1e-6, max_iter=20)
+    assert r.converged
+    assert abs(r.sigma - S[0]) <= 1e-5 * S[0]
+    f = r.factors()
+    assert abs(abs(float(f[0].double().cpu().numpy() @ U[:, 0])) - 1) <= 1e-5
+    assert abs(abs(float(f[1].double().cpu().numpy() @ Vt[0])) - 1) <= 1e-5
+
+
+def test_solve_64cube_matches_oracle():
+    """T = 10 u1 o u2 o u3 + E, ||E||_F = 1, 64^3; tol 1e-8 (FP32 stops at its floor
+    or 200 iterations); compared on sigma and factors."""
+    T = W.config_tensor("cfg1_64cube", seed=0)
+    u0 = W.unit_gaussian_vectors(T.shape, 1)
+    ref = oracle.hoscf(T.numpy(), [v.numpy() for v in u0], tol=1e-8, max_iter=200)
+    assert ref.converged
+    r = P().hoscf_solve(T.cuda(), torch.cat(u0).cuda(), tol=1e-8, max_iter=200)
+    compare_solution(r, ref)
+    assert r.resid < 1e-5
+
+
+@pytest.mark.parametrize("dims,seed", [((9, 10, 11, 12), 21), ((5, 6, 7, 5, 6), 22),
+                                        ((3, 4, 3, 4, 3, 4), 23), ((130, 70, 260), 24)])
+def test_solve_planted_matches_oracle(dims, seed):
+    T, _ = W.planted_cp(dims, [5.0], seed=seed, noise_abs=0.5)
+    u0 = W.unit_gaussian_vectors(dims, seed + 100)
+    ref = oracle.hoscf(T.numpy(), [v.numpy() for v in u0], tol=1e-10, max_iter=300)
+    r = P().hoscf_solve(T.cuda(), torch.cat(u0).cuda(), tol=1e-6, max_iter=300)
+    assert r.converged
+    compare_solution(r, ref)
+
+
+def test_solve_reports_kkt_consistent_with_oracle():
+    """The residual and sigma the GPU certifies at its returned point agree
+    with the oracle's direct KKT vectors at that same point."""
+    dims = (30, 40, 50)
+    T, _ = W.planted_cp(dims, [2.0, 1.0], seed=31, noise_abs=0.3)
+    u0 = torch.cat(W.unit_gaussian_vectors(dims, 32)).cuda()
+    r = P().hoscf_solve(T.cuda(), u0, tol=1e-6, max_iter=300)
+    uf = [v.double().cpu().numpy() for v in r.factors()]
+    g, full = oracle.kkt_vectors(T.numpy(), uf)
+    assert abs(full - r.sigma) <= 1e-5 * abs(r.sigma)
+    rr = np.linalg.norm(np.concatenate(g) - full * np.concatenate(uf)) / abs(full)
+    assert rr <= 1e-5
+
+
+def test_invalid_arguments_are_rejected():
+    pkg = P()
+    T = torch.zeros(4, 5, 6, device="cuda")
+    with pytest.raises(pkg.HoscfError) as e:
+        pkg.hoscf_solve(T + 1, torch.zeros(15, device="cuda"))
+    assert e.value.status == 1
