@@ -205,6 +205,31 @@ hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const f
 hoscf_status hoscf_quantize(hoscf_handle* h, const float* x, int64_t n, int dtype, void* q,
                             float* scales, void* stream);
 
+/*
+ * hoscf_ttvc_blocks_static - hoscf_ttvc_blocks without any allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc - for example a plugin whose host application
+ * owns the whole device-memory budget, or code that must not allocate after
+ * start-up - and so cannot create an hoscf_handle (a handle allocates its
+ * workspace with cudaMalloc).
+ *   T, u, H  as for hoscf_ttvc_blocks (the caller still owns and passes the
+ *            inputs and the output); F32 and BF16 tensors.
+ *   stream   cudaStream_t as void* (NULL = legacy default stream); the
+ *            buffers must belong to the calling thread's current device.
+ * Scratch comes from one file-scope device array of
+ * HOSCF_STATIC_SCRATCH_BYTES (64 MiB) that every GPU loading this library
+ * holds until the process exits.  Problems whose scratch would exceed it are
+ * rejected with HOSCF_EINVAL (e.g. 512^3 FP32 fits, 1024^3 does not).  The
+ * first call on each device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture.
+ * All calls share the array and every call overwrites it: calls that overlap
+ * on the GPU (other streams, other threads) race and must be serialised by
+ * the caller.  Asynchronous on `stream`; status codes only (no message).
+ */
+#define HOSCF_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+hoscf_status hoscf_ttvc_blocks_static(const hoscf_tensor_desc* T, const float* u, float* H,
+                                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,8 @@ MAX_ORDER = 8
 # Every entry point the header declares (checked by the ABI test).
 EXPORTS = ("hoscf_create", "hoscf_destroy", "hoscf_last_error", "hoscf_opts_default",
            "hoscf_workspace_size", "hoscf_ttvc_blocks", "hoscf_eig_step", "hoscf_solve",
-           "hoscf_solve_batched", "hoscf_backward", "hoscf_quantize")
+           "hoscf_solve_batched", "hoscf_backward", "hoscf_quantize",
+           "hoscf_ttvc_blocks_static")
 
 
 class TensorDesc(ctypes.Structure):
@@ -80,6 +81,7 @@ def load():
                                    c_void_p, c_void_p, c_void_p]
     lib.hoscf_quantize.argtypes = [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_void_p,
                                    c_void_p]
+    lib.hoscf_ttvc_blocks_static.argtypes = [P(TensorDesc), c_void_p, c_void_p, c_void_p]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name != "hoscf_last_error":

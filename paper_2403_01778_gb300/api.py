@@ -122,6 +122,24 @@ def hoscf_ttvc_blocks(T: torch.Tensor, u: torch.Tensor, H: torch.Tensor | None =
     return H
 
 
+def hoscf_ttvc_blocks_static(T: torch.Tensor, u: torch.Tensor, H: torch.Tensor | None = None,
+                             stream=None) -> torch.Tensor:
+    """hoscf_ttvc_blocks without allocation inside the library: scratch comes
+    from the library's fixed 64 MiB device array (calls must not overlap).
+    The output tensor is allocated here by torch unless H is given."""
+    d = _Desc(T)
+    u = u.contiguous()
+    if u.dtype != torch.float32 or u.numel() != n_tot(d.shape):
+        raise ValueError("u must be float32 with sum(dims) entries")
+    if H is None:
+        H = torch.empty(n_blocks(d.shape), device=T.device, dtype=torch.float32)
+    st = _lib.load().hoscf_ttvc_blocks_static(ctypes.byref(d.desc), ctypes.c_void_p(u.data_ptr()),
+                                              ctypes.c_void_p(H.data_ptr()), _stream_ptr(stream))
+    if st != 0:
+        raise HoscfError(st, "hoscf_ttvc_blocks_static failed")
+    return H
+
+
 def _opts(tol=None, max_iter=None, variant=None, eig_tol=None, eig_max_steps=None,
           refine_desc=None, switch_tol=None, timeout_ns=None) -> Opts:
     o = hoscf_opts_default()
