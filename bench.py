@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg2a_1024cube_rank5")
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-residual extras")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
+    ap.add_argument("--dims", default=None,
+                    help="comma-separated dims: same planted rank-5 recipe at another size")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -119,9 +123,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
-def make_workload(name, seed, device):
+def make_workload(name, seed, device, dims=None):
     import workloads as W
-    T = W.config_tensor(name, seed=seed, device=device)
+    if dims:
+        T, _ = W.planted_cp(dims, [2.0 ** -r for r in range(5)], seed=seed, noise_rel=0.05,
+                            device=device)
+    else:
+        T = W.config_tensor(name, seed=seed, device=device)
     u0 = __import__("torch").cat(W.unit_gaussian_vectors(T.shape, seed + 1, device=device))
     return T, u0
 
@@ -216,7 +224,8 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    T, u0 = make_workload(args.workload, seed=rank, device=dev)
+    dims_arg = [int(v) for v in args.dims.split(",")] if args.dims else None
+    T, u0 = make_workload(args.workload, seed=rank, device=dev, dims=dims_arg)
     dims = tuple(T.shape)
     d = len(dims)
     nb = pass_bytes(dims, T.element_size())
@@ -282,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- end to end: tensor copied from pinned host memory every step
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         host = torch.empty(T.shape, dtype=T.dtype, pin_memory=True)
         host.copy_(T)
         Td = torch.empty_like(T)
@@ -328,7 +337,8 @@ def run_ours(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if T.dtype == torch.float32 else str(T.dtype),
             "data": "synthetic",
-            "config": {"workload": args.workload, "dims": list(dims), "order": d,
+            "config": {"workload": args.workload if not args.dims else "planted rank-5 + 5% noise",
+                       "dims": list(dims), "order": d,
                        "step": "one HOSCF iteration from the seeded x0: TTVc pass + reduce + "
                                "Lanczos eigen step + block normalisation",
                        "l2": "inputs larger than L2 (4 GiB tensor), no flush",
@@ -345,7 +355,7 @@ def run_ours(args, rank, world, local_rank):
         }
         if extras:
             line["extras"] = extras
-        if world == 1:
+        if world == 1 and not args.no_cpu:
             try:
                 line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
             except Exception as exc:   # report, do not hide

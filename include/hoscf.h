@@ -76,6 +76,9 @@ typedef struct {
     int variant;               /* hoscf_variant */
     double eig_tol;            /* Lanczos stop: Ritz residual <= eig_tol * |theta| */
     int eig_max_steps;         /* Lanczos basis size limit (<= 128) */
+    double eig_adapt;          /* hoscf_solve: eigen steps stop at the looser
+                                  max(eig_tol, min(1e-5, eig_adapt * r)), r the
+                                  residual just certified (inexact SCF); 0 = off */
     const hoscf_tensor_desc* refine; /* precision form: FP32 copy of the same tensor, or NULL */
     double switch_tol;         /* precision form: residual at which passes move to `refine` */
     int64_t timeout_ns;        /* bound on every device-side wait (0 = 2 s) */
@@ -97,7 +100,7 @@ hoscf_status hoscf_destroy(hoscf_handle* h);
 const char* hoscf_last_error(const hoscf_handle* h);
 
 /* Defaults: tol 1e-6, max_iter 200, HOSCF, eig_tol 1e-10, eig_max_steps 64,
- * refine NULL, switch_tol 1e-3, timeout 2 s. */
+ * eig_adapt 1e-3, refine NULL, switch_tol 1e-3, timeout 2 s. */
 hoscf_status hoscf_opts_default(hoscf_opts* opts);
 
 /* Bytes of handle workspace a solve of this shape and dtype needs (host args). */
@@ -129,8 +132,13 @@ hoscf_status hoscf_ttvc_blocks(hoscf_handle* h, const hoscf_tensor_desc* T, cons
  *                 to unit length (eq. 3.4; a zero block stays zero).
  *   lambda_out    device, 1 double: the eigenvalue (ties between +l and -l
  *                 resolve to +l).
- * Lanczos with full reorthogonalisation in FP64 (stop: eig_tol,
- * eig_max_steps; opts may be NULL for defaults).  Asynchronous on `stream`.
+ * Lanczos with full reorthogonalisation (stop: Ritz residual <= tol*|theta|
+ * with tol = max(eig_tol, min(1e-5, eig_adapt * sqrt(d) * r0)), r0 the
+ * relative residual ||J x - rho x|| / |rho| of the normalised x_prev, or
+ * tol = eig_tol when eig_adapt = 0; at most eig_max_steps; opts may be NULL
+ * for defaults).  The start-point certificate, the tridiagonal matrix, the
+ * Ritz value and the final normalisation are FP64; the Lanczos vectors are
+ * FP32 like the blocks.  Asynchronous on `stream`.
  */
 hoscf_status hoscf_eig_step(hoscf_handle* h, int order, const int64_t* dims, const float* H,
                             const double* x_prev, double* x_out, float* u_out,

@@ -141,8 +141,10 @@ def hoscf_ttvc_blocks_static(T: torch.Tensor, u: torch.Tensor, H: torch.Tensor |
 
 
 def _opts(tol=None, max_iter=None, variant=None, eig_tol=None, eig_max_steps=None,
-          refine_desc=None, switch_tol=None, timeout_ns=None) -> Opts:
+          refine_desc=None, switch_tol=None, timeout_ns=None, eig_adapt=None) -> Opts:
     o = hoscf_opts_default()
+    if eig_adapt is not None:
+        o.eig_adapt = float(eig_adapt)
     if tol is not None:
         o.tol = float(tol)
     if max_iter is not None:
@@ -163,7 +165,7 @@ def _opts(tol=None, max_iter=None, variant=None, eig_tol=None, eig_max_steps=Non
 
 
 def hoscf_eig_step(dims, H: torch.Tensor, x_prev: torch.Tensor, eig_tol=None, eig_max_steps=None,
-                   stream=None):
+                   eig_adapt=None, stream=None):
     """Largest-magnitude eigenpair of J (Alg. 1 line 5) and the normalised
     factors (lines 6-9).  Returns (x float64, u float32, lambda float64 tensor)."""
     dims = [int(v) for v in dims]
@@ -175,7 +177,7 @@ def hoscf_eig_step(dims, H: torch.Tensor, x_prev: torch.Tensor, eig_tol=None, ei
     u = torch.empty(n, device=H.device, dtype=torch.float32)
     lam = torch.empty(1, device=H.device, dtype=torch.float64)
     arr = (ctypes.c_int64 * len(dims))(*dims)
-    o = _opts(eig_tol=eig_tol, eig_max_steps=eig_max_steps)
+    o = _opts(eig_tol=eig_tol, eig_max_steps=eig_max_steps, eig_adapt=eig_adapt)
     h = handle(H.device.index)
     _check(_lib.load().hoscf_eig_step(h, len(dims), arr, ctypes.c_void_p(H.data_ptr()),
                                       ctypes.c_void_p(x_prev.data_ptr()),
@@ -210,7 +212,7 @@ class SolveResult:
 def hoscf_solve(T: torch.Tensor, u0: torch.Tensor, tol=1e-6, max_iter=200, variant="hoscf",
                 eig_tol=None, eig_max_steps=None, scales=None, refine: torch.Tensor | None = None,
                 switch_tol=None, timeout_ns=None, u_out: torch.Tensor | None = None,
-                stream=None) -> SolveResult:
+                eig_adapt=None, refine_scales=None, stream=None) -> SolveResult:
     """HOSCF / iHOSCF (Algorithm 1, Sec. 4.4).  Synchronous."""
     d = _Desc(T, scales)
     u0 = u0.contiguous()
@@ -219,7 +221,7 @@ def hoscf_solve(T: torch.Tensor, u0: torch.Tensor, tol=1e-6, max_iter=200, varia
         raise ValueError("u0 must be float32 with sum(dims) entries")
     rd = _Desc(refine) if refine is not None else None
     o = _opts(tol, max_iter, variant, eig_tol, eig_max_steps,
-              rd.desc if rd is not None else None, switch_tol, timeout_ns)
+              rd.desc if rd is not None else None, switch_tol, timeout_ns, eig_adapt)
     if u_out is None:
         u_out = torch.empty(n, device=T.device, dtype=torch.float32)
     sigma = ctypes.c_double()

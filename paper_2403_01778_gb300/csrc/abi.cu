@@ -160,7 +160,8 @@ hoscf_status dev_status(hoscf_handle* h, int code) {
 // Eigen step launcher (shared by hoscf_eig_step and the solve driver).
 hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const double* x0,
                         const float* u0, double* x_out, float* u_out, double* lambda_out,
-                        const hoscf_opts* o, int check, double kkt_tol, cudaStream_t st) {
+                        const hoscf_opts* o, int check, double kkt_tol, cudaStream_t st,
+                        double adapt = 0.0) {
     char* eb = h->ws + L.off_eig;
     float* Jr = reinterpret_cast<float*>(eb + L.ep.off_jr);
     cudaError_t e = launch_build_jr(L.s, H, Jr, st);
@@ -184,6 +185,9 @@ hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const 
     ll.bar = reinterpret_cast<unsigned*>(h->ws + kOffBar);
     ll.err = dev_err(h);
     ll.timeout_ns = timeout_of(o);
+    ll.cache_floats = L.ep.cache_floats;
+    ll.adapt = adapt;
+    ll.smem = L.ep.smem;
     e = launch_lanczos(L.s, ll, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "lanczos");
     return HOSCF_OK;
@@ -240,6 +244,7 @@ hoscf_status hoscf_opts_default(hoscf_opts* o) {
     o->variant = HOSCF_VARIANT_HOSCF;
     o->eig_tol = 1e-10;
     o->eig_max_steps = 64;
+    o->eig_adapt = 1e-3;
     o->refine = nullptr;
     o->switch_tol = 1e-3;
     o->timeout_ns = 0;
@@ -300,7 +305,8 @@ hoscf_status hoscf_eig_step(hoscf_handle* h, int order, const int64_t* dims, con
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     st = reset_dev_state(h, s);
     if (st) return st;
-    return eig_launch(h, L, H, x_prev, nullptr, x_out, u_out, lambda_out, &o, 0, 0.0, s);
+    return eig_launch(h, L, H, x_prev, nullptr, x_out, u_out, lambda_out, &o, 0, 0.0, s,
+                      o.eig_adapt);
 }
 
 hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u0,
@@ -370,7 +376,8 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
         if (q) return fail(h, q, "%s", err.msg);
         ++passes;
         if (use_ref) ++passes_ref;
-        q = eig_launch(h, L, H, nullptr, u, nullptr, u_eig_out, nullptr, &o, check, o.tol, s);
+        q = eig_launch(h, L, H, nullptr, u, nullptr, u_eig_out, nullptr, &o, check, o.tol, s,
+                       o.eig_adapt);
         if (q) return q;
         cudaError_t e = cudaMemcpyAsync(h->h_pinned, scal, sizeof(double) * SC_COUNT,
                                         cudaMemcpyDeviceToHost, s);

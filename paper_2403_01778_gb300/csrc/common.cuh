@@ -133,14 +133,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned* state, unsigned nblocks, 
             atomicAdd(state + 1, 1u);
         } else {
             const uint64_t t0 = global_timer_ns();
+            unsigned spins = 0;
             while (*vgen == gen) {
-                if (*(volatile int*)err) { ok = 0; break; }
-                if (global_timer_ns() - t0 > limit_ns) {
-                    atomicCAS(err, 0, (int)DEV_TIMEOUT);
-                    ok = 0;
-                    break;
+                __nanosleep(20);
+                if ((++spins & 255u) == 0) {
+                    if (*(volatile int*)err) { ok = 0; break; }
+                    if (global_timer_ns() - t0 > limit_ns) {
+                        atomicCAS(err, 0, (int)DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();

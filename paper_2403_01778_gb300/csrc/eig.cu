@@ -49,6 +49,8 @@ struct EigArgs {
     double eig_tol;
     int check;              // 1: certify the start point first, stop if r <= kkt_tol
     double kkt_tol;
+    int64_t cache_floats;   // shared floats holding this CTA's Jr rows (0: read from L2)
+    double adapt;           // > 0: inexact eigen steps (see hoscf_opts.eig_adapt)
     unsigned* bar;
     int* err;
     uint64_t timeout_ns;
@@ -60,41 +62,50 @@ __device__ __forceinline__ int mode_of(const EigArgs& a, int q) {
     return m;
 }
 
+__device__ __forceinline__ int64_t row_len(const EigArgs& a, int m) {
+    return a.n - (a.moff[m + 1] - a.moff[m]);
+}
+
 // y[q] = (1/(d-1)) * Jr_row(q) . v  for the rows of this CTA, one warp per
-// row; FP32 products summed in FP32 over runs of 32 terms per lane, FP64
-// beyond.  Also accumulates the squared row norms (for ||J||_F) when asked.
+// row, FP32 (lane sums, then a butterfly).  Rows come from the shared-memory
+// cache when it holds them; on the first call (fill) they are read from L2 and
+// copied into the cache.  Also returns the squared row norms (||J||_F) when
+// sq != NULL (FP32 per row, accumulated in FP64 per CTA).
 __device__ void matvec_rows(const EigArgs& a, const float* __restrict__ vf, int r0, int r1,
-                            double* sq) {
+                            float* cache, const int64_t* crow, bool fill, double* sq,
+                            float* yrow) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double sqacc = 0.0;
+    float sqacc = 0.f;
     for (int q = r0 + warp; q < r1; q += kEigWarps) {
         const int m = mode_of(a, q);
         const int64_t Im = a.moff[m + 1] - a.moff[m];
         const int64_t len = a.n - Im;
-        const float* row = a.Jr + a.jroff[m] + (int64_t)(q - a.moff[m]) * len;
-        const int64_t lo = a.moff[m];
-        double acc = 0.0;
-        double sacc = 0.0;
-        for (int64_t j0 = 0; j0 < len; j0 += 1024) {
-            float f = 0.f, s2 = 0.f;
-            const int64_t j1 = min(len, j0 + 1024);
-            for (int64_t j = j0 + lane; j < j1; j += 32) {
-                const float h = __ldg(row + j);
-                const int64_t col = j < lo ? j : j + Im;
-                f = fmaf(h, vf[col], f);
+        const float* grow = a.Jr + a.jroff[m] + (int64_t)(q - a.moff[m]) * len;
+        float* srow = cache ? cache + crow[q - r0] : nullptr;
+        const bool from_smem = cache && !fill;
+        const int lo = (int)a.moff[m];
+        float f = 0.f, s2 = 0.f;
+        // row columns: J columns [0, lo) then [lo + Im, n)
+        const float* vhi = vf + Im;   // column j + Im for Jr index j >= lo
+        if (from_smem) {
+            for (int j = lane; j < lo; j += 32) f = fmaf(srow[j], vf[j], f);
+            for (int j = lo + lane; j < (int)len; j += 32) f = fmaf(srow[j], vhi[j], f);
+        } else {
+            for (int j = lane; j < (int)len; j += 32) {
+                const float h = __ldg(grow + j);
+                if (srow) srow[j] = h;
+                f = fmaf(h, j < lo ? vf[j] : vhi[j], f);
                 s2 = fmaf(h, h, s2);
             }
-            acc += (double)f;
-            sacc += (double)s2;
         }
-        acc = warp_sum_d(acc);
-        if (sq) sacc = warp_sum_d(sacc);
-        if (lane == 0) {
-            a.Y[q] = acc * (double)a.scale;
-            sqacc += sacc;
+        f = warp_sum(f);
+        if (lane == 0) yrow[q - r0] = f * a.scale;
+        if (sq) {
+            s2 = warp_sum(s2);
+            sqacc += s2;
         }
     }
-    if (sq && lane == 0) atomicAdd(sq, sqacc);   // shared-memory scratch, per CTA
+    if (sq && lane == 0) atomicAdd(sq, (double)sqacc);   // shared-memory scratch, per CTA
 }
 
 // --- small symmetric tridiagonal Ritz problem (k <= kMaxLanczos), one warp.
@@ -144,7 +155,6 @@ __device__ void tridiag_inverse_iteration(const float* al, const float* be, int 
     // Zero pivots are replaced by eps32 * ||T|| (standard inverse iteration).
     const float eps = fmaxf(1.2e-7f * bound, 1e-30f);
     for (int i = 0; i < k; ++i) s[i] = 1.f;
-    // factorisation (LAPACK gttrf-style): diag wa, super wb, super2 wc, multipliers wd
     for (int i = 0; i < k; ++i) {
         wa[i] = al[i] - theta;
         wb[i] = (i < k - 1) ? be[i] : 0.f;
@@ -154,14 +164,13 @@ __device__ void tridiag_inverse_iteration(const float* al, const float* be, int 
         const float sub = be[i];   // element (i+1, i)
         if (fabsf(wa[i]) >= fabsf(sub)) {
             piv[i] = 0;
-            const float l = (wa[i] != 0.f) ? sub / wa[i] : 0.f;
+            const float l = (wa[i] != 0.f) ? __fdividef(sub, wa[i]) : 0.f;
             wd[i] = l;
             wa[i + 1] -= l * wb[i];
         } else {
             piv[i] = 1;
-            const float l = wa[i] / sub;
+            const float l = __fdividef(wa[i], sub);
             wd[i] = l;
-            // swap rows i and i+1
             const float a_ip1 = wa[i + 1];
             wa[i] = sub;
             const float t = wb[i];
@@ -173,8 +182,9 @@ __device__ void tridiag_inverse_iteration(const float* al, const float* be, int 
             }
         }
     }
+    for (int i = 0; i < k; ++i)
+        if (fabsf(wa[i]) <= eps) wa[i] = (wa[i] < 0.f) ? -eps : eps;
     for (int it = 0; it < 2; ++it) {
-        // forward: apply row interchanges and multipliers
         for (int i = 0; i < k - 1; ++i) {
             if (piv[i]) {
                 const float t = s[i];
@@ -184,47 +194,40 @@ __device__ void tridiag_inverse_iteration(const float* al, const float* be, int 
                 s[i + 1] -= wd[i] * s[i];
             }
         }
-        // backward
+        float mx = 0.f;
         for (int i = k - 1; i >= 0; --i) {
             float v = s[i];
             if (i + 1 < k) v -= wb[i] * s[i + 1];
             if (i + 2 < k) v -= wc[i] * s[i + 2];
-            const float dd = fabsf(wa[i]) > eps ? wa[i] : (wa[i] < 0 ? -eps : eps);
-            s[i] = v / dd;
+            s[i] = __fdividef(v, wa[i]);
             if (fabsf(s[i]) > 1e30f) {   // rescale to stay finite
                 for (int t = i; t < k; ++t) s[t] *= 1e-30f;
             }
         }
-        float mx = 0.f;
         for (int i = 0; i < k; ++i) mx = fmaxf(mx, fabsf(s[i]));
         if (!(mx > 0.f) || !isfinite(mx)) {
             for (int i = 0; i < k; ++i) s[i] = (i == 0) ? 1.f : 0.f;
             mx = 1.f;
         }
-        float nrm = 0.f;
-        for (int i = 0; i < k; ++i) {
-            s[i] /= mx;
-            nrm = fmaf(s[i], s[i], nrm);
-        }
-        nrm = rsqrtf(nrm);
-        for (int i = 0; i < k; ++i) s[i] *= nrm;
+        const float inv = 1.f / mx;
+        for (int i = 0; i < k; ++i) s[i] *= inv;
     }
 }
 
 struct RitzOut {
     double theta;
-    double resid;   // |beta_k * s_k|
+    double resid;   // |beta_k * s_k| / ||s||
 };
 
-// Largest-magnitude Ritz pair of T_k (alpha, beta in FP64, k >= 1); writes s
-// (FP64) to shared memory.  Called by warp 0; result broadcast by the caller.
+// Largest-magnitude Ritz pair of T_k (alpha, beta in FP64, k >= 1); writes the
+// unit vector s (FP64) to s_out.  Called by one full warp.
 __device__ RitzOut ritz_largest_magnitude(const double* alpha, const double* beta, int k,
                                           double beta_k, double* s_out, float* scratch) {
     const int lane = threadIdx.x & 31;
-    float* al = scratch;                 // k
-    float* be = al + kMaxLanczos;        // k
-    float* be2 = be + kMaxLanczos;       // k
-    float* sv = be2 + kMaxLanczos;       // k
+    float* al = scratch;
+    float* be = al + kMaxLanczos;
+    float* be2 = be + kMaxLanczos;
+    float* sv = be2 + kMaxLanczos;
     float* wa = sv + kMaxLanczos;
     float* wb = wa + kMaxLanczos;
     float* wc = wb + kMaxLanczos;
@@ -257,48 +260,84 @@ __device__ RitzOut ritz_largest_magnitude(const double* alpha, const double* bet
     const float tmin = __shfl_sync(HOSCF_FULLMASK, ext, 16);
     // ties between +l and -l go to the positive end
     const float theta32 = (tmax >= -tmin) ? tmax : tmin;
-    RitzOut ro;
     if (lane == 0) {
         if (k == 1) {
             sv[0] = 1.f;
         } else {
             tridiag_inverse_iteration(al, be, k, theta32, bound, sv, wa, wb, wc, wd, piv);
         }
-        // refine theta with the FP64 Rayleigh quotient of s
-        double num = 0.0, den = 0.0;
-        for (int i = 0; i < k; ++i) {
-            const double si = sv[i];
-            double ts = alpha[i] * si;
-            if (i > 0) ts += beta[i - 1] * (double)sv[i - 1];
-            if (i < k - 1) ts += beta[i] * (double)sv[i + 1];
-            num += si * ts;
-            den += si * si;
-            s_out[i] = si;
-        }
-        ro.theta = num / den;
-        ro.resid = fabs(beta_k * (double)sv[k - 1]) / sqrt(den);
     }
-    ro.theta = __shfl_sync(HOSCF_FULLMASK, ro.theta, 0);
-    ro.resid = __shfl_sync(HOSCF_FULLMASK, ro.resid, 0);
+    __syncwarp();
+    // FP64 Rayleigh quotient of s, lane-parallel
+    double num = 0.0, den = 0.0;
+    for (int i = lane; i < k; i += 32) {
+        const double si = sv[i];
+        double ts = alpha[i] * si;
+        if (i > 0) ts += beta[i - 1] * (double)sv[i - 1];
+        if (i < k - 1) ts += beta[i] * (double)sv[i + 1];
+        num += si * ts;
+        den += si * si;
+    }
+    num = warp_sum_d(num);
+    den = warp_sum_d(den);
+    const double inv = 1.0 / sqrt(den);
+    for (int i = lane; i < k; i += 32) s_out[i] = (double)sv[i] * inv;
+    RitzOut ro;
+    ro.theta = num / den;
+    ro.resid = fabs(beta_k * (double)sv[k - 1]) * inv;
     return ro;
 }
 
-// Sum over CTAs of partial vectors: out[i] = sum_c part[c * stride + i],
-// i < cnt, fixed order (lane stride then butterfly), one warp per index.
-// Callers alternate between two partial buffers so that a CTA writing the
-// next reduction's partials never overwrites ones another CTA is still
-// reading (consecutive reductions are separated by one grid barrier only).
-__device__ void sum_partials(const double* part, int stride, int G, int cnt, double* out) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < cnt; i += kEigWarps) {
-        double s = 0.0;
-        for (int c = lane; c < G; c += 32) s += ((volatile const double*)part)[(size_t)c * stride + i];
-        s = warp_sum_d(s);
-        if (lane == 0) out[i] = s;
+// out[i] = sum_{c < G} pb[c * ps + i] for i < cnt, every CTA computing the
+// same values in the same order: TPI threads per index (a power of two within
+// a warp) each sum a strided subset of CTAs, then a butterfly combines them.
+// All loads are independent, so one L2 round trip dominates.
+template <typename T>
+__device__ void reduce_partials(const T* pb, int ps, int G, int cnt, T* out) {
+    int tpi = 32;
+    while (tpi > 1 && tpi * cnt > kEigThreads) tpi >>= 1;
+    const int per_round = kEigThreads / tpi;
+    const int sub = threadIdx.x % tpi;
+    for (int base = 0; base < cnt; base += per_round) {
+        const int i = base + (int)threadIdx.x / tpi;
+        T s = 0;
+        if (i < cnt) {
+#pragma unroll 8
+            for (int c = sub; c < G; c += tpi) s += __ldcg(pb + (size_t)c * ps + i);
+        }
+        for (int o = tpi / 2; o > 0; o >>= 1) s += __shfl_xor_sync(HOSCF_FULLMASK, s, o);
+        if (sub == 0 && i < cnt) out[i] = s;
     }
     __syncthreads();
 }
 
+// Convergence checks of the Ritz pair: every step early on (a good warm start
+// converges in a few steps), sparser later.
+__device__ __forceinline__ bool check_now(int k) {
+    return k >= 2 && (k <= 6 || (k <= 16 && (k & 1) == 0) || (k & 3) == 0);
+}
+
+// Grid-wide barrier; a single-CTA launch only needs __syncthreads.
+__device__ __forceinline__ bool eig_sync(const EigArgs& a, int G) {
+    if (G == 1) {
+        __syncthreads();
+        return true;
+    }
+    return grid_barrier(a.bar, G, a.err, a.timeout_ns);
+}
+
+// Lanczos with full reorthogonalisation.  Each CTA owns rows [r0, r1) of J:
+// its rows of Jr (shared-memory cache), its rows of the Lanczos basis and of
+// the work vector, all in shared memory.  Only the current Lanczos vector and
+// the per-CTA dot-product partials cross CTAs, through L2.
+//
+// Precision: the certificate of the start point (sigma = x^T J x, the KKT
+// residual, ||J||_F) and the final normalisation are FP64; the Lanczos
+// vectors, mat-vecs and Gram-Schmidt are FP32 with a second Gram-Schmidt pass
+// whenever cancellation appears; the tridiagonal matrix and the Ritz value
+// are FP64.  J itself is FP32 (the blocks), so FP32 vectors lose nothing that
+// the blocks had, and GB300's FP64 rate (1/64 of FP32) would make FP64 vector
+// work the bottleneck.
 __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     const int G = gridDim.x;
     const int c = blockIdx.x;
@@ -306,117 +345,137 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     const int n = a.n;
     const int R = (n + G - 1) / G;
     const int r0 = min(n, c * R), r1 = min(n, r0 + R);
+    const int nr = r1 - r0;
+    const int M1 = a.mmax + 1;
 
     extern __shared__ __align__(16) uint8_t sm_raw[];
-    float* vf = reinterpret_cast<float*>(sm_raw);                       // n floats
-    double* hsum = reinterpret_cast<double*>(vf + ((n + 3) & ~3));       // kMaxLanczos + 8
-    double* alpha = hsum + kMaxLanczos + 8;                              // kMaxLanczos
-    double* beta = alpha + kMaxLanczos;                                  // kMaxLanczos
-    double* sv = beta + kMaxLanczos;                                     // kMaxLanczos
-    double* misc = sv + kMaxLanczos;                                     // 16
-    float* rscratch = reinterpret_cast<float*>(misc + 16);               // 9 * kMaxLanczos
+    double* hd = reinterpret_cast<double*>(sm_raw);                       // 16 (FP64 scalars)
+    double* alpha = hd + 16;                                              // kMaxLanczos
+    double* beta = alpha + kMaxLanczos;                                   // kMaxLanczos
+    double* sv = beta + kMaxLanczos;                                      // kMaxLanczos
+    double* xrow = sv + kMaxLanczos;                                      // R (Ritz vector rows)
+    int64_t* crow = reinterpret_cast<int64_t*>(xrow + R);                 // R + 2
+    float* hsum = reinterpret_cast<float*>(crow + R + 2);                 // kMaxLanczos + 8
+    float* Vl = hsum + kMaxLanczos + 8;                                   // M1 x R
+    float* Yl = Vl + (size_t)M1 * R;                                      // R
+    float* vf = Yl + ((R + 3) & ~3);                                      // n (padded)
+    float* rscratch = vf + ((n + 3) & ~3);                                // 9 * kMaxLanczos
+    float* jcache = rscratch + 9 * kMaxLanczos;                           // cache_floats
 
-    double* V = a.V;
+    // shared-memory row cache for this CTA's rows of Jr, if it fits
+    if (tid == 0) {
+        int64_t off = 0;
+        for (int q = r0; q < r1; ++q) {
+            crow[q - r0] = off;
+            off += row_len(a, mode_of(a, q));
+        }
+        crow[nr] = off;
+        hd[0] = 0.0;
+        hd[15] = (off <= a.cache_floats) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    float* cache = (hd[15] != 0.0) ? jcache : nullptr;
+
     const int ps = a.pstride;
     int phase = 0;
-    auto pbuf = [&]() { return a.part + (size_t)(phase & 1) * G * ps; };
+    // partial buffers: FP32 for the Lanczos dots, FP64 for the certificate
+    float* pf = reinterpret_cast<float*>(a.part);
+    double* pdd = a.part + (size_t)2 * G * ps;   // after the two FP32 buffers (sized in doubles)
+    auto pbuf = [&]() { return pf + (size_t)(phase & 1) * G * ps; };
     const double sqrt_d = sqrt((double)a.d);
+    // the current vector is exchanged as FP32 through a ping-pong buffer in
+    // global memory (the V workspace): slot (j & 1)
+    float* vx = reinterpret_cast<float*>(a.V);
+    auto vslot = [&](int j) { return vx + (size_t)(j & 1) * ((n + 3) & ~3); };
 
-    // ---- start vector V[0] (unnormalised) for my rows
+    // ---- start vector (unnormalised), FP32
     for (int q = r0 + tid; q < r1; q += kEigThreads) {
-        double v;
-        if (a.x0) {
-            v = a.x0[q];
-        } else {
-            v = (double)a.u0[q] / sqrt_d;
-        }
-        V[q] = v;
+        const float v = a.x0 ? (float)a.x0[q] : (float)((double)a.u0[q] / sqrt_d);
+        Vl[q - r0] = v;
+        vslot(0)[q] = v;
     }
-    if (tid == 0) misc[0] = 0.0;
-    if (!grid_barrier(a.bar, G, a.err, a.timeout_ns)) return;
+    if (!eig_sync(a, G)) return;
 
-    int k = 0;             // basis size
+    int k = 0;
     double beta_last = 0.0;
     RitzOut ro;
     ro.theta = 0.0;
     ro.resid = 0.0;
     bool done = false;
-    int j = 0;
-    for (j = 0; j < a.mmax && !done; ++j) {
-        // stage V[j] into shared memory as FP32
-        for (int q = tid; q < n; q += kEigThreads) vf[q] = (float)((volatile double*)V)[(size_t)j * n + q];
+    for (int j = 0; j < a.mmax && !done; ++j) {
+        // every CTA gets the whole current vector
+        const float* src = vslot(j);
+        for (int q = tid; q < n; q += kEigThreads) vf[q] = __ldcg(src + q);
         __syncthreads();
-        matvec_rows(a, vf, r0, r1, j == 0 ? &misc[0] : nullptr);
+        matvec_rows(a, vf, r0, r1, cache, crow, j == 0, j == 0 ? &hd[0] : nullptr, Yl);
         __syncthreads();
-        // partial dots over my rows: h_i = V[i].y (i <= j), yy, and (j==0) xx, ||J||^2
-        const int cnt = j + 2 + (j == 0 ? 2 : 0);
-        for (int i = warp; i < cnt; i += kEigWarps) {
-            double s = 0.0;
-            if (i <= j) {
-                for (int q = r0 + lane; q < r1; q += 32) s += V[(size_t)i * n + q] * a.Y[q];
-            } else if (i == j + 1) {
-                for (int q = r0 + lane; q < r1; q += 32) s += a.Y[q] * a.Y[q];
-            } else if (i == j + 2) {
-                for (int q = r0 + lane; q < r1; q += 32) s += V[q] * V[q];
-            }
-            s = warp_sum_d(s);
-            if (lane == 0) pbuf()[(size_t)c * ps + i] = (i == j + 3) ? misc[0] : s;
-        }
-        if (!grid_barrier(a.bar, G, a.err, a.timeout_ns)) return;
-        sum_partials(pbuf(), ps, G, cnt, hsum);
-        ++phase;
         if (j == 0) {
-            // normalise the start vector (delayed): v0 = x0/|x0|, y = J v0
-            const double xx = hsum[2];
-            if (!(xx > 0.0) || !isfinite(xx)) {
+            // FP64 certificate of the start point x0 (unnormalised):
+            // rho = x.y / x.x, ||y - rho x||^2, ||Jr||_F^2 -> one reduction
+            double sxy = 0.0, sxx = 0.0, syy = 0.0;
+            for (int q = tid; q < nr; q += kEigThreads) {
+                const double x = Vl[q], y = Yl[q];
+                sxy += x * y;
+                sxx += x * x;
+                syy += y * y;
+            }
+            __shared__ double red[3][kEigWarps];
+            sxy = warp_sum_d(sxy);
+            sxx = warp_sum_d(sxx);
+            syy = warp_sum_d(syy);
+            if (lane == 0) {
+                red[0][warp] = sxy;
+                red[1][warp] = sxx;
+                red[2][warp] = syy;
+            }
+            __syncthreads();
+            if (tid < 3) {
+                double t = 0.0;
+                for (int w8 = 0; w8 < kEigWarps; ++w8) t += red[tid][w8];
+                pdd[(size_t)c * 4 + tid] = t;
+            }
+            if (tid == 3) pdd[(size_t)c * 4 + 3] = hd[0];
+            if (!eig_sync(a, G)) return;
+            reduce_partials<double>(pdd, 4, G, 4, hd + 1);   // hd[1..4]
+            const double xy = hd[1], xx = hd[2], yy = hd[3];
+            if (!(xx > 0.0) || !isfinite(xx) || !isfinite(yy)) {
                 if (tid == 0) atomicCAS(a.err, 0, (int)DEV_NONFINITE);
                 return;
             }
+            const double rho = xy / xx;
+            // ||J v0 - rho v0||^2 = (yy - xy^2/xx) / xx, evaluated as a sum of
+            // squares to avoid cancellation
             const double inv = 1.0 / sqrt(xx);
-            for (int q = r0 + tid; q < r1; q += kEigThreads) {
-                V[q] *= inv;
-                a.Y[q] *= inv;
+            double sw = 0.0;
+            for (int q = tid; q < nr; q += kEigThreads) {
+                const double w = ((double)Yl[q] - rho * (double)Vl[q]) * inv;
+                sw += w * w;
             }
-            if (tid == 0) {
-                hsum[0] *= inv * inv;
-                hsum[1] *= inv * inv;
-                misc[1] = sqrt(hsum[3]) * (double)a.scale;   // ||J||_F
-            }
-            __syncthreads();
-            // exact ||y - alpha0 v0||^2 over my rows (one more reduction)
-            const double al0 = hsum[0];
-            double s = 0.0;
-            for (int q = r0 + tid; q < r1; q += kEigThreads) {
-                const double w = a.Y[q] - al0 * V[q];
-                a.Y[q] = w;
-                s += w * w;
-            }
-            s = warp_sum_d(s);
-            __shared__ double red[kEigWarps];
-            if (lane == 0) red[warp] = s;
+            sw = warp_sum_d(sw);
+            if (lane == 0) red[0][warp] = sw;
             __syncthreads();
             if (tid == 0) {
                 double t = 0.0;
-                for (int w8 = 0; w8 < kEigWarps; ++w8) t += red[w8];
-                pbuf()[(size_t)c * ps + 0] = t;
+                for (int w8 = 0; w8 < kEigWarps; ++w8) t += red[0][w8];
+                pdd[(size_t)(G + c) * 4] = t;
             }
-            if (!grid_barrier(a.bar, G, a.err, a.timeout_ns)) return;
-            sum_partials(pbuf(), ps, G, 1, misc + 2);
-            ++phase;
-            const double b0 = sqrt(fmax(misc[2], 0.0));
-            const double rho = al0;
+            if (!eig_sync(a, G)) return;
+            reduce_partials<double>(pdd + (size_t)G * 4, 4, G, 1, hd + 5);
+            const double b0 = sqrt(fmax(hd[5], 0.0));
+            const double jfro = sqrt(hd[4]) * (double)a.scale;
+            const double r = (rho != 0.0) ? sqrt_d * b0 / fabs(rho) : INFINITY;
             if (c == 0 && tid == 0) {
                 a.scal[SC_SIGMA] = rho;
-                a.scal[SC_KKT] = (rho != 0.0) ? sqrt_d * b0 / fabs(rho) : INFINITY;
-                a.scal[SC_R41] = b0 / (misc[1] + fabs(rho));
-                a.scal[SC_JFRO] = misc[1];
+                a.scal[SC_KKT] = r;
+                a.scal[SC_R41] = b0 / (jfro + fabs(rho));
+                a.scal[SC_JFRO] = jfro;
                 a.scal[SC_CONVERGED] = 0.0;
             }
             if (!isfinite(rho) || !isfinite(b0)) {
                 if (tid == 0) atomicCAS(a.err, 0, (int)DEV_NONFINITE);
                 return;
             }
-            if (a.check && rho != 0.0 && sqrt_d * b0 / fabs(rho) <= a.kkt_tol) {
+            if (a.check && rho != 0.0 && r <= a.kkt_tol) {
                 // the start point is certified: no eigen step
                 if (c == 0 && tid == 0) {
                     a.scal[SC_CONVERGED] = 1.0;
@@ -426,112 +485,145 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 }
                 return;
             }
-            alpha[0] = rho;
-            // w = y - alpha0 v0 -> V[1] after normalisation
+            if (a.adapt > 0.0 && rho != 0.0) a.eig_tol = fmax(a.eig_tol, fmin(1e-5, a.adapt * r));
+            // Lanczos start: v0 = x0/|x0|, w = J v0 - rho v0 (FP32)
+            const float finv = (float)inv, frho = (float)rho;
+            for (int q = tid; q < nr; q += kEigThreads) {
+                const float v = Vl[q] * finv;
+                Vl[q] = v;
+                Yl[q] = Yl[q] * finv - frho * v;
+            }
+            if (tid == 0) {
+                alpha[0] = rho;
+                beta[0] = b0;
+            }
             beta_last = b0;
-            if (tid == 0) beta[0] = b0;
             k = 1;
         } else {
-            // full classical Gram-Schmidt against V[0..j]
-            double ssq = 0.0;
-            for (int i = 0; i <= j; ++i) ssq += hsum[i] * hsum[i];
-            const double yy = hsum[j + 1];
-            double b2 = yy - ssq;
-            if (tid == 0) alpha[j] = hsum[j];
-            __syncthreads();
-            for (int q = r0 + tid; q < r1; q += kEigThreads) {
-                double w = a.Y[q];
-                for (int i = 0; i <= j; ++i) w -= hsum[i] * V[(size_t)i * n + q];
-                a.Y[q] = w;
+            // partial dots over my rows: h_i = V[i].y (i <= j), yy
+            const int cnt = j + 2;
+            for (int i = warp; i < cnt; i += kEigWarps) {
+                float s = 0.f;
+                if (i <= j) {
+                    for (int q = lane; q < nr; q += 32) s = fmaf(Vl[(size_t)i * R + q], Yl[q], s);
+                } else {
+                    for (int q = lane; q < nr; q += 32) s = fmaf(Yl[q], Yl[q], s);
+                }
+                s = warp_sum(s);
+                if (lane == 0) pbuf()[(size_t)c * ps + i] = s;
             }
-            if (b2 < 0.25 * yy) {
+            if (!eig_sync(a, G)) return;
+            reduce_partials<float>(pbuf(), ps, G, cnt, hsum);
+            ++phase;
+            // full classical Gram-Schmidt against V[0..j]
+            float ssq = 0.f;
+            for (int i = 0; i <= j; ++i) ssq = fmaf(hsum[i], hsum[i], ssq);
+            const float yy = hsum[j + 1];
+            float b2 = yy - ssq;
+            for (int q = tid; q < nr; q += kEigThreads) {
+                float w = Yl[q];
+                for (int i = 0; i <= j; ++i) w = fmaf(-hsum[i], Vl[(size_t)i * R + q], w);
+                Yl[q] = w;
+            }
+            double alj = hsum[j];
+            if (b2 < 0.25f * yy) {
                 // heavy cancellation: second Gram-Schmidt pass with exact norm
                 __syncthreads();
                 for (int i = warp; i < j + 2; i += kEigWarps) {
-                    double s = 0.0;
+                    float s = 0.f;
                     if (i <= j) {
-                        for (int q = r0 + lane; q < r1; q += 32) s += V[(size_t)i * n + q] * a.Y[q];
+                        for (int q = lane; q < nr; q += 32) s = fmaf(Vl[(size_t)i * R + q], Yl[q], s);
                     } else {
-                        for (int q = r0 + lane; q < r1; q += 32) s += a.Y[q] * a.Y[q];
+                        for (int q = lane; q < nr; q += 32) s = fmaf(Yl[q], Yl[q], s);
                     }
-                    s = warp_sum_d(s);
+                    s = warp_sum(s);
                     if (lane == 0) pbuf()[(size_t)c * ps + i] = s;
                 }
-                if (!grid_barrier(a.bar, G, a.err, a.timeout_ns)) return;
-                sum_partials(pbuf(), ps, G, j + 2, hsum);
+                if (!eig_sync(a, G)) return;
+                reduce_partials<float>(pbuf(), ps, G, j + 2, hsum);
                 ++phase;
-                double ssq2 = 0.0;
-                for (int i = 0; i <= j; ++i) ssq2 += hsum[i] * hsum[i];
+                float ssq2 = 0.f;
+                for (int i = 0; i <= j; ++i) ssq2 = fmaf(hsum[i], hsum[i], ssq2);
                 b2 = hsum[j + 1] - ssq2;
-                if (tid == 0) alpha[j] += hsum[j];
-                __syncthreads();
-                for (int q = r0 + tid; q < r1; q += kEigThreads) {
-                    double w = a.Y[q];
-                    for (int i = 0; i <= j; ++i) w -= hsum[i] * V[(size_t)i * n + q];
-                    a.Y[q] = w;
+                alj += hsum[j];
+                for (int q = tid; q < nr; q += kEigThreads) {
+                    float w = Yl[q];
+                    for (int i = 0; i <= j; ++i) w = fmaf(-hsum[i], Vl[(size_t)i * R + q], w);
+                    Yl[q] = w;
                 }
             }
-            beta_last = sqrt(fmax(b2, 0.0));
-            if (tid == 0) beta[j] = beta_last;
+            beta_last = sqrt(fmax((double)b2, 0.0));
+            if (tid == 0) {
+                alpha[j] = alj;
+                beta[j] = beta_last;
+            }
             k = j + 1;
         }
         __syncthreads();
-        // convergence test on the Ritz pair (every 4 steps, and at the limits)
-        const bool last = (k == a.mmax) || (k == n) || beta_last <= 1e-300;
-        if (k >= 2 && ((k % 4) == 0 || last)) {
+        // convergence test on the largest-magnitude Ritz pair
+        const bool last = (k == a.mmax) || (k == n) || !(beta_last > 1e-30);
+        if (check_now(k) || last) {
             __shared__ RitzOut s_ro;
-            if (warp == 0) {
-                RitzOut t = ritz_largest_magnitude(alpha, beta, k, beta_last, sv, rscratch);
-                if (lane == 0) s_ro = t;
+            if (k >= 2) {
+                if (warp == 0) {
+                    RitzOut t = ritz_largest_magnitude(alpha, beta, k, beta_last, sv, rscratch);
+                    if (lane == 0) s_ro = t;
+                }
+            } else if (tid == 0) {
+                sv[0] = 1.0;
+                s_ro.theta = alpha[0];
+                s_ro.resid = beta_last;
             }
             __syncthreads();
             ro = s_ro;
             if (ro.resid <= a.eig_tol * fabs(ro.theta) || last) done = true;
-        } else if (last) {
-            if (tid == 0) sv[0] = 1.0;
-            ro.theta = alpha[0];
-            ro.resid = beta_last;
-            done = true;
         }
-        __syncthreads();
         if (!done) {
-            const double inv = 1.0 / beta_last;
-            for (int q = r0 + tid; q < r1; q += kEigThreads) V[(size_t)(j + 1) * n + q] = a.Y[q] * inv;
-            if (!grid_barrier(a.bar, G, a.err, a.timeout_ns)) return;
+            const float inv = (float)(1.0 / beta_last);
+            float* dst = vslot(j + 1);
+            for (int q = tid; q < nr; q += kEigThreads) {
+                const float v = Yl[q] * inv;
+                Vl[(size_t)(j + 1) * R + q] = v;
+                dst[r0 + q] = v;
+            }
+            if (!eig_sync(a, G)) return;
         }
     }
-    // ---- Ritz vector x = V[0..k-1] s for my rows; block norms and sign
+    // ---- Ritz vector x = V[0..k-1] s for my rows (FP64 accumulation); block
+    // norms and the sign reference <x, v0>
     const int d = a.d;
-    for (int q = r0 + tid; q < r1; q += kEigThreads) {
+    for (int q = tid; q < nr; q += kEigThreads) {
         double x = 0.0;
-        for (int i = 0; i < k; ++i) x += sv[i] * V[(size_t)i * n + q];
-        a.Y[q] = x;
+        for (int i = 0; i < k; ++i) x += sv[i] * (double)Vl[(size_t)i * R + q];
+        xrow[q] = x;
     }
     __syncthreads();
+    auto xval = [&](int q) -> double { return xrow[q]; };
     // partials: [0..d-1] block norms^2, [d] x . v0
     for (int i = warp; i < d + 1; i += kEigWarps) {
         double s = 0.0;
         if (i < d) {
             const int lo = max(r0, (int)a.moff[i]), hi = min(r1, (int)a.moff[i + 1]);
-            for (int q = lo + lane; q < hi; q += 32) s += a.Y[q] * a.Y[q];
+            for (int q = lo + lane; q < hi; q += 32) s += xval(q - r0) * xval(q - r0);
         } else {
-            for (int q = r0 + lane; q < r1; q += 32) s += a.Y[q] * V[q];
+            for (int q = lane; q < nr; q += 32) s += xval(q) * (double)Vl[q];
         }
         s = warp_sum_d(s);
-        if (lane == 0) pbuf()[(size_t)c * ps + i] = s;
+        if (lane == 0) pdd[(size_t)8 * G + (size_t)c * (kMaxOrder + 1) + i] = s;
     }
-    if (!grid_barrier(a.bar, G, a.err, a.timeout_ns)) return;
-    sum_partials(pbuf(), ps, G, d + 1, hsum);
+    if (!eig_sync(a, G)) return;
+    reduce_partials<double>(pdd + (size_t)8 * G, kMaxOrder + 1, G, d + 1, hd + 6);
+    const double* bn = hd + 6;
     double tot = 0.0;
-    for (int m = 0; m < d; ++m) tot += hsum[m];
-    const double sgn = (hsum[d] < 0.0) ? -1.0 : 1.0;
+    for (int m = 0; m < d; ++m) tot += bn[m];
+    const double sgn = (bn[d] < 0.0) ? -1.0 : 1.0;
     const double invx = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
     for (int q = r0 + tid; q < r1; q += kEigThreads) {
-        const double x = a.Y[q] * sgn;
+        const double x = xval(q - r0) * sgn;
         if (a.x_out) a.x_out[q] = x * invx;
         if (a.u_out) {
             const int m = mode_of(a, q);
-            const double nb = hsum[m];
+            const double nb = bn[m];
             a.u_out[q] = nb > 0.0 ? (float)(x / sqrt(nb)) : 0.f;
         }
     }
@@ -680,33 +772,76 @@ __global__ void final_fix_kernel(float* __restrict__ u, int d, ModeInfoArr mi, d
 }
 
 // ---------------------------------------------------------------- host
-static size_t lanczos_smem(int64_t n) {
-    return sizeof(float) * (size_t)((n + 3) & ~3) +
-           sizeof(double) * (size_t)(kMaxLanczos + 8 + 3 * kMaxLanczos + 16) +
-           sizeof(float) * 9 * kMaxLanczos + 64;
+static size_t lanczos_smem_base(int64_t n, int R, int mmax) {
+    return sizeof(double) * (size_t)(16 + 3 * kMaxLanczos) + sizeof(double) * (size_t)R +
+           sizeof(int64_t) * (size_t)(R + 2) +
+           sizeof(float) * (size_t)(kMaxLanczos + 8) + sizeof(float) * (size_t)(mmax + 1) * R +
+           sizeof(float) * (size_t)((R + 3) & ~3) + sizeof(float) * (size_t)((n + 3) & ~3) +
+           sizeof(float) * 9 * kMaxLanczos + 256;
+}
+
+constexpr size_t kEigSmemCap = 220 * 1024;
+
+// Rows of Jr owned by a CTA when the n rows are split over G CTAs: the cache
+// size is the largest such row block.
+static int64_t max_rows_floats(const Shape& s, int G) {
+    const int64_t n = s.n_tot;
+    const int64_t R = (n + G - 1) / G;
+    int64_t best = 0;
+    for (int c = 0; c < G; ++c) {
+        const int64_t r0 = std::min(n, c * R), r1 = std::min(n, r0 + R);
+        int64_t f = 0;
+        for (int m = 0; m < s.d; ++m) {
+            const int64_t lo = std::max(r0, s.moff[m]), hi = std::min(r1, s.moff[m + 1]);
+            if (hi > lo) f += (hi - lo) * (n - s.dims[m]);
+        }
+        best = std::max(best, f);
+    }
+    return best;
 }
 
 int lanczos_blocks_per_sm(int64_t n_tot) {
-    int nb = 0;
-    const size_t sm = lanczos_smem(n_tot);
-    cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lanczos_kernel, kEigThreads, sm) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        nb = 1;
-    }
-    return nb > 0 ? nb : 1;
+    (void)n_tot;
+    return 1;   // the kernel sizes its shared-memory row cache to own the SM
 }
 
 bool make_eig_plan(const Shape& s, int nsm, int blocks_per_sm, int mmax, EigPlan& e) {
+    (void)blocks_per_sm;
     e = EigPlan();
     if (mmax < 2) mmax = 2;
     if (mmax > kMaxLanczos) mmax = kMaxLanczos;
     e.mmax = mmax;
-    if (lanczos_smem(s.n_tot) > 200 * 1024) return false;
-    const int64_t want = (s.n_tot + 15) / 16;   // ~16 rows per CTA
-    int64_t G = std::min<int64_t>(want, (int64_t)nsm * std::max(1, blocks_per_sm));
-    e.G = (int)std::max<int64_t>(1, G);
+    // One CTA when the whole of J fits in its shared memory (no grid
+    // barriers at all); otherwise the fewest CTAs (from ~32 rows each) whose
+    // row blocks of J fit, up to one per SM.
+    int64_t G = 1;
+    {
+        const size_t base1 = lanczos_smem_base(s.n_tot, (int)s.n_tot, mmax);
+        if (base1 + sizeof(float) * 2 * (size_t)s.P > kEigSmemCap)
+            G = std::min<int64_t>(std::max<int64_t>(2, (s.n_tot + 31) / 32), nsm);
+    }
+    int64_t cache = 0;
+    for (;; ++G) {
+        const int64_t R = (s.n_tot + G - 1) / G;
+        const size_t base = lanczos_smem_base(s.n_tot, (int)R, mmax);
+        if (base > kEigSmemCap) {
+            if (G >= nsm) return false;
+            continue;
+        }
+        const int64_t need = max_rows_floats(s, (int)G);
+        if (base + sizeof(float) * (size_t)need <= kEigSmemCap) {
+            cache = need;
+            break;
+        }
+        if (G >= nsm) {
+            cache = 0;   // rows do not fit: stream them from L2 every step
+            break;
+        }
+    }
+    e.G = (int)G;
+    e.cache_floats = cache;
+    e.smem = lanczos_smem_base(s.n_tot, (int)((s.n_tot + G - 1) / G), mmax) +
+             sizeof(float) * (size_t)((cache + 3) & ~int64_t(3));
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -716,7 +851,8 @@ bool make_eig_plan(const Shape& s, int nsm, int blocks_per_sm, int mmax, EigPlan
     e.off_jr = take(sizeof(float) * 2 * (size_t)s.P);
     e.off_V = take(sizeof(double) * (size_t)(mmax + 1) * s.n_tot);
     e.off_Y = take(sizeof(double) * (size_t)s.n_tot);
-    e.off_part = take(sizeof(double) * 2 * (size_t)e.G * (mmax + 8));
+    e.off_part = take(sizeof(double) * 2 * (size_t)e.G * (mmax + 8) +
+                      sizeof(double) * 2 * (size_t)e.G * (kMaxOrder + 1));
     e.bytes = off;
     return true;
 }
@@ -775,7 +911,9 @@ cudaError_t launch_lanczos(const Shape& s, const LanczosLaunch& l, cudaStream_t 
     a.bar = l.bar;
     a.err = l.err;
     a.timeout_ns = l.timeout_ns;
-    const size_t sm = lanczos_smem(s.n_tot);
+    a.cache_floats = l.cache_floats;
+    a.adapt = l.adapt;
+    const size_t sm = l.smem;
     cudaError_t e = cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;

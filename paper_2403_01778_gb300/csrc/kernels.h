@@ -13,6 +13,10 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
                       const float* scales, const float* u, float* H, char* ws, int* dev_err,
                       uint64_t timeout_ns, cudaStream_t st, Err& err);
 
+// small.cu
+cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const void* data,
+                      const float* u, float* H, char* ws, cudaStream_t st);
+
 // eig.cu
 struct LanczosLaunch {
     const float* Jr;
@@ -33,6 +37,9 @@ struct LanczosLaunch {
     unsigned* bar;
     int* err;
     uint64_t timeout_ns;
+    int64_t cache_floats;
+    size_t smem;
+    double adapt;   // > 0: eig_tol = max(eig_tol, min(1e-5, adapt * r)) after the certificate
 };
 
 enum EigScal {

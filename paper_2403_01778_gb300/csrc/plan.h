@@ -32,10 +32,27 @@ inline int block_index(int d, int m, int n) { return m * d - m * (m + 1) / 2 + (
 
 bool make_shape(int d, const int64_t* dims, Shape& s);
 
+// Small-face pass (A*B <= 1024): contiguous outer ranges per CTA, in-CTA fold.
+struct SmallPlanInfo {
+    int G = 0;
+    int64_t L = 0;
+    int Rmax[kMaxOrder] = {0};
+    int64_t x1off[kMaxOrder] = {0}, x2off[kMaxOrder] = {0}, poff[kMaxBlocks] = {0};
+    int npairs = 0;
+    int pm[kMaxBlocks] = {0}, pn[kMaxBlocks] = {0};
+    int64_t patch_floats = 0;
+    size_t smem = 0;
+    size_t off_patch = 0, off_cover = 0;   // workspace offsets (bytes)
+};
+
+bool make_small_plan(const Shape& s, int nsm, SmallPlanInfo& sp);
+
 // Tiled pass configuration (face tiles of FA x FB, stream-K over
 // (tile, outer index) items).
 struct PassPlan {
     bool copy_only = false;   // d == 2: the single block is the tensor itself
+    bool small = false;       // small-face path (see SmallPlanInfo)
+    SmallPlanInfo sp;
     bool tma = false;
     int rows = 8;             // rows per consumer warp; FA = 8 * rows
     int FA = 64, FB = 128;
@@ -50,10 +67,14 @@ struct PassPlan {
 
 bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p);
 
+
+
 // Eigen-step configuration (cooperative Lanczos over G CTAs).
 struct EigPlan {
     int G = 1;
     int mmax = 64;
+    int64_t cache_floats = 0;   // per-CTA shared-memory cache of J rows (floats)
+    size_t smem = 0;            // dynamic shared memory of the Lanczos kernel
     size_t off_jr = 0, off_V = 0, off_Y = 0, off_part = 0, off_scal = 0, off_bar = 0;
     size_t bytes = 0;
 };

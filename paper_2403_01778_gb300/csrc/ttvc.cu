@@ -73,6 +73,16 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
         return true;
     }
     const int es = elem_size(dtype);
+    if (dtype != HOSCF_F8E4M3 && make_small_plan(s, nsm, p.sp)) {
+        p.small = true;
+        size_t off = 0;
+        p.sp.off_patch = off;
+        off = align_up(off + sizeof(float) * (size_t)p.sp.G * p.sp.patch_floats, 256);
+        p.sp.off_cover = off;
+        off = align_up(off + sizeof(int) * (size_t)p.sp.G * std::max(1, s.D) * 2, 256);
+        p.bytes = off;
+        return true;
+    }
     p.rows = 8;
     p.FA = 8 * p.rows;
     p.FB = 128;
@@ -587,6 +597,10 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         err.code = HOSCF_EUNSUPPORTED;
         snprintf(err.msg, sizeof(err.msg), "dtype %d not supported by this pass", dtype);
         return err.code;
+    }
+    if (p.small) {
+        HOSCF_CK(run_small(s, p.sp, dtype, data, u, H, ws, st));
+        return HOSCF_OK;
     }
     const OuterInfo oi = make_outer(s);
     float* w = reinterpret_cast<float*>(ws + p.off_w);

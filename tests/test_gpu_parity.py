@@ -60,6 +60,11 @@ SHAPES = [
     (5, 4, 3, 6, 8),         # d = 5
     (3, 2, 4, 3, 2, 5),      # d = 6
     (1, 1, 5),               # unit dims
+    (5, 6, 40, 36),          # d = 4, tiled path (face 1440) with outer folds
+    (7, 9, 11, 13, 5),       # small-face path, d = 5
+    (2, 3, 2, 3, 2, 3, 2, 3),  # d = 8
+    (4, 5, 3, 7, 2, 9, 2),   # d = 7, ragged
+    (33, 1, 17, 32),         # a unit mode among outer ones
 ]
 
 
@@ -97,6 +102,30 @@ def test_blocks_bf16_match_dequantised_oracle():
     assert np.all(np.abs(Hg - Hr) <= bound(Tq, u))
 
 
+@pytest.mark.parametrize("dims,nsample", [((24, 20, 24, 20, 24, 20), 40), ((8,) * 8, 40),
+                                           ((32, 32, 32, 32, 16), 24)])
+def test_blocks_full_size_sampled_entries(dims, nsample):
+    """Paper-scale small-face shapes: sampled entries of every block against the
+    oracle's one-entry definition (eq. 3.3)."""
+    T = W.planted_cp(dims, [1.0], seed=61, noise_abs=0.05)[0]
+    u = [v.numpy().astype(np.float64) for v in W.unit_gaussian_vectors(dims, 62)]
+    Hg = P().hoscf_ttvc_blocks(T.cuda(), to_gpu(np.concatenate(u).astype(np.float32)))
+    Hg = Hg.double().cpu().numpy()
+    Tn = T.numpy()
+    Ta = np.abs(Tn)
+    ua = [np.abs(v) for v in u]
+    rng = np.random.default_rng(63)
+    offs, _ = oracle.block_offsets(list(dims))
+    M = np.prod(dims)
+    for (m, n), o in zip(oracle.block_pairs(len(dims)), offs):
+        for _ in range(max(1, nsample // len(offs))):
+            i, j = int(rng.integers(dims[m])), int(rng.integers(dims[n]))
+            ref = oracle.block_entry(Tn, u, m, n, i, j)
+            sc = oracle.block_entry(Ta, ua, m, n, i, j)
+            tol = 8 * EPS32 * math.sqrt(M / (dims[m] * dims[n]) + 1) * sc + 1e-30
+            assert abs(Hg[o + i * dims[n] + j] - ref) <= tol, ((m, n), i, j)
+
+
 def test_eig_step_matches_dense_eigh():
     dims = (20, 30, 25)
     T, _ = W.planted_cp(dims, [3.0], seed=7, noise_abs=1.0)
@@ -107,7 +136,7 @@ def test_eig_step_matches_dense_eigh():
     x_prev = np.concatenate(u) / math.sqrt(3)
     lam, x = oracle.largest_magnitude_eigpair(J, x_prev)
     Hg = to_gpu(Hr.astype(np.float32))
-    xg, ug, lg = P().hoscf_eig_step(dims, Hg, to_gpu(x_prev))
+    xg, ug, lg = P().hoscf_eig_step(dims, Hg, to_gpu(x_prev), eig_adapt=0.0)
     torch.cuda.synchronize()
     assert abs(lg.item() - lam) <= 1e-5 * abs(lam)
     assert abs(abs(float(xg.cpu().numpy() @ x)) - 1) <= 1e-6
