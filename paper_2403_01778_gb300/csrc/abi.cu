@@ -69,7 +69,8 @@ struct Layout {
     Shape s;
     PassPlan pp;
     EigPlan ep;
-    size_t off_pass = 0, off_eig = 0, off_H = 0, off_H2 = 0, off_ua = 0, off_ub = 0, off_x = 0;
+    size_t off_pass = 0, off_eig = 0, off_H = 0, off_H2 = 0, off_ua = 0, off_ub = 0, off_uc = 0,
+           off_x = 0;
     size_t total = 0;
 };
 
@@ -110,14 +111,23 @@ hoscf_status check_desc(hoscf_handle* h, const hoscf_tensor_desc* T) {
     return HOSCF_OK;
 }
 
+// Workspace for one shape.  `dtype2` (>= 0) is a second tensor dtype whose
+// pass must fit in the same pass region (precision form: low-precision tensor
+// plus its FP32 refinement copy).
 hoscf_status plan_all(hoscf_handle* h, int order, const int64_t* dims, int dtype, bool pass,
-                      bool eig, int mmax, Layout& L) {
+                      bool eig, int mmax, Layout& L, int dtype2 = -1) {
     if (!make_shape(order, dims, L.s)) return fail(h, HOSCF_EINVAL, "invalid shape");
     size_t off = kHeadBytes;
     if (pass) {
         make_pass_plan(L.s, dtype, h->nsm, true, L.pp);
+        size_t need = L.pp.bytes;
+        if (dtype2 >= 0) {
+            PassPlan p2;
+            make_pass_plan(L.s, dtype2, h->nsm, true, p2);
+            need = std::max(need, p2.bytes);
+        }
         L.off_pass = off;
-        off = align_up(off + L.pp.bytes, 256);
+        off = align_up(off + need, 256);
     }
     if (eig) {
         if (!make_eig_plan(L.s, h->nsm, lanczos_blocks_per_sm(L.s.n_tot), mmax, L.ep))
@@ -132,6 +142,8 @@ hoscf_status plan_all(hoscf_handle* h, int order, const int64_t* dims, int dtype
     L.off_ua = off;
     off = align_up(off + sizeof(float) * (size_t)L.s.n_tot, 256);
     L.off_ub = off;
+    off = align_up(off + sizeof(float) * (size_t)L.s.n_tot, 256);
+    L.off_uc = off;
     off = align_up(off + sizeof(float) * (size_t)L.s.n_tot, 256);
     L.off_x = off;
     off = align_up(off + sizeof(double) * (size_t)L.s.n_tot, 256);
@@ -161,7 +173,7 @@ hoscf_status dev_status(hoscf_handle* h, int code) {
 hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const double* x0,
                         const float* u0, double* x_out, float* u_out, double* lambda_out,
                         const hoscf_opts* o, int check, double kkt_tol, cudaStream_t st,
-                        double adapt = 0.0) {
+                        double adapt = 0.0, int rqi = 0) {
     char* eb = h->ws + L.off_eig;
     float* Jr = reinterpret_cast<float*>(eb + L.ep.off_jr);
     cudaError_t e = launch_build_jr(L.s, H, Jr, st);
@@ -187,6 +199,7 @@ hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const 
     ll.timeout_ns = timeout_of(o);
     ll.cache_floats = L.ep.cache_floats;
     ll.adapt = adapt;
+    ll.rqi = rqi;
     ll.smem = L.ep.smem;
     e = launch_lanczos(L.s, ll, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "lanczos");
@@ -259,12 +272,13 @@ hoscf_status hoscf_workspace_size(int order, const int64_t* dims, int dtype, siz
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
-    PassPlan pp;
+    PassPlan pp, p32;
     EigPlan ep;
     make_pass_plan(s, dtype, nsm, true, pp);
+    make_pass_plan(s, HOSCF_F32, nsm, true, p32);   // a refinement copy is FP32
     make_eig_plan(s, nsm, 1, 64, ep);
-    size_t t = kHeadBytes + align_up(pp.bytes, 256) + align_up(ep.bytes, 256) +
-               2 * align_up(sizeof(float) * s.P, 256) + 2 * align_up(sizeof(float) * s.n_tot, 256) +
+    size_t t = kHeadBytes + align_up(std::max(pp.bytes, p32.bytes), 256) + align_up(ep.bytes, 256) +
+               2 * align_up(sizeof(float) * s.P, 256) + 3 * align_up(sizeof(float) * s.n_tot, 256) +
                align_up(sizeof(double) * s.n_tot, 256);
     *bytes = t;
     return HOSCF_OK;
@@ -336,8 +350,9 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Layout L;
     const int mmax = std::min(std::max(o.eig_max_steps, 2), 128);
-    // plan for the larger of the two element sizes (FP32 refine dominates)
-    st = plan_all(h, T->order, T->dims, Tr ? HOSCF_F32 : T->dtype, true, true, mmax, L);
+    // the pass region must fit both the low-precision and the FP32 pass
+    st = plan_all(h, T->order, T->dims, Tr ? HOSCF_F32 : T->dtype, true, true, mmax, L,
+                  Tr ? T->dtype : -1);
     if (st) return st;
     PassPlan pp_lo = L.pp;
     if (Tr) make_pass_plan(L.s, T->dtype, h->nsm, true, pp_lo);
@@ -359,25 +374,35 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
     CK(launch_scale_modes(S, u0, norms, ua, s));
 
     const uint64_t tmo = timeout_of(&o);
-    const bool ihoscf = o.variant != HOSCF_VARIANT_HOSCF;
     int iters = 0, passes = 0, passes_ref = 0, accepts = 0;
     double sigma = 0.0, resid = INFINITY, r41 = NAN;
     bool use_ref = false;
     hoscf_status result = HOSCF_NOT_CONVERGED;
+    // three factor buffers (current point, eigen step, RQI candidate) and two
+    // block buffers, so a rejected RQI step never costs a repeated pass
     float* ucur = ua;
     float* unext = ub;
+    float* uy = reinterpret_cast<float*>(h->ws + L.off_uc);
+    float* Hcur = H;
+    float* Hoth = reinterpret_cast<float*>(h->ws + L.off_H2);
     Err err;
 
-    auto pass_and_check = [&](const float* u, float* u_eig_out, int check, double* out) -> hoscf_status {
+    auto do_pass = [&](const float* u, float* Hdst) -> hoscf_status {
         const hoscf_tensor_desc* TT = use_ref ? Tr : T;
         const PassPlan& pp = use_ref ? L.pp : (Tr ? pp_lo : L.pp);
-        hoscf_status q = run_ttvc(S, pp, TT->dtype, TT->data, TT->scales, u, H,
+        hoscf_status q = run_ttvc(S, pp, TT->dtype, TT->data, TT->scales, u, Hdst,
                                   h->ws + L.off_pass, dev_err(h), tmo, s, err);
         if (q) return fail(h, q, "%s", err.msg);
         ++passes;
         if (use_ref) ++passes_ref;
-        q = eig_launch(h, L, H, nullptr, u, nullptr, u_eig_out, nullptr, &o, check, o.tol, s,
-                       o.eig_adapt);
+        return HOSCF_OK;
+    };
+    // certificate at u (+ the eigen step or the RQI solve into u_res unless u
+    // is certified); scalars are read back synchronously
+    auto do_step = [&](const float* Hsrc, const float* u, float* u_res, int rqi, double* out,
+                       int check = 1) -> hoscf_status {
+        hoscf_status q = eig_launch(h, L, Hsrc, nullptr, u, nullptr, u_res, nullptr, &o, check,
+                                    o.tol, s, o.eig_adapt, rqi);
         if (q) return q;
         cudaError_t e = cudaMemcpyAsync(h->h_pinned, scal, sizeof(double) * SC_COUNT,
                                         cudaMemcpyDeviceToHost, s);
@@ -390,48 +415,107 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
         memcpy(&code, h->h_pinned + 32, sizeof(int));
         if (code) return dev_status(h, code);
         memcpy(out, h->h_pinned, sizeof(double) * SC_COUNT);
+        if (!std::isfinite(out[SC_SIGMA]) || std::isnan(out[SC_KKT]))
+            return fail(h, HOSCF_NONFINITE, "non-finite sigma or residual");
         return HOSCF_OK;
     };
 
-    double sc[SC_COUNT];
+    double sc[SC_COUNT], sk[SC_COUNT], sy[SC_COUNT];
+    st = do_pass(ucur, Hcur);
+    if (st) return st;
     while (true) {
-        st = pass_and_check(ucur, unext, 1, sc);
+        // certify the current point; unless certified, take the eigen step
+        st = do_step(Hcur, ucur, unext, 0, sc);
         if (st) return st;
         sigma = sc[SC_SIGMA];
         resid = sc[SC_KKT];
         r41 = sc[SC_R41];
-        if (!std::isfinite(sigma) || !std::isfinite(resid)) {
-            if (resid == INFINITY && sigma == 0.0) {
-                result = HOSCF_NOT_CONVERGED;
-                break;
-            }
-            return fail(h, HOSCF_NONFINITE, "non-finite sigma or residual");
-        }
-        if (Tr && !use_ref && resid <= o.switch_tol) {
+        if (Tr && !use_ref && (resid <= o.switch_tol || sc[SC_CONVERGED] != 0.0)) {
             // precision form: the low-precision tensor has done its part; the
-            // remaining passes (and the certificate) use the FP32 tensor
+            // remaining passes and the certificate use the FP32 tensor
             use_ref = true;
-            if (sc[SC_CONVERGED] != 0.0) continue;   // no eigen step taken: recertify here
-            if (iters >= o.max_iter) {
-                result = HOSCF_NOT_CONVERGED;
-                break;
+            if (sc[SC_CONVERGED] == 0.0 && iters < o.max_iter) {
+                ++iters;
+                std::swap(ucur, unext);
             }
-            ++iters;
-            std::swap(ucur, unext);
+            st = do_pass(ucur, Hcur);
+            if (st) return st;
             continue;
         }
-        if (sc[SC_CONVERGED] != 0.0 && (!Tr || use_ref)) {
+        if (sc[SC_CONVERGED] != 0.0) {
             result = HOSCF_OK;
             break;
         }
-        if (iters >= o.max_iter) {
-            result = HOSCF_NOT_CONVERGED;
-            break;
-        }
+        if (iters >= o.max_iter) break;
         ++iters;
-        std::swap(ucur, unext);
-        (void)ihoscf;
-        (void)accepts;
+        if (o.variant == HOSCF_VARIANT_HOSCF) {
+            std::swap(ucur, unext);
+            st = do_pass(ucur, Hcur);
+            if (st) return st;
+            continue;
+        }
+        if (o.variant == HOSCF_VARIANT_IHOSCF) {
+            // RQI with J built at the new point x_k (Sec. 4.4, reading in the design doc)
+            st = do_pass(unext, Hoth);                 // J(x_k)
+            if (st) return st;
+            st = do_step(Hoth, unext, uy, 1, sk);      // certify x_k, then solve for y
+            if (st) return st;
+            if (sk[SC_CONVERGED] != 0.0) {
+                std::swap(ucur, unext);
+                std::swap(Hcur, Hoth);
+                sigma = sk[SC_SIGMA];
+                resid = sk[SC_KKT];
+                r41 = sk[SC_R41];
+                result = HOSCF_OK;
+                break;
+            }
+            st = do_pass(uy, Hcur);                    // J(y)
+            if (st) return st;
+            st = do_step(Hcur, uy, ucur, 0, sy);       // certificate of y (eig result unused)
+            if (st) return st;
+            if (sy[SC_CONVERGED] != 0.0 || std::fabs(sy[SC_SIGMA]) >= std::fabs(sk[SC_SIGMA])) {
+                ++accepts;                             // keep y: Hcur holds J(y)
+                std::swap(ucur, uy);
+                if (sy[SC_CONVERGED] != 0.0) {
+                    sigma = sy[SC_SIGMA];
+                    resid = sy[SC_KKT];
+                    r41 = sy[SC_R41];
+                    result = HOSCF_OK;
+                    break;
+                }
+            } else {                                   // keep x_k: its blocks are in Hoth
+                std::swap(ucur, unext);
+                std::swap(Hcur, Hoth);
+            }
+            continue;
+        }
+        // HOSCF_VARIANT_IHOSCF_PREV: RQI with J_{k-1} (the matrix just used)
+        st = do_step(Hcur, unext, uy, 1, sk, 0);       // rho from J_{k-1} at x~_k
+        if (st) return st;
+        st = do_pass(uy, Hoth);
+        if (st) return st;
+        st = do_step(Hoth, uy, unext, 0, sy);
+        if (st) return st;
+        if (sy[SC_CONVERGED] != 0.0 || std::fabs(sy[SC_SIGMA]) >= std::fabs(sigma)) {
+            ++accepts;
+            std::swap(ucur, uy);
+            std::swap(Hcur, Hoth);
+            if (sy[SC_CONVERGED] != 0.0) {
+                sigma = sy[SC_SIGMA];
+                resid = sy[SC_KKT];
+                r41 = sy[SC_R41];
+                result = HOSCF_OK;
+                break;
+            }
+        } else {
+            // restore x_k with one extra pass; its eigen step was overwritten
+            // above, so recompute from J_{k-1}
+            st = do_step(Hcur, ucur, unext, 0, sc);
+            if (st) return st;
+            std::swap(ucur, unext);
+            st = do_pass(ucur, Hcur);
+            if (st) return st;
+        }
     }
     // final sign fix (Alg. 1 lines 12-15) and gauge, into u_out
     CK(cudaMemcpyAsync(u_out, ucur, sizeof(float) * S.n_tot, cudaMemcpyDeviceToDevice, s));
@@ -473,8 +557,14 @@ hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const f
 
 hoscf_status hoscf_quantize(hoscf_handle* h, const float* x, int64_t n, int dtype, void* q,
                             float* scales, void* stream) {
-    (void)x; (void)n; (void)dtype; (void)q; (void)scales; (void)stream;
-    return fail(h, HOSCF_EUNSUPPORTED, "quantize not built yet");
+    if (!h) return HOSCF_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !q))) return fail(h, HOSCF_EINVAL, "bad quantize arguments");
+    if (dtype != HOSCF_BF16 && dtype != HOSCF_F8E4M3)
+        return fail(h, HOSCF_EINVAL, "quantize dtype must be BF16 or F8E4M3");
+    if (dtype == HOSCF_F8E4M3 && n > 0 && !scales) return fail(h, HOSCF_EINVAL, "FP8 needs scales");
+    DeviceGuard g(h->device);
+    CK(launch_quantize(x, n, dtype, q, scales, reinterpret_cast<cudaStream_t>(stream)));
+    return HOSCF_OK;
 }
 
 }  // extern "C"

@@ -51,6 +51,8 @@ struct EigArgs {
     double kkt_tol;
     int64_t cache_floats;   // shared floats holding this CTA's Jr rows (0: read from L2)
     double adapt;           // > 0: inexact eigen steps (see hoscf_opts.eig_adapt)
+    int rqi;                // 1: solve (J - rho I) y = x0 in the Krylov space instead
+                            //    (rho = Rayleigh quotient of x0; iHOSCF, Sec. 4.4)
     unsigned* bar;
     int* err;
     uint64_t timeout_ns;
@@ -212,6 +214,72 @@ __device__ void tridiag_inverse_iteration(const float* al, const float* be, int 
         const float inv = 1.f / mx;
         for (int i = 0; i < k; ++i) s[i] *= inv;
     }
+}
+
+// Solution z of (T - shift I) z = e_1 for the k x k tridiagonal T (FP32,
+// partial-pivot LU as above); returns |z_k| / ||z|| and writes z / ||z|| to
+// s_out (FP64).  One thread.
+__device__ double tridiag_shifted_solve(const double* alpha, const double* beta, int k,
+                                        double shift, double* s_out, float* wa, float* wb,
+                                        float* wc, float* wd, float* z, int* piv) {
+    float bound = 0.f;
+    for (int i = 0; i < k; ++i) {
+        wa[i] = (float)(alpha[i] - shift);
+        wb[i] = (i < k - 1) ? (float)beta[i] : 0.f;
+        wc[i] = 0.f;
+        z[i] = (i == 0) ? 1.f : 0.f;
+        bound = fmaxf(bound, fabsf(wa[i]) + fabsf(wb[i]) + (i > 0 ? (float)fabs(beta[i - 1]) : 0.f));
+    }
+    const float eps = fmaxf(1.2e-7f * bound, 1e-30f);
+    for (int i = 0; i < k - 1; ++i) {
+        const float sub = (float)beta[i];
+        if (fabsf(wa[i]) >= fabsf(sub)) {
+            piv[i] = 0;
+            const float l = (wa[i] != 0.f) ? sub / wa[i] : 0.f;
+            wd[i] = l;
+            wa[i + 1] -= l * wb[i];
+        } else {
+            piv[i] = 1;
+            const float l = wa[i] / sub;
+            wd[i] = l;
+            const float a_ip1 = wa[i + 1];
+            wa[i] = sub;
+            const float t = wb[i];
+            wb[i] = a_ip1;
+            wa[i + 1] = t - l * a_ip1;
+            if (i < k - 2) {
+                wc[i] = wb[i + 1];
+                wb[i + 1] = -l * wb[i + 1];
+            }
+        }
+    }
+    for (int i = 0; i < k - 1; ++i) {
+        if (piv[i]) {
+            const float t = z[i];
+            z[i] = z[i + 1];
+            z[i + 1] = t - wd[i] * z[i];
+        } else {
+            z[i + 1] -= wd[i] * z[i];
+        }
+    }
+    for (int i = k - 1; i >= 0; --i) {
+        float v = z[i];
+        if (i + 1 < k) v -= wb[i] * z[i + 1];
+        if (i + 2 < k) v -= wc[i] * z[i + 2];
+        const float dd = fabsf(wa[i]) > eps ? wa[i] : (wa[i] < 0.f ? -eps : eps);
+        z[i] = v / dd;
+        if (fabsf(z[i]) > 1e30f)
+            for (int t = i; t < k; ++t) z[t] *= 1e-30f;
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < k; ++i) nrm += (double)z[i] * (double)z[i];
+    nrm = sqrt(nrm);
+    if (!(nrm > 0.0) || !isfinite(nrm)) {
+        for (int i = 0; i < k; ++i) s_out[i] = (i == 0) ? 1.0 : 0.0;
+        return 1.0;
+    }
+    for (int i = 0; i < k; ++i) s_out[i] = (double)z[i] / nrm;
+    return fabs((double)z[k - 1]) / nrm;
 }
 
 struct RitzOut {
@@ -564,7 +632,17 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         const bool last = (k == a.mmax) || (k == n) || !(beta_last > 1e-30);
         if (check_now(k) || last) {
             __shared__ RitzOut s_ro;
-            if (k >= 2) {
+            if (a.rqi) {
+                if (tid == 0) {
+                    float* w = rscratch;
+                    const double rel = tridiag_shifted_solve(
+                        alpha, beta, k, alpha[0], sv, w, w + kMaxLanczos, w + 2 * kMaxLanczos,
+                        w + 3 * kMaxLanczos, w + 4 * kMaxLanczos,
+                        reinterpret_cast<int*>(w + 5 * kMaxLanczos));
+                    s_ro.theta = alpha[0];
+                    s_ro.resid = beta_last * rel;   // relative Galerkin residual of the solve
+                }
+            } else if (k >= 2) {
                 if (warp == 0) {
                     RitzOut t = ritz_largest_magnitude(alpha, beta, k, beta_last, sv, rscratch);
                     if (lane == 0) s_ro = t;
@@ -576,7 +654,8 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             }
             __syncthreads();
             ro = s_ro;
-            if (ro.resid <= a.eig_tol * fabs(ro.theta) || last) done = true;
+            const double scale_t = a.rqi ? 1.0 : fabs(ro.theta);
+            if (ro.resid <= a.eig_tol * scale_t || last) done = true;
         }
         if (!done) {
             const float inv = (float)(1.0 / beta_last);
@@ -913,6 +992,7 @@ cudaError_t launch_lanczos(const Shape& s, const LanczosLaunch& l, cudaStream_t 
     a.timeout_ns = l.timeout_ns;
     a.cache_floats = l.cache_floats;
     a.adapt = l.adapt;
+    a.rqi = l.rqi;
     const size_t sm = l.smem;
     cudaError_t e = cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);

@@ -13,9 +13,13 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
                       const float* scales, const float* u, float* H, char* ws, int* dev_err,
                       uint64_t timeout_ns, cudaStream_t st, Err& err);
 
+// quant.cu
+cudaError_t launch_quantize(const float* x, int64_t n, int dtype, void* q, float* scales,
+                            cudaStream_t st);
+
 // small.cu
 cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const void* data,
-                      const float* u, float* H, char* ws, cudaStream_t st);
+                      const float* scales, const float* u, float* H, char* ws, cudaStream_t st);
 
 // eig.cu
 struct LanczosLaunch {
@@ -40,6 +44,7 @@ struct LanczosLaunch {
     int64_t cache_floats;
     size_t smem;
     double adapt;   // > 0: eig_tol = max(eig_tol, min(1e-5, adapt * r)) after the certificate
+    int rqi = 0;    // 1: Rayleigh-quotient solve instead of the eigenpair
 };
 
 enum EigScal {

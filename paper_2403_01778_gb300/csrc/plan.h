@@ -54,6 +54,7 @@ struct PassPlan {
     bool small = false;       // small-face path (see SmallPlanInfo)
     SmallPlanInfo sp;
     bool tma = false;
+    bool vec = false;         // rows allow 4-element vector loads (B % 4 == 0)
     int rows = 8;             // rows per consumer warp; FA = 8 * rows
     int FA = 64, FB = 128;
     int64_t TA = 1, TB = 1, TT = 1, items = 0, W = 0;

@@ -14,6 +14,10 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
+
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -39,6 +43,7 @@ struct SmallArgs {
     int64_t patch_floats;     // per CTA: F + X1 + X2 + pairs
     float* patch;             // G x patch_floats
     int* cover;               // G x D x 2: first digit, row count
+    const float* scales;      // FP8 only: one per 128 flat elements
 };
 
 template <typename E>
@@ -48,6 +53,12 @@ __device__ __forceinline__ float ld_elem<float>(const float* p) { return __ldcs(
 template <>
 __device__ __forceinline__ float ld_elem<bf16_t>(const bf16_t* p) {
     return __uint_as_float(static_cast<uint32_t>(__ldcs(reinterpret_cast<const unsigned short*>(p))) << 16);
+}
+template <>
+__device__ __forceinline__ float ld_elem<fp8_t>(const fp8_t* p) {
+    const __half_raw h = __nv_cvt_fp8_to_halfraw(
+        (__nv_fp8_storage_t)__ldcs(reinterpret_cast<const unsigned char*>(p)), __NV_E4M3);
+    return __half2float(*reinterpret_cast<const __half*>(&h));
 }
 
 constexpr int kSmallWarps = 8;
@@ -119,7 +130,11 @@ __global__ void __launch_bounds__(256) ttvc_small_kernel(const SmallArgs a) {
             const E* face = Tp + (size_t)o * F;
             float t[JF];
 #pragma unroll
-            for (int j = 0; j < JF; ++j) t[j] = sidx[j] >= 0 ? ld_elem<E>(face + lane + 32 * j) : 0.f;
+            for (int j = 0; j < JF; ++j) {
+                t[j] = sidx[j] >= 0 ? ld_elem<E>(face + lane + 32 * j) : 0.f;
+                if (std::is_same<E, fp8_t>::value && sidx[j] >= 0)
+                    t[j] *= __ldg(a.scales + ((o * F + lane + 32 * j) >> 7));
+            }
 #pragma unroll
             for (int j = 0; j < JF; ++j) {
                 hacc[j] = fmaf(wo, t[j], hacc[j]);
@@ -354,7 +369,7 @@ static cudaError_t launch_small_t(const Shape& s, const SmallPlanInfo& sp, const
 }
 
 cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const void* data,
-                      const float* u, float* H, char* ws, cudaStream_t st) {
+                      const float* scales, const float* u, float* H, char* ws, cudaStream_t st) {
     SmallArgs a;
     memset(&a, 0, sizeof(a));
     a.T = data;
@@ -386,8 +401,10 @@ cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const 
     a.patch_floats = sp.patch_floats;
     a.patch = reinterpret_cast<float*>(ws + sp.off_patch);
     a.cover = reinterpret_cast<int*>(ws + sp.off_cover);
-    cudaError_t e = dtype == HOSCF_F32 ? launch_small_t<float>(s, sp, a, st)
-                                       : launch_small_t<bf16_t>(s, sp, a, st);
+    a.scales = scales;
+    cudaError_t e = dtype == HOSCF_F32    ? launch_small_t<float>(s, sp, a, st)
+                    : dtype == HOSCF_BF16 ? launch_small_t<bf16_t>(s, sp, a, st)
+                                          : launch_small_t<fp8_t>(s, sp, a, st);
     if (e != cudaSuccess) return e;
     SmallReduceArgs r;
     memset(&r, 0, sizeof(r));

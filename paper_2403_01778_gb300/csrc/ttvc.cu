@@ -25,6 +25,10 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
+
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -73,7 +77,7 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
         return true;
     }
     const int es = elem_size(dtype);
-    if (dtype != HOSCF_F8E4M3 && make_small_plan(s, nsm, p.sp)) {
+    if (make_small_plan(s, nsm, p.sp)) {
         p.small = true;
         size_t off = 0;
         p.sp.off_patch = off;
@@ -83,7 +87,21 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
         p.bytes = off;
         return true;
     }
-    p.rows = 8;
+    // rows per warp: the candidate whose tiles waste the fewest rows of A
+    {
+        const int cand[3] = {8, 13, 16};
+        int best = 8;
+        double bw = 1e30;
+        for (int r : cand) {
+            const int64_t fa = 8 * r, ta = (s.A + fa - 1) / fa;
+            const double waste = (double)(ta * fa) / (double)s.A + (r == 8 ? 0.0 : 1e-3 * r);
+            if (waste < bw - 1e-9) {
+                bw = waste;
+                best = r;
+            }
+        }
+        p.rows = best;
+    }
     p.FA = 8 * p.rows;
     p.FB = 128;
     p.TA = (s.A + p.FA - 1) / p.FA;
@@ -92,6 +110,7 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
     p.items = p.TT * s.O;
     // TMA needs 16-byte row and slab pitches and coordinates below 2^31.
     p.tma = tma_ok && (s.B * es) % 16 == 0 && s.O < (int64_t(1) << 31);
+    p.vec = (s.B % 4) == 0;
     int64_t grid = std::max<int64_t>(nsm, p.TT);
     if (!p.tma) grid = std::max<int64_t>(grid, 4 * (int64_t)nsm);
     grid = std::min<int64_t>(grid, p.items);
@@ -163,6 +182,7 @@ struct TiledArgs {
     float* y2p;          // TA x O x B
     int* err;
     uint64_t timeout_ns;
+    const float* scales;   // FP8 only: one per 128 flat elements
 };
 
 // Reduce-scatter of NV per-lane row partials over the 32 lanes; returns the
@@ -188,42 +208,78 @@ __device__ __forceinline__ float rs_reduce(float (&y)[NV], int lane, int& row) {
     return y[0];
 }
 
-template <typename E>
-__device__ __forceinline__ void load4_smem(const E* row, int col, float (&v)[4]);
-
-template <>
-__device__ __forceinline__ void load4_smem<float>(const float* row, int col, float (&v)[4]) {
-    const float4 q = *reinterpret_cast<const float4*>(row + col);
+// Four consecutive elements -> float (no scaling).
+__device__ __forceinline__ void unpack4(float4 q, float (&v)[4]) {
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
-
-template <>
-__device__ __forceinline__ void load4_smem<bf16_t>(const bf16_t* row, int col, float (&v)[4]) {
-    const uint2 q = *reinterpret_cast<const uint2*>(row + col);
+__device__ __forceinline__ void unpack4(uint2 q, float (&v)[4]) {   // 4 x bf16
     v[0] = __uint_as_float(q.x << 16);
     v[1] = __uint_as_float(q.x & 0xffff0000u);
     v[2] = __uint_as_float(q.y << 16);
     v[3] = __uint_as_float(q.y & 0xffff0000u);
 }
+__device__ __forceinline__ void unpack4(uint32_t q, float (&v)[4]) {   // 4 x fp8 e4m3
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(q & 0xffffu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(q >> 16), __NV_E4M3);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+template <typename E> struct Pack4;
+template <> struct Pack4<float> { using T = float4; };
+template <> struct Pack4<bf16_t> { using T = uint2; };
+template <> struct Pack4<fp8_t> { using T = uint32_t; };
+
+template <typename E>
+__device__ __forceinline__ void load4_smem(const E* row, int col, float (&v)[4]) {
+    unpack4(*reinterpret_cast<const typename Pack4<E>::T*>(row + col), v);
+}
+
+template <typename E>
+__device__ __forceinline__ void load4_global_vec(const E* p, float (&v)[4]) {
+    unpack4(__ldcs(reinterpret_cast<const typename Pack4<E>::T*>(p)), v);
+}
 
 template <typename E>
 __device__ __forceinline__ float load1_global(const E* p);
-
 template <>
-__device__ __forceinline__ float load1_global<float>(const float* p) { return __ldg(p); }
-
+__device__ __forceinline__ float load1_global<float>(const float* p) { return __ldcs(p); }
 template <>
 __device__ __forceinline__ float load1_global<bf16_t>(const bf16_t* p) {
-    const uint16_t b = __ldg(reinterpret_cast<const unsigned short*>(p));
+    const uint16_t b = __ldcs(reinterpret_cast<const unsigned short*>(p));
     return __uint_as_float(static_cast<uint32_t>(b) << 16);
 }
+template <>
+__device__ __forceinline__ float load1_global<fp8_t>(const fp8_t* p) {
+    const uint8_t c = __ldcs(reinterpret_cast<const unsigned char*>(p));
+    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)c, __NV_E4M3);
+    return __half2float(*reinterpret_cast<const __half*>(&h));
+}
+
+// FP8 storage: multiply each of the lane's four values by the scale of its
+// 128-element group (flat row-major index f0 .. f0+3 spans at most two groups).
+__device__ __forceinline__ void apply_scales(const float* __restrict__ scales, int64_t f0,
+                                             float (&v)[4]) {
+    const int64_t g0 = f0 >> 7;
+    const float s0 = __ldg(scales + g0);
+    const float s1 = ((f0 + 3) >> 7) != g0 ? __ldg(scales + g0 + 1) : s0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] *= (((f0 + c) >> 7) == g0) ? s0 : s1;
+}
+
+// How the consumer warps get their tile rows.
+enum LoadMode : int { LOAD_TMA = 0, LOAD_VEC = 1, LOAD_SCALAR = 2 };
 
 // The streaming kernel.  Threads 0..255 are 8 consumer warps; with TMA a
 // ninth warp issues the bulk tensor copies.  Consumer warp w owns rows
 // [w*ROWS, (w+1)*ROWS) of the FA x 128 tile, lane l owns columns 4l..4l+3.
-template <typename E, bool TMA, int ROWS>
-__global__ void __launch_bounds__(TMA ? 288 : 256, 1)
+// Without TMA the consumers load their own rows (16-byte vector loads when
+// rows are aligned, else element by element).
+template <typename E, int MODE, int ROWS>
+__global__ void __launch_bounds__(MODE == LOAD_TMA ? 288 : 256, 1)
     ttvc_tiled_kernel(const __grid_constant__ CUtensorMap tmap, const TiledArgs a, int nstage) {
+    constexpr bool TMA = MODE == LOAD_TMA;
     constexpr int FA = 8 * ROWS;
     constexpr int FB = 128;
     constexpr int STAGE = FA * FB;   // elements
@@ -317,7 +373,10 @@ __global__ void __launch_bounds__(TMA ? 288 : 256, 1)
             }
         }
         const float wo = __ldg(a.w + o);
-        float y1[ROWS];
+        constexpr int RP = ROWS <= 8 ? 8 : (ROWS <= 16 ? 16 : 32);
+        float y1[RP];
+#pragma unroll
+        for (int r = ROWS; r < RP; ++r) y1[r] = 0.f;
         float y2[4] = {0.f, 0.f, 0.f, 0.f};
         const int s = TMA ? (int)(k % nstage) : 0;
         if (TMA) {
@@ -330,18 +389,28 @@ __global__ void __launch_bounds__(TMA ? 288 : 256, 1)
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
             float v[4];
+            const int64_t ar = ta * FA + warp * ROWS + r;
+            const int64_t b0 = tb * FB + 4 * lane;
             if (TMA) {
                 load4_smem<E>(stages + (size_t)s * STAGE + (size_t)(warp * ROWS + r) * FB,
                               4 * lane, v);
+            } else if (MODE == LOAD_VEC) {
+                const E* rowp = reinterpret_cast<const E*>(a.T) + ((size_t)o * a.A + ar) * a.B;
+                if (ar < a.A && b0 < a.B) {
+                    load4_global_vec<E>(rowp + b0, v);   // B % 4 == 0: all four in range
+                } else {
+                    v[0] = v[1] = v[2] = v[3] = 0.f;
+                }
             } else {
-                const int64_t ar = ta * FA + warp * ROWS + r;
                 const E* rowp = reinterpret_cast<const E*>(a.T) + ((size_t)o * a.A + ar) * a.B;
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) {
-                    const int64_t b = tb * FB + 4 * lane + cc;
+                    const int64_t b = b0 + cc;
                     v[cc] = (ar < a.A && b < a.B) ? load1_global<E>(rowp + b) : 0.f;
                 }
             }
+            if (std::is_same<E, fp8_t>::value && ar < a.A && b0 < a.B)
+                apply_scales(a.scales, ((int64_t)o * a.A + ar) * a.B + b0, v);
             float d1 = 0.f;
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
@@ -357,8 +426,8 @@ __global__ void __launch_bounds__(TMA ? 288 : 256, 1)
         }
         // row sums -> y1 partial of this b-tile
         int row;
-        const float ys = rs_reduce<ROWS>(y1, lane, row);
-        if ((lane & ((32 / ROWS) - 1)) == 0) {
+        const float ys = rs_reduce<RP>(y1, lane, row);
+        if ((lane & ((32 / RP) - 1)) == 0 && row < ROWS) {
             const int64_t ar = ta * FA + warp * ROWS + row;
             if (ar < a.A) a.y1p[((size_t)tb * a.O + o) * a.A + ar] = ys;
         }
@@ -552,16 +621,41 @@ static int grid_for(int64_t n, int threads, int cap) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
 }
 
-template <typename E, bool TMA>
-static cudaError_t launch_tiled(const PassPlan& p, const CUtensorMap& map, const TiledArgs& a,
-                                cudaStream_t st) {
-    auto kern = ttvc_tiled_kernel<E, TMA, 8>;
-    const size_t smem = TMA ? p.smem : (size_t)2 * 8 * 128 * sizeof(float);
+template <typename E, int MODE, int ROWS>
+static cudaError_t launch_tiled_k(const PassPlan& p, const CUtensorMap& map, const TiledArgs& a,
+                                  cudaStream_t st) {
+    auto kern = ttvc_tiled_kernel<E, MODE, ROWS>;
+    const size_t smem = MODE == LOAD_TMA ? p.smem : (size_t)2 * 8 * 128 * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<p.grid, TMA ? 288 : 256, smem, st>>>(map, a, p.nstage);
+    kern<<<p.grid, MODE == LOAD_TMA ? 288 : 256, smem, st>>>(map, a, p.nstage);
     return cudaGetLastError();
+}
+
+template <typename E, int MODE>
+static cudaError_t launch_tiled_rows(const PassPlan& p, const CUtensorMap& map, const TiledArgs& a,
+                                     cudaStream_t st) {
+    if (MODE == LOAD_SCALAR || p.rows == 8) return launch_tiled_k<E, MODE, 8>(p, map, a, st);
+    if (p.rows == 13) return launch_tiled_k<E, MODE, 13>(p, map, a, st);
+    return launch_tiled_k<E, MODE, 16>(p, map, a, st);
+}
+
+template <typename E>
+static cudaError_t launch_tiled(const PassPlan& p, int mode, const CUtensorMap& map,
+                                const TiledArgs& a, cudaStream_t st) {
+    if (mode == LOAD_TMA) return launch_tiled_rows<E, LOAD_TMA>(p, map, a, st);
+    if (mode == LOAD_VEC) return launch_tiled_rows<E, LOAD_VEC>(p, map, a, st);
+    return launch_tiled_rows<E, LOAD_SCALAR>(p, map, a, st);
+}
+
+__global__ void fp8_to_f32_kernel(const uint8_t* __restrict__ src, const float* __restrict__ scales,
+                                  float* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)src[i], __NV_E4M3);
+        dst[i] = __half2float(*reinterpret_cast<const __half*>(&h)) * scales[i >> 7];
+    }
 }
 
 // Runs the whole pass: blocks H (P floats, packed) from T and u.
@@ -586,20 +680,14 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
             bf16_to_f32_kernel<<<grid_for(s.N, 256, 4096), 256, 0, st>>>((const uint16_t*)data, H,
                                                                          s.N);
         } else {
-            err.code = HOSCF_EUNSUPPORTED;
-            snprintf(err.msg, sizeof(err.msg), "order-2 FP8 tensors are not supported");
-            return err.code;
+            fp8_to_f32_kernel<<<grid_for(s.N, 256, 4096), 256, 0, st>>>((const uint8_t*)data,
+                                                                        scales, H, s.N);
         }
         HOSCF_CK(cudaGetLastError());
         return HOSCF_OK;
     }
-    if (dtype != HOSCF_F32 && dtype != HOSCF_BF16) {
-        err.code = HOSCF_EUNSUPPORTED;
-        snprintf(err.msg, sizeof(err.msg), "dtype %d not supported by this pass", dtype);
-        return err.code;
-    }
     if (p.small) {
-        HOSCF_CK(run_small(s, p.sp, dtype, data, u, H, ws, st));
+        HOSCF_CK(run_small(s, p.sp, dtype, data, scales, u, H, ws, st));
         return HOSCF_OK;
     }
     const OuterInfo oi = make_outer(s);
@@ -628,6 +716,7 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
     a.y2p = reinterpret_cast<float*>(ws + p.off_y2p);
     a.err = dev_err;
     a.timeout_ns = timeout_ns;
+    a.scales = scales;
 
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
@@ -639,20 +728,24 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         cuuint64_t gstr[2] = {(cuuint64_t)(s.B * es), (cuuint64_t)(s.A * s.B * es)};
         cuuint32_t box[3] = {(cuuint32_t)p.FB, (cuuint32_t)p.FA, 1};
         cuuint32_t estr[3] = {1, 1, 1};
-        CUtensorMapDataType dt =
-            dtype == HOSCF_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        CUtensorMapDataType dt = dtype == HOSCF_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : dtype == HOSCF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                       : CU_TENSOR_MAP_DATA_TYPE_UINT8;
         if (!enc || (reinterpret_cast<uintptr_t>(data) & 15) != 0 ||
             enc(&map, dt, 3, const_cast<void*>(data), gdim, gstr, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             use_tma = false;
     }
-    if (use_tma) {
-        HOSCF_CK((dtype == HOSCF_F32 ? launch_tiled<float, true>(p, map, a, st)
-                                     : launch_tiled<bf16_t, true>(p, map, a, st)));
+    const int mode = use_tma ? LOAD_TMA
+                     : (p.vec && (reinterpret_cast<uintptr_t>(data) & 15) == 0) ? LOAD_VEC
+                                                                                : LOAD_SCALAR;
+    if (dtype == HOSCF_F32) {
+        HOSCF_CK(launch_tiled<float>(p, mode, map, a, st));
+    } else if (dtype == HOSCF_BF16) {
+        HOSCF_CK(launch_tiled<bf16_t>(p, mode, map, a, st));
     } else {
-        HOSCF_CK((dtype == HOSCF_F32 ? launch_tiled<float, false>(p, map, a, st)
-                                     : launch_tiled<bf16_t, false>(p, map, a, st)));
+        HOSCF_CK(launch_tiled<fp8_t>(p, mode, map, a, st));
     }
     // face block (d-2, d-1)
     float* Hface = H + s.boff[block_index(s.d, s.d - 2, s.d - 1)];

@@ -65,6 +65,8 @@ SHAPES = [
     (2, 3, 2, 3, 2, 3, 2, 3),  # d = 8
     (4, 5, 3, 7, 2, 9, 2),   # d = 7, ragged
     (33, 1, 17, 32),         # a unit mode among outer ones
+    (3, 200, 200),           # 13 rows per warp (tiles of 104 rows)
+    (4, 96, 36),             # vector loads without TMA (36 floats = 144 B rows)
 ]
 
 
@@ -186,6 +188,25 @@ def test_solve_planted_matches_oracle(dims, seed):
     r = P().hoscf_solve(T.cuda(), torch.cat(u0).cuda(), tol=1e-6, max_iter=300)
     assert r.converged
     compare_solution(r, ref)
+
+
+@pytest.mark.parametrize("variant", ["ihoscf", "ihoscf_prev"])
+@pytest.mark.parametrize("name", ["EXP", "ARCSIN"])
+def test_ihoscf_matches_oracle_on_example2(name, variant):
+    """Both iHOSCF readings reach the oracle's (and plain HOSCF's) solution on
+    the paper's Example 2 tensors; the default reading needs fewer eigen steps
+    than HOSCF (Table 3's direction)."""
+    T = W.example2(name)
+    u0 = W.uniform01_vectors(T.shape, 3)
+    ref = oracle.hoscf(T.numpy(), [v.numpy() for v in u0], tol=1e-8, max_iter=500,
+                       variant=variant)
+    r = P().hoscf_solve(T.cuda(), torch.cat(u0).cuda(), tol=1e-6, max_iter=500, variant=variant)
+    h = P().hoscf_solve(T.cuda(), torch.cat(u0).cuda(), tol=1e-6, max_iter=500)
+    assert r.converged and h.converged
+    compare_solution(r, ref)
+    if variant == "ihoscf":
+        assert r.iters < h.iters
+        assert r.passes <= 2 * r.iters + 1
 
 
 def test_solve_reports_kkt_consistent_with_oracle():
