@@ -7,4 +7,6 @@ functions works everywhere, calling them needs the built library and a GPU.
 """
 from .api import (HoscfError, SolveResult, balanced, handle, hoscf_backward, hoscf_eig_step,  # noqa: F401
                   hoscf_opts_default, hoscf_quantize, hoscf_solve, hoscf_solve_batched,
-                  hoscf_ttvc_blocks, hoscf_workspace_size, n_blocks, n_tot)
+                  hoscf_ttvc_blocks, hoscf_ttvc_blocks_static, hoscf_workspace_size, n_blocks,
+                  n_tot)
+from .autograd import HOSCFFunction, hoscf  # noqa: F401

@@ -70,7 +70,7 @@ struct Layout {
     PassPlan pp;
     EigPlan ep;
     size_t off_pass = 0, off_eig = 0, off_H = 0, off_H2 = 0, off_ua = 0, off_ub = 0, off_uc = 0,
-           off_x = 0;
+           off_x = 0, off_x2 = 0, off_extra = 0;
     size_t total = 0;
 };
 
@@ -115,7 +115,7 @@ hoscf_status check_desc(hoscf_handle* h, const hoscf_tensor_desc* T) {
 // pass must fit in the same pass region (precision form: low-precision tensor
 // plus its FP32 refinement copy).
 hoscf_status plan_all(hoscf_handle* h, int order, const int64_t* dims, int dtype, bool pass,
-                      bool eig, int mmax, Layout& L, int dtype2 = -1) {
+                      bool eig, int mmax, Layout& L, int dtype2 = -1, size_t extra = 0) {
     if (!make_shape(order, dims, L.s)) return fail(h, HOSCF_EINVAL, "invalid shape");
     size_t off = kHeadBytes;
     if (pass) {
@@ -147,6 +147,10 @@ hoscf_status plan_all(hoscf_handle* h, int order, const int64_t* dims, int dtype
     off = align_up(off + sizeof(float) * (size_t)L.s.n_tot, 256);
     L.off_x = off;
     off = align_up(off + sizeof(double) * (size_t)L.s.n_tot, 256);
+    L.off_x2 = off;
+    off = align_up(off + sizeof(double) * (size_t)L.s.n_tot, 256);
+    L.off_extra = off;
+    off = align_up(off + extra, 256);
     L.total = off;
     return ensure_ws(h, L.total);
 }
@@ -173,7 +177,9 @@ hoscf_status dev_status(hoscf_handle* h, int code) {
 hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const double* x0,
                         const float* u0, double* x_out, float* u_out, double* lambda_out,
                         const hoscf_opts* o, int check, double kkt_tol, cudaStream_t st,
-                        double adapt = 0.0, int rqi = 0) {
+                        double adapt = 0.0, int rqi = 0, float shift_add = 0.f,
+                        const float* proj_u = nullptr, float scale_override = 0.f,
+                        double tol_override = 0.0) {
     char* eb = h->ws + L.off_eig;
     float* Jr = reinterpret_cast<float*>(eb + L.ep.off_jr);
     cudaError_t e = launch_build_jr(L.s, H, Jr, st);
@@ -200,6 +206,10 @@ hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const 
     ll.cache_floats = L.ep.cache_floats;
     ll.adapt = adapt;
     ll.rqi = rqi;
+    ll.shift_add = shift_add;
+    ll.proj_u = proj_u;
+    ll.scale_override = scale_override;
+    if (tol_override > 0.0) ll.eig_tol = tol_override;
     ll.smem = L.ep.smem;
     e = launch_lanczos(L.s, ll, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "lanczos");
@@ -279,7 +289,7 @@ hoscf_status hoscf_workspace_size(int order, const int64_t* dims, int dtype, siz
     make_eig_plan(s, nsm, 1, 64, ep);
     size_t t = kHeadBytes + align_up(std::max(pp.bytes, p32.bytes), 256) + align_up(ep.bytes, 256) +
                2 * align_up(sizeof(float) * s.P, 256) + 3 * align_up(sizeof(float) * s.n_tot, 256) +
-               align_up(sizeof(double) * s.n_tot, 256);
+               2 * align_up(sizeof(double) * s.n_tot, 256);
     *bytes = t;
     return HOSCF_OK;
 }
@@ -551,8 +561,74 @@ hoscf_status hoscf_solve_batched(hoscf_handle* h, int count, const hoscf_tensor_
 hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u,
                             double sigma, double grad_sigma, const float* grad_u, float* grad_T,
                             void* stream) {
-    (void)T; (void)u; (void)sigma; (void)grad_sigma; (void)grad_u; (void)grad_T; (void)stream;
-    return fail(h, HOSCF_EUNSUPPORTED, "backward not built yet");
+    if (!h) return HOSCF_EINVAL;
+    hoscf_status st = check_desc(h, T);
+    if (st) return st;
+    if (T->dtype != HOSCF_F32) return fail(h, HOSCF_EINVAL, "backward needs an FP32 tensor");
+    if (!u || !grad_T) return fail(h, HOSCF_EINVAL, "NULL pointer argument");
+    if (!std::isfinite(sigma) || !std::isfinite(grad_sigma))
+        return fail(h, HOSCF_NONFINITE, "non-finite sigma or grad_sigma");
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Layout L;
+    {
+        Shape s0;
+        if (!make_shape(T->order, T->dims, s0)) return fail(h, HOSCF_EINVAL, "invalid shape");
+        // extra region: the write's per-outer-index coefficients (2 O floats)
+        st = plan_all(h, T->order, T->dims, HOSCF_F32, true, true, 128, L, -1,
+                      sizeof(float) * 2 * (size_t)s0.O);
+    }
+    if (st) return st;
+    const Shape& S = L.s;
+    st = reset_dev_state(h, s);
+    if (st) return st;
+    float* H = reinterpret_cast<float*>(h->ws + L.off_H);
+    double* b = reinterpret_cast<double*>(h->ws + L.off_x);
+    double* av = reinterpret_cast<double*>(h->ws + L.off_x2);
+    double* bn2 = reinterpret_cast<double*>(h->ws + kOffNorms);
+    double* scal = reinterpret_cast<double*>(h->ws + kOffScal);
+    Err err;
+    const double* aptr = nullptr;
+    hoscf_status result = HOSCF_OK;
+    if (grad_u) {
+        // adjoint: P (H - sigma I) P a = P w on the factors' tangent space
+        CK(launch_tangent_project(S, u, grad_u, b, bn2, s));
+        CK(cudaMemcpyAsync(h->h_pinned, bn2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double bnorm2 = h->h_pinned[0];
+        if (!std::isfinite(bnorm2)) return fail(h, HOSCF_NONFINITE, "non-finite grad_u");
+        if (bnorm2 > 0.0) {
+            st = run_ttvc(S, L.pp, HOSCF_F32, T->data, nullptr, u, H, h->ws + L.off_pass,
+                          dev_err(h), 2000000000ull, s, err);
+            if (st) return fail(h, st, "%s", err.msg);
+            hoscf_opts o;
+            hoscf_opts_default(&o);
+            o.eig_max_steps = 128;
+            st = eig_launch(h, L, H, b, nullptr, av, nullptr, nullptr, &o, 0, 0.0, s, 0.0, 2,
+                            (float)(-sigma), u, 1.0f, 1e-6);
+            if (st) return st;
+            CK(cudaMemcpyAsync(h->h_pinned, scal, sizeof(double) * SC_COUNT,
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(h->h_pinned + 32, h->ws + kOffErr, sizeof(int),
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            int code;
+            memcpy(&code, h->h_pinned + 32, sizeof(int));
+            if (code) return dev_status(h, code);
+            if (!std::isfinite(h->h_pinned[SC_RITZRES]))
+                return fail(h, HOSCF_NONFINITE, "adjoint system singular to working precision");
+            if (h->h_pinned[SC_CONVERGED] == 0.0) {
+                result = HOSCF_NOT_CONVERGED;
+                fail(h, HOSCF_NOT_CONVERGED, "adjoint solve stopped at relative residual %.3e",
+                     h->h_pinned[SC_RITZRES]);
+            }
+            aptr = av;
+        }
+    }
+    float* coef = reinterpret_cast<float*>(h->ws + L.off_extra);
+    CK(launch_grad_write(S, u, aptr, grad_sigma, coef, grad_T, s));
+    CK(cudaStreamSynchronize(s));
+    return result;
 }
 
 hoscf_status hoscf_quantize(hoscf_handle* h, const float* x, int64_t n, int dtype, void* q,

@@ -53,6 +53,11 @@ struct EigArgs {
     double adapt;           // > 0: inexact eigen steps (see hoscf_opts.eig_adapt)
     int rqi;                // 1: solve (J - rho I) y = x0 in the Krylov space instead
                             //    (rho = Rayleigh quotient of x0; iHOSCF, Sec. 4.4)
+                            // 2: solve A y = x0 (adjoint; A = operator below), y returned
+                            //    unnormalised in x_out
+    float shift_add;        // operator: y = scale * Jr v + shift_add * v
+    const float* proj_u;    // non-NULL: operator projected blockwise orthogonal to these unit
+                            //    vectors (the tangent space of the factors)
     unsigned* bar;
     int* err;
     uint64_t timeout_ns;
@@ -101,7 +106,7 @@ __device__ void matvec_rows(const EigArgs& a, const float* __restrict__ vf, int 
             }
         }
         f = warp_sum(f);
-        if (lane == 0) yrow[q - r0] = f * a.scale;
+        if (lane == 0) yrow[q - r0] = f * a.scale + a.shift_add * vf[q];
         if (sq) {
             s2 = warp_sum(s2);
             sqacc += s2;
@@ -221,7 +226,8 @@ __device__ void tridiag_inverse_iteration(const float* al, const float* be, int 
 // s_out (FP64).  One thread.
 __device__ double tridiag_shifted_solve(const double* alpha, const double* beta, int k,
                                         double shift, double* s_out, float* wa, float* wb,
-                                        float* wc, float* wd, float* z, int* piv) {
+                                        float* wc, float* wd, float* z, int* piv,
+                                        double* znorm) {
     float bound = 0.f;
     for (int i = 0; i < k; ++i) {
         wa[i] = (float)(alpha[i] - shift);
@@ -276,8 +282,10 @@ __device__ double tridiag_shifted_solve(const double* alpha, const double* beta,
     nrm = sqrt(nrm);
     if (!(nrm > 0.0) || !isfinite(nrm)) {
         for (int i = 0; i < k; ++i) s_out[i] = (i == 0) ? 1.0 : 0.0;
+        *znorm = NAN;
         return 1.0;
     }
+    *znorm = nrm;
     for (int i = 0; i < k; ++i) s_out[i] = (double)z[i] / nrm;
     return fabs((double)z[k - 1]) / nrm;
 }
@@ -423,8 +431,8 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     double* sv = beta + kMaxLanczos;                                      // kMaxLanczos
     double* xrow = sv + kMaxLanczos;                                      // R (Ritz vector rows)
     int64_t* crow = reinterpret_cast<int64_t*>(xrow + R);                 // R + 2
-    float* hsum = reinterpret_cast<float*>(crow + R + 2);                 // kMaxLanczos + 8
-    float* Vl = hsum + kMaxLanczos + 8;                                   // M1 x R
+    float* hsum = reinterpret_cast<float*>(crow + R + 2);                 // kMaxLanczos + 16
+    float* Vl = hsum + kMaxLanczos + 16;                                  // M1 x R
     float* Yl = Vl + (size_t)M1 * R;                                      // R
     float* vf = Yl + ((R + 3) & ~3);                                      // n (padded)
     float* rscratch = vf + ((n + 3) & ~3);                                // 9 * kMaxLanczos
@@ -443,6 +451,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     }
     __syncthreads();
     float* cache = (hd[15] != 0.0) ? jcache : nullptr;
+    __shared__ double s_znorm;   // |z| of the last tridiagonal solve (solve modes)
 
     const int ps = a.pstride;
     int phase = 0;
@@ -480,6 +489,24 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         if (j == 0) {
             // FP64 certificate of the start point x0 (unnormalised):
             // rho = x.y / x.x, ||y - rho x||^2, ||Jr||_F^2 -> one reduction
+            if (a.proj_u) {
+                // project y = A v0 onto the tangent space: y_n -= (u_n . y_n) u_n
+                __shared__ double mu_s[kMaxOrder];
+                for (int m = warp; m < a.d; m += kEigWarps) {
+                    const int lo = max(r0, (int)a.moff[m]), hi = min(r1, (int)a.moff[m + 1]);
+                    double t = 0.0;
+                    for (int q = lo + lane; q < hi; q += 32) t += (double)a.proj_u[q] * (double)Yl[q - r0];
+                    t = warp_sum_d(t);
+                    if (lane == 0) pdd[(size_t)24 * G + (size_t)c * kMaxOrder + m] = t;
+                }
+                if (!eig_sync(a, G)) return;
+                reduce_partials<double>(pdd + (size_t)24 * G, kMaxOrder, G, a.d, mu_s);
+                for (int q = tid; q < nr; q += kEigThreads) {
+                    const int m = mode_of(a, q + r0);
+                    Yl[q] = (float)((double)Yl[q] - mu_s[m] * (double)a.proj_u[q + r0]);
+                }
+                __syncthreads();
+            }
             double sxy = 0.0, sxx = 0.0, syy = 0.0;
             for (int q = tid; q < nr; q += kEigThreads) {
                 const double x = Vl[q], y = Yl[q];
@@ -568,14 +595,21 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             beta_last = b0;
             k = 1;
         } else {
-            // partial dots over my rows: h_i = V[i].y (i <= j), yy
-            const int cnt = j + 2;
+            // partial dots over my rows: h_i = V[i].y (i <= j), yy, and with a
+            // projection mu_n = u_n . y_n (the basis already lies in the tangent
+            // space, so h_i is unchanged by projecting y)
+            const int nproj = a.proj_u ? a.d : 0;
+            const int cnt = j + 2 + nproj;
             for (int i = warp; i < cnt; i += kEigWarps) {
                 float s = 0.f;
                 if (i <= j) {
                     for (int q = lane; q < nr; q += 32) s = fmaf(Vl[(size_t)i * R + q], Yl[q], s);
-                } else {
+                } else if (i == j + 1) {
                     for (int q = lane; q < nr; q += 32) s = fmaf(Yl[q], Yl[q], s);
+                } else {
+                    const int m = i - j - 2;
+                    const int lo = max(r0, (int)a.moff[m]), hi = min(r1, (int)a.moff[m + 1]);
+                    for (int q = lo + lane; q < hi; q += 32) s = fmaf(a.proj_u[q], Yl[q - r0], s);
                 }
                 s = warp_sum(s);
                 if (lane == 0) pbuf()[(size_t)c * ps + i] = s;
@@ -583,6 +617,16 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             if (!eig_sync(a, G)) return;
             reduce_partials<float>(pbuf(), ps, G, cnt, hsum);
             ++phase;
+            if (nproj) {
+                float mu2 = 0.f;
+                for (int m = 0; m < a.d; ++m) mu2 = fmaf(hsum[j + 2 + m], hsum[j + 2 + m], mu2);
+                for (int q = tid; q < nr; q += kEigThreads) {
+                    const int m = mode_of(a, q + r0);
+                    Yl[q] = fmaf(-hsum[j + 2 + m], a.proj_u[q + r0], Yl[q]);
+                }
+                if (tid == 0) hsum[j + 1] -= mu2;
+                __syncthreads();
+            }
             // full classical Gram-Schmidt against V[0..j]
             float ssq = 0.f;
             for (int i = 0; i <= j; ++i) ssq = fmaf(hsum[i], hsum[i], ssq);
@@ -636,9 +680,9 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 if (tid == 0) {
                     float* w = rscratch;
                     const double rel = tridiag_shifted_solve(
-                        alpha, beta, k, alpha[0], sv, w, w + kMaxLanczos, w + 2 * kMaxLanczos,
-                        w + 3 * kMaxLanczos, w + 4 * kMaxLanczos,
-                        reinterpret_cast<int*>(w + 5 * kMaxLanczos));
+                        alpha, beta, k, a.rqi == 1 ? alpha[0] : 0.0, sv, w, w + kMaxLanczos,
+                        w + 2 * kMaxLanczos, w + 3 * kMaxLanczos, w + 4 * kMaxLanczos,
+                        reinterpret_cast<int*>(w + 5 * kMaxLanczos), &s_znorm);
                     s_ro.theta = alpha[0];
                     s_ro.resid = beta_last * rel;   // relative Galerkin residual of the solve
                 }
@@ -671,6 +715,22 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     // ---- Ritz vector x = V[0..k-1] s for my rows (FP64 accumulation); block
     // norms and the sign reference <x, v0>
     const int d = a.d;
+    if (a.rqi == 2) {
+        // linear solve: y = |b| |z| V (z / |z|), returned as is
+        const double sc = sqrt(hd[2]) * s_znorm;
+        for (int q = tid; q < nr; q += kEigThreads) {
+            double x = 0.0;
+            for (int i = 0; i < k; ++i) x += sv[i] * (double)Vl[(size_t)i * R + q];
+            if (a.x_out) a.x_out[r0 + q] = x * sc;
+        }
+        if (c == 0 && tid == 0) {
+            a.scal[SC_LAMBDA] = ro.theta;
+            a.scal[SC_STEPS] = (double)k;
+            a.scal[SC_RITZRES] = ro.resid;
+            a.scal[SC_CONVERGED] = (ro.resid <= a.eig_tol && isfinite(sc)) ? 1.0 : 0.0;
+        }
+        return;
+    }
     for (int q = tid; q < nr; q += kEigThreads) {
         double x = 0.0;
         for (int i = 0; i < k; ++i) x += sv[i] * (double)Vl[(size_t)i * R + q];
@@ -854,7 +914,7 @@ __global__ void final_fix_kernel(float* __restrict__ u, int d, ModeInfoArr mi, d
 static size_t lanczos_smem_base(int64_t n, int R, int mmax) {
     return sizeof(double) * (size_t)(16 + 3 * kMaxLanczos) + sizeof(double) * (size_t)R +
            sizeof(int64_t) * (size_t)(R + 2) +
-           sizeof(float) * (size_t)(kMaxLanczos + 8) + sizeof(float) * (size_t)(mmax + 1) * R +
+           sizeof(float) * (size_t)(kMaxLanczos + 16) + sizeof(float) * (size_t)(mmax + 1) * R +
            sizeof(float) * (size_t)((R + 3) & ~3) + sizeof(float) * (size_t)((n + 3) & ~3) +
            sizeof(float) * 9 * kMaxLanczos + 256;
 }
@@ -930,8 +990,8 @@ bool make_eig_plan(const Shape& s, int nsm, int blocks_per_sm, int mmax, EigPlan
     e.off_jr = take(sizeof(float) * 2 * (size_t)s.P);
     e.off_V = take(sizeof(double) * (size_t)(mmax + 1) * s.n_tot);
     e.off_Y = take(sizeof(double) * (size_t)s.n_tot);
-    e.off_part = take(sizeof(double) * 2 * (size_t)e.G * (mmax + 8) +
-                      sizeof(double) * 2 * (size_t)e.G * (kMaxOrder + 1));
+    e.off_part = take(sizeof(double) * 2 * (size_t)e.G * (mmax + 8 + kMaxOrder) +
+                      sizeof(double) * 40 * (size_t)e.G);
     e.bytes = off;
     return true;
 }
@@ -978,7 +1038,7 @@ cudaError_t launch_lanczos(const Shape& s, const LanczosLaunch& l, cudaStream_t 
     a.V = l.V;
     a.Y = l.Y;
     a.part = l.part;
-    a.pstride = l.mmax + 8;
+    a.pstride = l.mmax + 8 + kMaxOrder;
     a.scal = l.scal;
     a.x_out = l.x_out;
     a.u_out = l.u_out;
@@ -993,6 +1053,9 @@ cudaError_t launch_lanczos(const Shape& s, const LanczosLaunch& l, cudaStream_t 
     a.cache_floats = l.cache_floats;
     a.adapt = l.adapt;
     a.rqi = l.rqi;
+    a.shift_add = l.shift_add;
+    a.proj_u = l.proj_u;
+    if (l.scale_override != 0.f) a.scale = l.scale_override;
     const size_t sm = l.smem;
     cudaError_t e = cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);

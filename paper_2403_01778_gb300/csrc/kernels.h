@@ -13,6 +13,12 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
                       const float* scales, const float* u, float* H, char* ws, int* dev_err,
                       uint64_t timeout_ns, cudaStream_t st, Err& err);
 
+// backward.cu
+cudaError_t launch_tangent_project(const Shape& s, const float* u, const float* w, double* b,
+                                   double* bnorm2, cudaStream_t st);
+cudaError_t launch_grad_write(const Shape& s, const float* u, const double* a, double c,
+                              float* coef, float* out, cudaStream_t st);
+
 // quant.cu
 cudaError_t launch_quantize(const float* x, int64_t n, int dtype, void* q, float* scales,
                             cudaStream_t st);
@@ -44,7 +50,10 @@ struct LanczosLaunch {
     int64_t cache_floats;
     size_t smem;
     double adapt;   // > 0: eig_tol = max(eig_tol, min(1e-5, adapt * r)) after the certificate
-    int rqi = 0;    // 1: Rayleigh-quotient solve instead of the eigenpair
+    int rqi = 0;    // 1: Rayleigh-quotient solve instead of the eigenpair; 2: plain solve
+    float shift_add = 0.f;        // operator: scale * Jr v + shift_add * v
+    const float* proj_u = nullptr;   // project the operator onto the factors' tangent space
+    float scale_override = 0.f;   // non-zero: mat-vec scale instead of 1/(d-1)
 };
 
 enum EigScal {
