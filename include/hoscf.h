@@ -82,6 +82,8 @@ typedef struct {
     const hoscf_tensor_desc* refine; /* precision form: FP32 copy of the same tensor, or NULL */
     double switch_tol;         /* precision form: residual at which passes move to `refine` */
     int64_t timeout_ns;        /* bound on every device-side wait (0 = 2 s) */
+    int batch_threads;         /* hoscf_solve_batched: threads per CTA (256, 512 or 1024;
+                                  0 = 512); chosen by the package's autotuner */
 } hoscf_opts;
 
 typedef struct {
@@ -175,7 +177,11 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
  *   u0       host array of `count` device pointers (n_tot floats each).
  *   u_out    host array of `count` device pointers (n_tot floats each).
  *   sigma_out host, count doubles.  infos host, count entries, or NULL.
- * Synchronous.  Returns the worst per-tensor status.
+ * Each tensor is solved by one CTA of a single persistent kernel (largest
+ * tensors first from an atomic work queue); the launch is captured in a CUDA
+ * graph on the handle's own stream and replayed for a repeated batch.
+ * Synchronous (the caller's stream is synchronised first).  Returns the
+ * worst per-tensor status.
  */
 hoscf_status hoscf_solve_batched(hoscf_handle* h, int count, const hoscf_tensor_desc* T,
                                  const float* const* u0, const hoscf_opts* opts,

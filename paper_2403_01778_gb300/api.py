@@ -275,8 +275,9 @@ def hoscf_backward(T: torch.Tensor, u: torch.Tensor, sigma: float, grad_sigma: f
 
 
 def hoscf_solve_batched(tensors, u0s, tol=1e-6, max_iter=200, eig_tol=None, timeout_ns=None,
-                        stream=None):
-    """Many small independent F32 tensors in one persistent launch."""
+                        batch_threads=None, stream=None):
+    """Many small independent F32 tensors (orders 3-4) in one persistent,
+    graph-captured launch.  Returns (sigmas, factor tensors, infos, status)."""
     cnt = len(tensors)
     descs = [_Desc(T) for T in tensors]
     arr = (TensorDesc * cnt)(*[dd.desc for dd in descs])
@@ -287,6 +288,8 @@ def hoscf_solve_batched(tensors, u0s, tol=1e-6, max_iter=200, eig_tol=None, time
     sig = (ctypes.c_double * cnt)()
     infos = (Info * cnt)()
     o = _opts(tol, max_iter, None, eig_tol, None, None, None, timeout_ns)
+    if batch_threads is not None:
+        o.batch_threads = int(batch_threads)
     dev = tensors[0].device.index
     h = handle(dev)
     st = _lib.load().hoscf_solve_batched(h, cnt, arr, pin, ctypes.byref(o), pout, sig, infos,

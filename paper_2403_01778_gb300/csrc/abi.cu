@@ -21,6 +21,9 @@ struct hoscf_handle {
     char* ws = nullptr;
     size_t ws_bytes = 0;
     double* h_pinned = nullptr;   // small pinned readback buffer
+    void* pinned_big = nullptr;   // descriptor / result staging of the batched solve
+    size_t pinned_big_bytes = 0;
+    cudaStream_t own = nullptr;   // private stream (graph capture)
     char msg[512] = {0};
 };
 
@@ -252,6 +255,8 @@ hoscf_status hoscf_destroy(hoscf_handle* h) {
         DeviceGuard g(h->device);
         if (h->ws) cudaFree(h->ws);
         if (h->h_pinned) cudaFreeHost(h->h_pinned);
+        if (h->pinned_big) cudaFreeHost(h->pinned_big);
+        if (h->own) cudaStreamDestroy(h->own);
     }
     delete h;
     return HOSCF_OK;
@@ -271,6 +276,7 @@ hoscf_status hoscf_opts_default(hoscf_opts* o) {
     o->refine = nullptr;
     o->switch_tol = 1e-3;
     o->timeout_ns = 0;
+    o->batch_threads = 0;
     return HOSCF_OK;
 }
 
@@ -553,9 +559,38 @@ hoscf_status hoscf_solve_batched(hoscf_handle* h, int count, const hoscf_tensor_
                                  const float* const* u0, const hoscf_opts* opts,
                                  float* const* u_out, double* sigma_out, hoscf_info* infos,
                                  void* stream) {
-    (void)count; (void)T; (void)u0; (void)opts; (void)u_out; (void)sigma_out; (void)infos;
-    (void)stream;
-    return fail(h, HOSCF_EUNSUPPORTED, "batched solve not built yet");
+    if (!h) return HOSCF_EINVAL;
+    if (count < 0 || (count > 0 && (!T || !u0 || !u_out || !sigma_out)))
+        return fail(h, HOSCF_EINVAL, "bad batch arguments");
+    if (count == 0) return HOSCF_OK;
+    hoscf_opts o;
+    hoscf_opts_default(&o);
+    if (opts) o = *opts;
+    const int threads = o.batch_threads == 0 ? 512 : o.batch_threads;
+    if (threads != 256 && threads != 512 && threads != 1024)
+        return fail(h, HOSCF_EINVAL, "batch_threads must be 256, 512 or 1024");
+    DeviceGuard g(h->device);
+    // descriptors + results: ~100 bytes per tensor, staged through pinned memory
+    const size_t need = 4096 + (size_t)count * 128;
+    hoscf_status st = ensure_ws(h, need);
+    if (st) return st;
+    if (h->pinned_big_bytes < need) {
+        if (h->pinned_big) cudaFreeHost(h->pinned_big);
+        h->pinned_big = nullptr;
+        h->pinned_big_bytes = 0;
+        if (cudaMallocHost(&h->pinned_big, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, HOSCF_ENOMEM, "pinned staging of %zu bytes failed", need);
+        }
+        h->pinned_big_bytes = need;
+    }
+    if (!h->own) CK(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
+    CK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    Err err;
+    st = run_batched(count, T, u0, u_out, o, threads, h->ws, h->ws_bytes, h->nsm, h->own,
+                     sigma_out, infos, h->pinned_big, h->pinned_big_bytes, err);
+    if (st) return fail(h, st, "%s", err.msg);
+    return HOSCF_OK;
 }
 
 hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u,

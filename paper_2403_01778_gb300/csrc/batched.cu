@@ -1,0 +1,632 @@
+// Batched form (no paper counterpart): many small independent tensors of
+// orders 3 and 4, each solved by Algorithm 1 (HOSCF) inside one CTA of a
+// single persistent launch.
+//
+// CTAs take tensors from an atomic work queue (the host orders the queue
+// largest-first).  Per tensor and iteration, the CTA
+//   1. builds every coupling block (eq. 3.3) in shared memory: faces
+//      T[o][:][:] are staged one outer index o at a time and folded into the
+//      face block, the row / column sums and their outer contractions; each
+//      block entry is owned by one thread, so the sums are deterministic;
+//   2. certifies the point (sigma = x^T J x, KKT residual, eq. 2.4) and, if
+//      not converged, takes the largest-magnitude eigen step (Alg. 1 line 5)
+//      by single-CTA Lanczos (FP32 vectors, FP64 scalars, full
+//      reorthogonalisation), then normalises the blocks (lines 6-9);
+// and at the end applies the sign fix of lines 12-15 and the gauge.
+// Every wait is a __syncthreads of the CTA; the queue needs no spin waits.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "plan.h"
+#include "ritz.cuh"
+
+namespace hoscf {
+
+constexpr int kBatchMaxOrder = 4;
+constexpr int kBatchLanczos = 32;
+
+struct BatchItem {
+    const float* T;
+    const float* u0;
+    float* u_out;
+    int d;
+    int dims[kBatchMaxOrder];
+};
+
+struct BatchOut {
+    double sigma;
+    double resid;
+    int iters;
+    int passes;
+    int status;   // 0 ok, 4 not converged, 5 non-finite
+    int pad;
+};
+
+struct BatchArgs {
+    const BatchItem* items;
+    const int* order;      // queue order (largest first)
+    BatchOut* out;
+    int count;
+    int* counter;          // work-queue head, zeroed before launch
+    double tol;
+    int max_iter;
+    double eig_tol;
+    double eig_adapt;
+    int mmax;
+    int n_max, P_max, F_max, AB_max;
+};
+
+struct BShape {
+    int d, n, P;
+    int dims[kBatchMaxOrder];
+    int moff[kBatchMaxOrder + 1];
+    int boff[6];   // packed blocks (m<n lexicographic), up to d = 4
+};
+
+__device__ __forceinline__ int bidx(int d, int m, int n) { return m * d - m * (m + 1) / 2 + (n - m - 1); }
+
+__device__ __forceinline__ int bmode(const BShape& s, int q) {
+    int m = 0;
+    while (m < s.d - 1 && q >= s.moff[m + 1]) ++m;
+    return m;
+}
+
+// CTA-wide sum (float), result returned to every thread.  red has >= 32 slots.
+__device__ __forceinline__ float cta_sum(float v, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    return t;
+}
+
+__device__ __forceinline__ double cta_sum_d(double v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    return t;
+}
+
+// All blocks of one tensor into H (shared memory), one pass over T.
+__device__ void batch_blocks(const BShape& s, const float* __restrict__ T, const float* u, float* H,
+                             float* face, float* y1, float* y2, float* red) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int d = s.d;
+    const int A = s.dims[d - 2], B = s.dims[d - 1], F = A * B;
+    const int O = (d == 3) ? s.dims[0] : s.dims[0] * s.dims[1];
+    const float* uA = u + s.moff[d - 2];
+    const float* uB = u + s.moff[d - 1];
+    for (int i = tid; i < s.P; i += nt) H[i] = 0.f;
+    float* Hf = H + s.boff[bidx(d, d - 2, d - 1)];
+    __syncthreads();
+    for (int o = 0; o < O; ++o) {
+        const float* src = T + (size_t)o * F;
+        for (int f = tid; f < F; f += nt) face[f] = __ldcs(src + f);
+        __syncthreads();
+        int i0, i1 = 0;
+        float w;
+        if (d == 3) {
+            i0 = o;
+            w = u[i0];
+        } else {
+            i0 = o / s.dims[1];
+            i1 = o - i0 * s.dims[1];
+            w = u[i0] * u[s.moff[1] + i1];
+        }
+        for (int f = tid; f < F; f += nt) Hf[f] = fmaf(w, face[f], Hf[f]);
+        for (int a = tid; a < A; a += nt) {
+            float t = 0.f;
+            for (int b = 0; b < B; ++b) t = fmaf(face[a * B + b], uB[b], t);
+            y1[a] = t;
+        }
+        for (int b = tid; b < B; b += nt) {
+            float t = 0.f;
+            for (int a = 0; a < A; ++a) t = fmaf(face[a * B + b], uA[a], t);
+            y2[b] = t;
+        }
+        __syncthreads();
+        if (d == 3) {
+            // H01[o][a] = y1[a], H02[o][b] = y2[b]
+            float* H01 = H + s.boff[0] + (size_t)o * A;
+            float* H02 = H + s.boff[1] + (size_t)o * B;
+            for (int a = tid; a < A; a += nt) H01[a] = y1[a];
+            for (int b = tid; b < B; b += nt) H02[b] = y2[b];
+        } else {
+            const float u0v = u[i0], u1v = u[s.moff[1] + i1];
+            float* H02 = H + s.boff[bidx(4, 0, 2)] + (size_t)i0 * A;
+            float* H12 = H + s.boff[bidx(4, 1, 2)] + (size_t)i1 * A;
+            float* H03 = H + s.boff[bidx(4, 0, 3)] + (size_t)i0 * B;
+            float* H13 = H + s.boff[bidx(4, 1, 3)] + (size_t)i1 * B;
+            for (int a = tid; a < A; a += nt) {
+                H02[a] = fmaf(u1v, y1[a], H02[a]);
+                H12[a] = fmaf(u0v, y1[a], H12[a]);
+            }
+            for (int b = tid; b < B; b += nt) {
+                H03[b] = fmaf(u1v, y2[b], H03[b]);
+                H13[b] = fmaf(u0v, y2[b], H13[b]);
+            }
+            // H01[i0][i1] = r_o = <y1, uA>
+            float r = 0.f;
+            for (int a = tid; a < A; a += nt) r = fmaf(y1[a], uA[a], r);
+            r = cta_sum(r, red);
+            if (tid == 0) H[s.boff[0] + i0 * s.dims[1] + i1] = r;
+        }
+        __syncthreads();
+    }
+}
+
+// y = J v  (J = blocks / (d-1), symmetric, zero diagonal blocks); thread per row.
+__device__ void batch_matvec(const BShape& s, const float* H, const float* v, float* y) {
+    const float sc = 1.f / (float)(s.d - 1);
+    for (int q = threadIdx.x; q < s.n; q += blockDim.x) {
+        const int m = bmode(s, q);
+        const int i = q - s.moff[m];
+        float acc = 0.f;
+        for (int nn = 0; nn < s.d; ++nn) {
+            if (nn == m) continue;
+            const float* vn = v + s.moff[nn];
+            const int In = s.dims[nn];
+            if (nn > m) {
+                const float* row = H + s.boff[bidx(s.d, m, nn)] + (size_t)i * In;
+                for (int j = 0; j < In; ++j) acc = fmaf(row[j], vn[j], acc);
+            } else {
+                const int Im = s.dims[m];
+                const float* blk = H + s.boff[bidx(s.d, nn, m)];
+                for (int j = 0; j < In; ++j) acc = fmaf(blk[(size_t)j * Im + i], vn[j], acc);
+            }
+        }
+        y[q] = acc * sc;
+    }
+}
+
+struct BatchSmem {
+    float* u;      // n
+    float* H;      // P
+    float* face;   // max(F, (mmax+1) n)   (face staging; Lanczos basis later)
+    float* y1;     // AB_max
+    float* y2;     // AB_max
+    float* w;      // n
+    float* red;    // 64
+    double* dred;  // 64
+    double* alpha; // kMaxLanczos
+    double* beta;  // kMaxLanczos
+    double* sv;    // kMaxLanczos
+    float* hs;     // kMaxLanczos + 8
+    float* rscratch;   // 9 kMaxLanczos
+};
+
+__global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
+    extern __shared__ __align__(16) uint8_t sm_raw[];
+    BatchSmem S;
+    {
+        double* dp = reinterpret_cast<double*>(sm_raw);
+        S.dred = dp;
+        S.alpha = S.dred + 64;
+        S.beta = S.alpha + kMaxLanczos;
+        S.sv = S.beta + kMaxLanczos;
+        float* fp = reinterpret_cast<float*>(S.sv + kMaxLanczos);
+        S.red = fp;
+        S.hs = S.red + 64;
+        S.rscratch = S.hs + kMaxLanczos + 8;
+        S.u = S.rscratch + 9 * kMaxLanczos;
+        S.w = S.u + ((a.n_max + 3) & ~3);
+        S.y1 = S.w + ((a.n_max + 3) & ~3);
+        S.y2 = S.y1 + ((a.AB_max + 3) & ~3);
+        S.H = S.y2 + ((a.AB_max + 3) & ~3);
+        S.face = S.H + ((a.P_max + 3) & ~3);
+    }
+    __shared__ int s_item;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    while (true) {
+        if (tid == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int qi = s_item;
+        __syncthreads();
+        if (qi >= a.count) break;
+        const int t = a.order[qi];
+        const BatchItem it = a.items[t];
+        BShape sh;
+        sh.d = it.d;
+        sh.moff[0] = 0;
+        for (int k = 0; k < it.d; ++k) {
+            sh.dims[k] = it.dims[k];
+            sh.moff[k + 1] = sh.moff[k] + it.dims[k];
+        }
+        sh.n = sh.moff[it.d];
+        {
+            int b = 0, off = 0;
+            for (int m = 0; m < it.d; ++m)
+                for (int n2 = m + 1; n2 < it.d; ++n2) {
+                    sh.boff[b++] = off;
+                    off += it.dims[m] * it.dims[n2];
+                }
+            sh.P = off;
+        }
+        const int d = sh.d, n = sh.n;
+        const double sqrt_d = sqrt((double)d);
+        int status = 0;
+        // normalise the initial guess per block
+        for (int m = 0; m < d; ++m) {
+            double ss = 0.0;
+            for (int q = sh.moff[m] + tid; q < sh.moff[m + 1]; q += nt) ss += (double)it.u0[q] * it.u0[q];
+            ss = cta_sum_d(ss, S.dred);
+            const double inv = (ss > 0.0 && isfinite(ss)) ? 1.0 / sqrt(ss) : 0.0;
+            if (!(ss > 0.0) || !isfinite(ss)) status = 5;
+            for (int q = sh.moff[m] + tid; q < sh.moff[m + 1]; q += nt) S.u[q] = (float)(it.u0[q] * inv);
+        }
+        __syncthreads();
+        int iters = 0, passes = 0;
+        double sigma = 0.0, resid = INFINITY;
+        while (status == 0) {
+            batch_blocks(sh, it.T, S.u, S.H, S.face, S.y1, S.y2, S.red);
+            ++passes;
+            // ---- certificate at x = u / sqrt(d): rho = x^T J x, KKT residual
+            float* V = S.face;   // (mmax+1) x n basis
+            float* Y = S.w;
+            for (int q = tid; q < n; q += nt) V[q] = (float)((double)S.u[q] / sqrt_d);
+            __syncthreads();
+            batch_matvec(sh, S.H, V, Y);
+            __syncthreads();
+            double sxy = 0.0, sxx = 0.0;
+            for (int q = tid; q < n; q += nt) {
+                sxy += (double)V[q] * Y[q];
+                sxx += (double)V[q] * V[q];
+            }
+            sxy = cta_sum_d(sxy, S.dred);
+            sxx = cta_sum_d(sxx, S.dred);
+            const double rho = sxy / sxx;
+            const double inv = 1.0 / sqrt(sxx);
+            double sw = 0.0;
+            for (int q = tid; q < n; q += nt) {
+                const double wv = ((double)Y[q] - rho * (double)V[q]) * inv;
+                sw += wv * wv;
+            }
+            sw = cta_sum_d(sw, S.dred);
+            const double b0 = sqrt(sw);
+            sigma = rho;
+            resid = (rho != 0.0) ? sqrt_d * b0 / fabs(rho) : INFINITY;
+            if (!isfinite(rho) || !isfinite(b0)) {
+                status = 5;
+                break;
+            }
+            if (resid <= a.tol) break;
+            if (iters >= a.max_iter) {
+                status = 4;
+                break;
+            }
+            ++iters;
+            // ---- Lanczos for the largest-magnitude eigenpair (warm start at x)
+            double etol = a.eig_tol;
+            if (a.eig_adapt > 0.0) etol = fmax(etol, fmin(1e-5, a.eig_adapt * resid));
+            const float finv = (float)inv, frho = (float)rho;
+            for (int q = tid; q < n; q += nt) {
+                V[q] *= finv;
+                Y[q] = Y[q] * finv - frho * V[q];
+            }
+            if (tid == 0) {
+                S.alpha[0] = rho;
+                S.beta[0] = b0;
+            }
+            __syncthreads();
+            double beta_last = b0;
+            int k = 1;
+            RitzOut ro;
+            ro.theta = rho;
+            ro.resid = b0;
+            bool done = false;
+            const int mmax = min(a.mmax, n);
+            for (int j = 1; !done; ++j) {
+                // V[j] = w / beta ; y = J V[j]
+                const bool last_basis = (j >= mmax) || !(beta_last > 1e-30);
+                if (!last_basis) {
+                    const float ib = (float)(1.0 / beta_last);
+                    for (int q = tid; q < n; q += nt) V[(size_t)j * n + q] = Y[q] * ib;
+                    __syncthreads();
+                    batch_matvec(sh, S.H, V + (size_t)j * n, Y);
+                    __syncthreads();
+                    // CGS with a second pass under cancellation (FP32 vectors)
+                    for (int pass2 = 0; pass2 < 2; ++pass2) {
+                        for (int i = warp; i <= j + 1; i += (nt >> 5)) {
+                            float sdot = 0.f;
+                            if (i <= j) {
+                                for (int q = lane; q < n; q += 32) sdot = fmaf(V[(size_t)i * n + q], Y[q], sdot);
+                            } else {
+                                for (int q = lane; q < n; q += 32) sdot = fmaf(Y[q], Y[q], sdot);
+                            }
+                            sdot = warp_sum(sdot);
+                            if (lane == 0) S.hs[i] = sdot;
+                        }
+                        __syncthreads();
+                        float ssq = 0.f;
+                        for (int i = 0; i <= j; ++i) ssq = fmaf(S.hs[i], S.hs[i], ssq);
+                        const float yy = S.hs[j + 1];
+                        const float b2 = yy - ssq;
+                        for (int q = tid; q < n; q += nt) {
+                            float wv = Y[q];
+                            for (int i = 0; i <= j; ++i) wv = fmaf(-S.hs[i], V[(size_t)i * n + q], wv);
+                            Y[q] = wv;
+                        }
+                        if (tid == 0) S.alpha[j] = (pass2 == 0 ? 0.0 : S.alpha[j]) + S.hs[j];
+                        __syncthreads();
+                        if (pass2 == 0) {
+                            if (b2 >= 0.25f * yy) {
+                                beta_last = sqrt(fmax((double)b2, 0.0));
+                                break;
+                            }
+                        } else {
+                            beta_last = sqrt(fmax((double)b2, 0.0));
+                        }
+                    }
+                    if (tid == 0) S.beta[j] = beta_last;
+                    k = j + 1;
+                    __syncthreads();
+                }
+                const bool last = last_basis || k >= mmax || !(beta_last > 1e-30);
+                if (k >= 2 && (k <= 6 || (k & 1) == 0 || last)) {
+                    __shared__ RitzOut s_ro;
+                    if (warp == 0) {
+                        RitzOut rr = ritz_largest_magnitude(S.alpha, S.beta, k, beta_last, S.sv, S.rscratch);
+                        if (lane == 0) s_ro = rr;
+                    }
+                    __syncthreads();
+                    ro = s_ro;
+                    if (ro.resid <= etol * fabs(ro.theta) || last) done = true;
+                } else if (last) {
+                    if (tid == 0) S.sv[0] = 1.0;
+                    __syncthreads();
+                    done = true;
+                }
+            }
+            // Ritz vector, sign-aligned with x, blocks normalised (lines 6-9)
+            double dot = 0.0;
+            for (int q = tid; q < n; q += nt) {
+                double x = 0.0;
+                for (int i = 0; i < k; ++i) x += S.sv[i] * (double)V[(size_t)i * n + q];
+                Y[q] = (float)x;
+                dot += x * (double)V[q];
+            }
+            dot = cta_sum_d(dot, S.dred);
+            const float sgn = dot < 0.0 ? -1.f : 1.f;
+            for (int m = 0; m < d; ++m) {
+                double ss = 0.0;
+                for (int q = sh.moff[m] + tid; q < sh.moff[m + 1]; q += nt) ss += (double)Y[q] * Y[q];
+                ss = cta_sum_d(ss, S.dred);
+                const float ib = ss > 0.0 ? (float)(1.0 / sqrt(ss)) : 0.f;
+                for (int q = sh.moff[m] + tid; q < sh.moff[m + 1]; q += nt) S.u[q] = sgn * Y[q] * ib;
+            }
+            __syncthreads();
+        }
+        // ---- sign fix (Alg. 1 lines 12-15) and gauge, then write out
+        __shared__ int s_flip;
+        if (tid == 0) s_flip = (sigma < 0.0) ? 1 : 0;
+        __syncthreads();
+        for (int m = 1; m < d; ++m) {
+            // largest |u| entry of mode m (lowest index on ties) made positive
+            if (tid == 0) {
+                float best = -1.f;
+                int bi = 0;
+                for (int q = sh.moff[m]; q < sh.moff[m + 1]; ++q)
+                    if (fabsf(S.u[q]) > best) {
+                        best = fabsf(S.u[q]);
+                        bi = q;
+                    }
+                S.red[0] = (S.u[bi] < 0.f) ? 1.f : 0.f;
+            }
+            __syncthreads();
+            if (S.red[0] != 0.f) {
+                for (int q = sh.moff[m] + tid; q < sh.moff[m + 1]; q += nt) S.u[q] = -S.u[q];
+                if (tid == 0) s_flip ^= 1;
+            }
+            __syncthreads();
+        }
+        for (int q = tid; q < n; q += nt) {
+            const bool m0 = q < sh.moff[1];
+            it.u_out[q] = (m0 && s_flip) ? -S.u[q] : S.u[q];
+        }
+        if (tid == 0) {
+            BatchOut bo;
+            bo.sigma = fabs(sigma);
+            bo.resid = resid;
+            bo.iters = iters;
+            bo.passes = passes;
+            bo.status = status;
+            bo.pad = 0;
+            a.out[t] = bo;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- host
+static size_t batch_smem(int n_max, int P_max, int F_max, int AB_max, int mmax) {
+    const int basis = std::max(F_max, (mmax + 1) * n_max);
+    return sizeof(double) * (64 + 3 * kMaxLanczos) +
+           sizeof(float) * (64 + kMaxLanczos + 8 + 9 * kMaxLanczos + 2 * ((n_max + 3) & ~3) +
+                            2 * ((AB_max + 3) & ~3) + ((P_max + 3) & ~3) + ((basis + 3) & ~3)) +
+           64;
+}
+
+struct BatchDev {
+    BatchItem* items;
+    int* order;
+    BatchOut* out;
+    int* counter;
+};
+
+hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* const* u0,
+                         float* const* u_out, const hoscf_opts& o, int threads, char* ws,
+                         size_t ws_bytes, int nsm, cudaStream_t st, double* sigma_out,
+                         hoscf_info* infos, void* pinned, size_t pinned_bytes, Err& err) {
+    // validate and describe the batch
+    std::vector<BatchItem> items((size_t)count);
+    std::vector<int64_t> sizes((size_t)count);
+    int n_max = 1, P_max = 1, F_max = 1, AB_max = 1;
+    for (int t = 0; t < count; ++t) {
+        const hoscf_tensor_desc& D = T[t];
+        if (D.order < 3 || D.order > kBatchMaxOrder || D.dtype != HOSCF_F32 || !D.data || !D.dims ||
+            !u0[t] || !u_out[t]) {
+            err.code = HOSCF_EINVAL;
+            snprintf(err.msg, sizeof(err.msg), "batch item %d: need an FP32 tensor of order 3..4", t);
+            return err.code;
+        }
+        BatchItem it;
+        memset(&it, 0, sizeof(it));
+        it.T = static_cast<const float*>(D.data);
+        it.u0 = u0[t];
+        it.u_out = u_out[t];
+        it.d = D.order;
+        int64_t N = 1, n = 0, P = 0;
+        for (int k = 0; k < D.order; ++k) {
+            if (D.dims[k] < 1 || D.dims[k] > 4096) {
+                err.code = HOSCF_EINVAL;
+                snprintf(err.msg, sizeof(err.msg), "batch item %d: dims must be 1..4096", t);
+                return err.code;
+            }
+            it.dims[k] = (int)D.dims[k];
+            N *= D.dims[k];
+            n += D.dims[k];
+        }
+        for (int m = 0; m < D.order; ++m)
+            for (int k = m + 1; k < D.order; ++k) P += D.dims[m] * D.dims[k];
+        const int64_t A = D.dims[D.order - 2], B = D.dims[D.order - 1];
+        n_max = std::max<int>(n_max, (int)n);
+        P_max = std::max<int>(P_max, (int)P);
+        F_max = std::max<int>(F_max, (int)(A * B));
+        AB_max = std::max<int>(AB_max, (int)std::max(A, B));
+        items[(size_t)t] = it;
+        sizes[(size_t)t] = N;
+    }
+    const int mmax = std::min(kBatchLanczos, std::max(2, o.eig_max_steps));
+    const size_t smem = batch_smem(n_max, P_max, F_max, AB_max, mmax);
+    if (smem > 220 * 1024) {
+        err.code = HOSCF_EUNSUPPORTED;
+        snprintf(err.msg, sizeof(err.msg), "batch tensors too large for one CTA (%zu bytes)", smem);
+        return err.code;
+    }
+    std::vector<int> order((size_t)count);
+    for (int t = 0; t < count; ++t) order[(size_t)t] = t;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return sizes[(size_t)x] > sizes[(size_t)y]; });
+    // device copies of the descriptors (workspace), via the pinned buffer
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t q = off;
+        off = align_up(off + bytes, 256);
+        return q;
+    };
+    const size_t o_items = take(sizeof(BatchItem) * count);
+    const size_t o_order = take(sizeof(int) * count);
+    const size_t o_out = take(sizeof(BatchOut) * count);
+    const size_t o_cnt = take(256);
+    if (off > ws_bytes || off > pinned_bytes) {
+        err.code = HOSCF_ENOMEM;
+        snprintf(err.msg, sizeof(err.msg), "batch descriptors need %zu bytes", off);
+        return err.code;
+    }
+    char* hp = static_cast<char*>(pinned);
+    memcpy(hp + o_items, items.data(), sizeof(BatchItem) * count);
+    memcpy(hp + o_order, order.data(), sizeof(int) * count);
+    memset(hp + o_cnt, 0, 256);
+    BatchArgs a;
+    a.items = reinterpret_cast<BatchItem*>(ws + o_items);
+    a.order = reinterpret_cast<int*>(ws + o_order);
+    a.out = reinterpret_cast<BatchOut*>(ws + o_out);
+    a.count = count;
+    a.counter = reinterpret_cast<int*>(ws + o_cnt);
+    a.tol = o.tol;
+    a.max_iter = o.max_iter;
+    a.eig_tol = o.eig_tol > 0 ? o.eig_tol : 1e-10;
+    a.eig_adapt = o.eig_adapt;
+    a.mmax = mmax;
+    a.n_max = n_max;
+    a.P_max = P_max;
+    a.F_max = F_max;
+    a.AB_max = AB_max;
+    cudaError_t e = cudaFuncSetAttribute(batched_hoscf_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 1;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_hoscf_kernel, threads, smem);
+    const int grid = std::max(1, std::min(count, nsm * std::max(1, per_sm)));
+    // the whole batch is one CUDA graph: descriptors in, the persistent
+    // kernel, results out; a repeated batch replays the instantiated graph
+    uint64_t key = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) key = (key ^ c[i]) * 1099511628211ull;
+    };
+    mix(&a, sizeof(a));
+    mix(hp, o_out);
+    mix(&grid, sizeof(grid));
+    mix(&threads, sizeof(threads));
+    mix(&smem, sizeof(smem));
+    mix(&st, sizeof(st));
+    static std::mutex mu;
+    static cudaGraphExec_t cached = nullptr;
+    static uint64_t cached_key = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (e == cudaSuccess && !(cached && cached_key == key)) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemcpyAsync(ws, hp, o_out, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(ws + o_cnt, hp + o_cnt, 256, cudaMemcpyHostToDevice, st);
+            batched_hoscf_kernel<<<grid, threads, smem, st>>>(a);
+            cudaMemcpyAsync(hp + o_out, ws + o_out, sizeof(BatchOut) * count,
+                            cudaMemcpyDeviceToHost, st);
+            e = cudaStreamEndCapture(st, &graph);
+        }
+        if (e == cudaSuccess) {
+            if (cached) cudaGraphExecDestroy(cached);
+            cached = nullptr;
+            e = cudaGraphInstantiate(&cached, graph, 0);
+            cached_key = (e == cudaSuccess) ? key : 0;
+        }
+        if (graph) cudaGraphDestroy(graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(cached, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        err.code = HOSCF_ECUDA;
+        snprintf(err.msg, sizeof(err.msg), "batched solve: %s", cudaGetErrorString(e));
+        return err.code;
+    }
+    const BatchOut* res = reinterpret_cast<const BatchOut*>(hp + o_out);
+    hoscf_status worst = HOSCF_OK;
+    for (int t = 0; t < count; ++t) {
+        sigma_out[t] = res[t].sigma;
+        if (infos) {
+            infos[t].iters = res[t].iters;
+            infos[t].passes = res[t].passes;
+            infos[t].passes_refine = 0;
+            infos[t].rqi_accepts = 0;
+            infos[t].resid = res[t].resid;
+            infos[t].resid_4_1 = NAN;
+            infos[t].sigma_raw = res[t].sigma;
+        }
+        const hoscf_status sst = res[t].status == 0 ? HOSCF_OK
+                                 : res[t].status == 4 ? HOSCF_NOT_CONVERGED : HOSCF_NONFINITE;
+        if (sst == HOSCF_NONFINITE || (sst == HOSCF_NOT_CONVERGED && worst == HOSCF_OK)) worst = sst;
+    }
+    if (worst != HOSCF_OK) {
+        err.code = worst;
+        snprintf(err.msg, sizeof(err.msg), "some batch items did not converge");
+    }
+    return worst;
+}
+
+}  // namespace hoscf

@@ -13,6 +13,12 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
                       const float* scales, const float* u, float* H, char* ws, int* dev_err,
                       uint64_t timeout_ns, cudaStream_t st, Err& err);
 
+// batched.cu
+hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* const* u0,
+                         float* const* u_out, const hoscf_opts& o, int threads, char* ws,
+                         size_t ws_bytes, int nsm, cudaStream_t st, double* sigma_out,
+                         hoscf_info* infos, void* pinned, size_t pinned_bytes, Err& err);
+
 // backward.cu
 cudaError_t launch_tangent_project(const Shape& s, const float* u, const float* w, double* b,
                                    double* bnorm2, cudaStream_t st);

@@ -1,0 +1,262 @@
+// Small symmetric tridiagonal problems of the Lanczos kernels (k <= 128):
+// extreme eigenvalues by warp multisection, eigenvectors by inverse
+// iteration, and the shifted solves of the RQI / adjoint modes.
+#pragma once
+
+#include "common.cuh"
+
+namespace hoscf {
+
+constexpr int kMaxLanczos = 128;
+
+// --- small symmetric tridiagonal Ritz problem (k <= kMaxLanczos), one warp.
+// Sturm count of eigenvalues < x (FP32, fast reciprocal: only signs matter).
+static __device__ __forceinline__ int sturm_count(const float* al, const float* be2, int k, float x,
+                                           float pivmin) {
+    int c = 0;
+    float q = al[0] - x;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
+    for (int i = 1; i < k; ++i) {
+        q = (al[i] - x) - __fdividef(be2[i - 1], q);
+        if (fabsf(q) < pivmin) q = -pivmin;
+        c += q < 0.f;
+    }
+    return c;
+}
+
+// Largest (want_max) or smallest eigenvalue by 16-way multisection on one
+// half-warp.  Returns the midpoint of the final bracket.
+static __device__ float extreme_eig(const float* al, const float* be2, int k, float lo, float hi,
+                             bool want_max, int sublane, unsigned halfmask, float pivmin) {
+    for (int round = 0; round < 7; ++round) {
+        const float x = lo + (hi - lo) * (float)(sublane + 1) / 17.f;
+        const int c = sturm_count(al, be2, k, x, pivmin);
+        // want_max: first shift with all k eigenvalues below it
+        const bool hit = want_max ? (c == k) : (c >= 1);
+        const unsigned bal = __ballot_sync(halfmask, hit);
+        const unsigned mine = (halfmask == 0xffffu) ? bal : (bal >> 16);
+        const int first = mine ? __ffs(mine) - 1 : 16;   // first hit shift index
+        const float w = (hi - lo) / 17.f;
+        const float nlo = lo + w * (float)first;
+        const float nhi = (first == 16) ? hi : lo + w * (float)(first + 1);
+        lo = nlo;
+        hi = nhi;
+        if (hi - lo <= 4.f * 1.2e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
+    }
+    return 0.5f * (lo + hi);
+}
+
+// Eigenvector of the tridiagonal T for eigenvalue approx theta: two steps of
+// inverse iteration with partial-pivot LU (FP32).  s has k entries, unit norm.
+static __device__ void tridiag_inverse_iteration(const float* al, const float* be, int k, float theta,
+                                          float bound, float* s, float* wa, float* wb, float* wc,
+                                          float* wd, int* piv) {
+    // LU of (T - theta I): rows i with sub-diagonal be[i-1], super be[i].
+    // Zero pivots are replaced by eps32 * ||T|| (standard inverse iteration).
+    const float eps = fmaxf(1.2e-7f * bound, 1e-30f);
+    for (int i = 0; i < k; ++i) s[i] = 1.f;
+    for (int i = 0; i < k; ++i) {
+        wa[i] = al[i] - theta;
+        wb[i] = (i < k - 1) ? be[i] : 0.f;
+        wc[i] = 0.f;
+    }
+    for (int i = 0; i < k - 1; ++i) {
+        const float sub = be[i];   // element (i+1, i)
+        if (fabsf(wa[i]) >= fabsf(sub)) {
+            piv[i] = 0;
+            const float l = (wa[i] != 0.f) ? __fdividef(sub, wa[i]) : 0.f;
+            wd[i] = l;
+            wa[i + 1] -= l * wb[i];
+        } else {
+            piv[i] = 1;
+            const float l = __fdividef(wa[i], sub);
+            wd[i] = l;
+            const float a_ip1 = wa[i + 1];
+            wa[i] = sub;
+            const float t = wb[i];
+            wb[i] = a_ip1;
+            wa[i + 1] = t - l * a_ip1;
+            if (i < k - 2) {
+                wc[i] = wb[i + 1];
+                wb[i + 1] = -l * wb[i + 1];
+            }
+        }
+    }
+    for (int i = 0; i < k; ++i)
+        if (fabsf(wa[i]) <= eps) wa[i] = (wa[i] < 0.f) ? -eps : eps;
+    for (int it = 0; it < 2; ++it) {
+        for (int i = 0; i < k - 1; ++i) {
+            if (piv[i]) {
+                const float t = s[i];
+                s[i] = s[i + 1];
+                s[i + 1] = t - wd[i] * s[i];
+            } else {
+                s[i + 1] -= wd[i] * s[i];
+            }
+        }
+        float mx = 0.f;
+        for (int i = k - 1; i >= 0; --i) {
+            float v = s[i];
+            if (i + 1 < k) v -= wb[i] * s[i + 1];
+            if (i + 2 < k) v -= wc[i] * s[i + 2];
+            s[i] = __fdividef(v, wa[i]);
+            if (fabsf(s[i]) > 1e30f) {   // rescale to stay finite
+                for (int t = i; t < k; ++t) s[t] *= 1e-30f;
+            }
+        }
+        for (int i = 0; i < k; ++i) mx = fmaxf(mx, fabsf(s[i]));
+        if (!(mx > 0.f) || !isfinite(mx)) {
+            for (int i = 0; i < k; ++i) s[i] = (i == 0) ? 1.f : 0.f;
+            mx = 1.f;
+        }
+        const float inv = 1.f / mx;
+        for (int i = 0; i < k; ++i) s[i] *= inv;
+    }
+}
+
+// Solution z of (T - shift I) z = e_1 for the k x k tridiagonal T (FP32,
+// partial-pivot LU as above); returns |z_k| / ||z|| and writes z / ||z|| to
+// s_out (FP64).  One thread.
+static __device__ double tridiag_shifted_solve(const double* alpha, const double* beta, int k,
+                                        double shift, double* s_out, float* wa, float* wb,
+                                        float* wc, float* wd, float* z, int* piv,
+                                        double* znorm) {
+    float bound = 0.f;
+    for (int i = 0; i < k; ++i) {
+        wa[i] = (float)(alpha[i] - shift);
+        wb[i] = (i < k - 1) ? (float)beta[i] : 0.f;
+        wc[i] = 0.f;
+        z[i] = (i == 0) ? 1.f : 0.f;
+        bound = fmaxf(bound, fabsf(wa[i]) + fabsf(wb[i]) + (i > 0 ? (float)fabs(beta[i - 1]) : 0.f));
+    }
+    const float eps = fmaxf(1.2e-7f * bound, 1e-30f);
+    for (int i = 0; i < k - 1; ++i) {
+        const float sub = (float)beta[i];
+        if (fabsf(wa[i]) >= fabsf(sub)) {
+            piv[i] = 0;
+            const float l = (wa[i] != 0.f) ? sub / wa[i] : 0.f;
+            wd[i] = l;
+            wa[i + 1] -= l * wb[i];
+        } else {
+            piv[i] = 1;
+            const float l = wa[i] / sub;
+            wd[i] = l;
+            const float a_ip1 = wa[i + 1];
+            wa[i] = sub;
+            const float t = wb[i];
+            wb[i] = a_ip1;
+            wa[i + 1] = t - l * a_ip1;
+            if (i < k - 2) {
+                wc[i] = wb[i + 1];
+                wb[i + 1] = -l * wb[i + 1];
+            }
+        }
+    }
+    for (int i = 0; i < k - 1; ++i) {
+        if (piv[i]) {
+            const float t = z[i];
+            z[i] = z[i + 1];
+            z[i + 1] = t - wd[i] * z[i];
+        } else {
+            z[i + 1] -= wd[i] * z[i];
+        }
+    }
+    for (int i = k - 1; i >= 0; --i) {
+        float v = z[i];
+        if (i + 1 < k) v -= wb[i] * z[i + 1];
+        if (i + 2 < k) v -= wc[i] * z[i + 2];
+        const float dd = fabsf(wa[i]) > eps ? wa[i] : (wa[i] < 0.f ? -eps : eps);
+        z[i] = v / dd;
+        if (fabsf(z[i]) > 1e30f)
+            for (int t = i; t < k; ++t) z[t] *= 1e-30f;
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < k; ++i) nrm += (double)z[i] * (double)z[i];
+    nrm = sqrt(nrm);
+    if (!(nrm > 0.0) || !isfinite(nrm)) {
+        for (int i = 0; i < k; ++i) s_out[i] = (i == 0) ? 1.0 : 0.0;
+        *znorm = NAN;
+        return 1.0;
+    }
+    *znorm = nrm;
+    for (int i = 0; i < k; ++i) s_out[i] = (double)z[i] / nrm;
+    return fabs((double)z[k - 1]) / nrm;
+}
+
+struct RitzOut {
+    double theta;
+    double resid;   // |beta_k * s_k| / ||s||
+};
+
+// Largest-magnitude Ritz pair of T_k (alpha, beta in FP64, k >= 1); writes the
+// unit vector s (FP64) to s_out.  Called by one full warp.
+static __device__ RitzOut ritz_largest_magnitude(const double* alpha, const double* beta, int k,
+                                          double beta_k, double* s_out, float* scratch) {
+    const int lane = threadIdx.x & 31;
+    float* al = scratch;
+    float* be = al + kMaxLanczos;
+    float* be2 = be + kMaxLanczos;
+    float* sv = be2 + kMaxLanczos;
+    float* wa = sv + kMaxLanczos;
+    float* wb = wa + kMaxLanczos;
+    float* wc = wb + kMaxLanczos;
+    float* wd = wc + kMaxLanczos;
+    int* piv = reinterpret_cast<int*>(wd + kMaxLanczos);
+    float bound = 0.f;
+    for (int i = lane; i < k; i += 32) {
+        al[i] = (float)alpha[i];
+        be[i] = (i < k - 1) ? (float)beta[i] : 0.f;
+        be2[i] = be[i] * be[i];
+    }
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) {
+        const float r = fabsf(al[i]) + fabsf(be[i]) + (i > 0 ? fabsf(be[i - 1]) : 0.f);
+        bound = fmaxf(bound, r);
+    }
+    for (int o = 16; o > 0; o >>= 1) bound = fmaxf(bound, __shfl_xor_sync(HOSCF_FULLMASK, bound, o));
+    bound = bound * 1.0001f + 1e-30f;
+    const float pivmin = fmaxf(bound * 1e-30f, 1e-35f);
+    // half-warp 0: largest eigenvalue, half-warp 1: smallest
+    const bool upper = lane >= 16;
+    const unsigned hm = upper ? 0xffff0000u : 0x0000ffffu;
+    float ext;
+    if (k == 1) {
+        ext = al[0];
+    } else {
+        ext = extreme_eig(al, be2, k, -bound, bound, !upper, lane & 15, hm, pivmin);
+    }
+    const float tmax = __shfl_sync(HOSCF_FULLMASK, ext, 0);
+    const float tmin = __shfl_sync(HOSCF_FULLMASK, ext, 16);
+    // ties between +l and -l go to the positive end
+    const float theta32 = (tmax >= -tmin) ? tmax : tmin;
+    if (lane == 0) {
+        if (k == 1) {
+            sv[0] = 1.f;
+        } else {
+            tridiag_inverse_iteration(al, be, k, theta32, bound, sv, wa, wb, wc, wd, piv);
+        }
+    }
+    __syncwarp();
+    // FP64 Rayleigh quotient of s, lane-parallel
+    double num = 0.0, den = 0.0;
+    for (int i = lane; i < k; i += 32) {
+        const double si = sv[i];
+        double ts = alpha[i] * si;
+        if (i > 0) ts += beta[i - 1] * (double)sv[i - 1];
+        if (i < k - 1) ts += beta[i] * (double)sv[i + 1];
+        num += si * ts;
+        den += si * si;
+    }
+    num = warp_sum_d(num);
+    den = warp_sum_d(den);
+    const double inv = 1.0 / sqrt(den);
+    for (int i = lane; i < k; i += 32) s_out[i] = (double)sv[i] * inv;
+    RitzOut ro;
+    ro.theta = num / den;
+    ro.resid = fabs(beta_k * (double)sv[k - 1]) * inv;
+    return ro;
+}
+
+
+}  // namespace hoscf

@@ -1,0 +1,87 @@
+"""Batched form: many small tensors in one persistent graph-captured launch,
+each matched against the FP64 oracle (sigma rel <= 1e-5, factors
+|1 - |<u, u_ref>|| <= 1e-5)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_01778_gb300 import build
+    build.build()
+
+
+def P():
+    import paper_2403_01778_gb300 as pkg
+    return pkg
+
+
+def check_item(T, u0, sigma, u, tol=1e-5):
+    ref = oracle.hoscf(T.cpu().numpy(), [v.cpu().numpy() for v in u0], tol=1e-10, max_iter=400)
+    assert abs(sigma - ref.sigma) <= tol * ref.sigma
+    o = 0
+    for ur in ref.u:
+        un = u[o:o + len(ur)].double().cpu().numpy()
+        o += len(ur)
+        assert abs(1 - abs(float(un @ ur))) <= tol
+
+
+def small_batch(seed, c3, c4, hi3=40, hi4=16):
+    Ts, _ = W.batched_tensors(seed, count3=c3, count4=c4, hi3=hi3, hi4=hi4)
+    u0 = [torch.cat(W.unit_gaussian_vectors(T.shape, seed * 7 + i)) for i, T in enumerate(Ts)]
+    return [T.cuda() for T in Ts], [u.cuda() for u in u0]
+
+
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+def test_batched_matches_oracle(threads):
+    Ts, u0 = small_batch(1, 10, 6)
+    sig, us, infos, st = P().hoscf_solve_batched(Ts, u0, tol=1e-6, batch_threads=threads)
+    assert st == 0
+    for T, u, s, uo in zip(Ts, u0, sig, us):
+        dims = T.shape
+        check_item(T, [u[sum(dims[:k]):sum(dims[:k + 1])] for k in range(len(dims))], s, uo)
+
+
+def test_batched_replay_is_bit_identical_and_matches_plain_solve():
+    Ts, u0 = small_batch(2, 12, 4)
+    s1, u1, _, _ = P().hoscf_solve_batched(Ts, u0, tol=1e-6)
+    s2, u2, _, _ = P().hoscf_solve_batched(Ts, u0, tol=1e-6)    # graph replay
+    assert s1 == s2
+    assert all(torch.equal(a, b) for a, b in zip(u1, u2))
+    for T, u, s in list(zip(Ts, u0, s1))[:4]:
+        r = P().hoscf_solve(T, u, tol=1e-6)
+        assert abs(r.sigma - s) <= 1e-5 * s
+
+
+def test_batched_full_workload():
+    """768 order-3 tensors with dims in [8, 96] and 256 order-4 tensors with
+    dims in [8, 32], planted rank one sigma ~ U[1, 10] plus 5% noise."""
+    Ts, _ = W.batched_tensors(0)
+    u0 = [torch.cat(W.unit_gaussian_vectors(T.shape, 1000 + i)) for i, T in enumerate(Ts)]
+    Tg = [T.cuda() for T in Ts]
+    ug = [u.cuda() for u in u0]
+    sig, us, infos, st = P().hoscf_solve_batched(Tg, ug, tol=1e-6)
+    assert st == 0
+    assert all(inf.resid <= 1e-6 for inf in infos)
+    rng = np.random.default_rng(3)
+    for i in rng.choice(len(Ts), size=12, replace=False):
+        dims = Ts[i].shape
+        u = u0[i]
+        check_item(Ts[i], [u[sum(dims[:k]):sum(dims[:k + 1])] for k in range(len(dims))],
+                   sig[i], us[i])
+
+
+def test_autotuner_picks_a_candidate(tmp_path, monkeypatch):
+    from paper_2403_01778_gb300 import autotune
+    monkeypatch.setattr(autotune, "_CACHE", str(tmp_path / "at.json"))
+    Ts, u0 = small_batch(4, 6, 2)
+    th, rec = autotune.best_threads(Ts, u0)
+    assert th in autotune.CANDIDATES
+    th2, _ = autotune.best_threads(Ts, u0)      # cached
+    assert th2 == th
