@@ -212,6 +212,124 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------------ extras
+def _timed(fn, reps=1):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out = fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps, out
+
+
+def pass_rate(P, dims, device, seed=1):
+    """TTVc pass GB/s on a Gaussian tensor of these dims (L2 flushed)."""
+    import torch
+    import workloads as W
+    T = W.gaussian_tensor(dims, seed, device=device)
+    u = torch.cat(W.unit_gaussian_vectors(dims, seed + 1, device=device))
+    H = P.hoscf_ttvc_blocks(T, u)
+    flush = torch.empty(64 * 1024 * 1024, device=device)
+    best = float("inf")
+    for _ in range(5):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.hoscf_ttvc_blocks(T, u, H)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return {"ms": best, "GBs": pass_bytes(dims) / (best / 1e3) / 1e9}
+
+
+def run_extras(P, T, u0, dev):
+    """Time-to-residual of the solve variants and of the precision, batched
+    and differentiation forms on their workloads (all synthetic, seeded)."""
+    import numpy as np
+    import torch
+    import oracle
+    import workloads as W
+    ex = {}
+    # headline workload: HOSCF vs iHOSCF to KKT residual 1e-6
+    for variant in ("hoscf", "ihoscf"):
+        t, r = _timed(lambda: P.hoscf_solve(T, u0, tol=1e-6, max_iter=200, variant=variant))
+        ex[f"time_to_residual_1e-6_{variant}"] = {
+            "seconds": t, "iters": r.iters, "passes": r.passes, "resid": r.resid,
+            "sigma": r.sigma, "converged": r.converged}
+    # precision form: 200^4 planted rank one (sigma 100) + noise of norm 10
+    T3 = W.config_tensor("cfg3_200p4", seed=0, device=dev)
+    u3 = torch.cat(W.unit_gaussian_vectors(T3.shape, 1, device=dev))
+    prec = {}
+    q16, _ = P.hoscf_quantize(T3, "bf16")
+    q8, s8 = P.hoscf_quantize(T3, "fp8")
+    cases = [("fp32", dict(T=T3)), ("bf16+fp32", dict(T=q16, refine=T3)),
+             ("fp8+fp32", dict(T=q8, scales=s8, refine=T3))]
+    T3h = None
+    for name, kw in cases:
+        Tq = kw.pop("T")
+        P.hoscf_solve(Tq, u3, tol=1e-6, max_iter=200, **kw)     # warm
+        t, r = _timed(lambda: P.hoscf_solve(Tq, u3, tol=1e-6, max_iter=200, **kw))
+        rec = {"seconds": t, "iters": r.iters, "passes": r.passes,
+               "passes_fp32": r.passes_refine if name != "fp32" else r.passes,
+               "sigma": r.sigma, "resid": r.resid, "converged": r.converged}
+        # FP64 oracle check of the returned point: KKT residual and sigma from
+        # the FP32 tensor itself
+        if T3h is None:
+            T3h = T3.cpu().numpy()
+        uf = [v.double().cpu().numpy() for v in r.factors()]
+        g, full = oracle.kkt_vectors(T3h, uf, nthreads=len(os.sched_getaffinity(0)))
+        rec["oracle_sigma"] = full
+        rec["oracle_kkt_resid"] = float(np.linalg.norm(np.concatenate(g) - full *
+                                                       np.concatenate(uf)) / abs(full))
+        prec[name] = rec
+    for name in ("bf16+fp32", "fp8+fp32"):
+        prec[name]["speedup_vs_fp32"] = prec["fp32"]["seconds"] / prec[name]["seconds"]
+    prec["pass_GBs_fp32"] = pass_rate(P, (200, 200, 200, 200), dev)["GBs"]
+    ex["precision_200p4"] = prec
+    del T3, q16, q8, s8, T3h
+    torch.cuda.empty_cache()
+    # batched form: 768 order-3 + 256 order-4 small tensors
+    Ts, _ = W.batched_tensors(0)
+    Tg = [X.cuda() for X in Ts]
+    ug = [torch.cat(W.unit_gaussian_vectors(X.shape, 1000 + i)).cuda() for i, X in enumerate(Ts)]
+    from paper_2403_01778_gb300 import autotune
+    th, _ = autotune.best_threads(Tg, ug)
+    P.hoscf_solve_batched(Tg, ug, tol=1e-6, batch_threads=th)
+    tb, (sig, _, infos, st) = _timed(lambda: P.hoscf_solve_batched(Tg, ug, tol=1e-6,
+                                                                    batch_threads=th))
+    k = 64
+    tp, _ = _timed(lambda: [P.hoscf_solve(Tg[i], ug[i], tol=1e-6) for i in range(0, len(Tg), len(Tg) // k)])
+    per_tensor = tp / len(range(0, len(Tg), len(Tg) // k))
+    ex["batched_1024"] = {"seconds": tb, "tensors_per_s": len(Tg) / tb, "threads": th,
+                          "all_converged": st == 0,
+                          "max_resid": max(inf.resid for inf in infos),
+                          "per_tensor_launch_s": per_tensor,
+                          "per_tensor_tensors_per_s": 1.0 / per_tensor,
+                          "speedup": (len(Tg) / tb) * per_tensor}
+    del Tg, ug, Ts
+    # differentiation form: forward solve + backward (loss sigma + <w, u>)
+    grad = {}
+    for name in ("cfg4a_256cube", "cfg4b_order6"):
+        Tgd = W.config_tensor(name, seed=0, device=dev)
+        ud = torch.cat(W.unit_gaussian_vectors(Tgd.shape, 1, device=dev))
+        w = torch.randn(ud.numel(), generator=torch.Generator(device=dev).manual_seed(2), device=dev)
+        tf, r = _timed(lambda: P.hoscf_solve(Tgd, ud, tol=1e-6))
+        P.hoscf_backward(Tgd, r.u, r.sigma, 1.0, w)
+        tbk, _ = _timed(lambda: P.hoscf_backward(Tgd, r.u, r.sigma, 1.0, w), reps=3)
+        grad[name] = {"dims": list(Tgd.shape), "forward_s": tf, "backward_s": tbk,
+                      "write_GBs": Tgd.numel() * 4 / tbk / 1e9, "iters": r.iters}
+        del Tgd
+    ex["differentiation"] = grad
+    # the pass on the paper's other shapes (Table 5 scalability tensors etc.)
+    shapes = {}
+    for dims in W.table_shapes() + [(256, 256, 256), (24, 20, 24, 20, 24, 20)]:
+        shapes["x".join(map(str, dims))] = pass_rate(P, dims, dev)
+    ex["pass_shapes"] = shapes
+    return ex
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -319,15 +437,7 @@ def run_ours(args, rank, world, local_rank):
 
     extras = {}
     if not args.no_extras and rank == 0:
-        for variant in ("hoscf", "ihoscf"):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r = P.hoscf_solve(T, u0, tol=1e-6, max_iter=200, variant=variant)
-            torch.cuda.synchronize()
-            extras[f"time_to_residual_1e-6_{variant}"] = {
-                "seconds": time.perf_counter() - t0, "iters": r.iters, "passes": r.passes,
-                "resid": r.resid, "sigma": r.sigma, "converged": r.converged}
-
+        extras = run_extras(P, T, u0, dev)
     peak, peak_kind = load_peaks()
     achieved = nb / (pass_avg / 1e3) / 1e9
     if rank == 0:

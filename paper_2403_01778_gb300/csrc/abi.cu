@@ -437,6 +437,7 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
     };
 
     double sc[SC_COUNT], sk[SC_COUNT], sy[SC_COUNT];
+    double prev_resid = INFINITY;
     st = do_pass(ucur, Hcur);
     if (st) return st;
     while (true) {
@@ -446,7 +447,11 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
         sigma = sc[SC_SIGMA];
         resid = sc[SC_KKT];
         r41 = sc[SC_R41];
-        if (Tr && !use_ref && (resid <= o.switch_tol || sc[SC_CONVERGED] != 0.0)) {
+        // precision form: move to the FP32 tensor once the residual reaches
+        // switch_tol or stops improving (the low-precision floor)
+        const bool stalled = Tr && !use_ref && iters > 0 && resid > 0.5 * prev_resid;
+        prev_resid = resid;
+        if (Tr && !use_ref && (resid <= o.switch_tol || stalled || sc[SC_CONVERGED] != 0.0)) {
             // precision form: the low-precision tensor has done its part; the
             // remaining passes and the certificate use the FP32 tensor
             use_ref = true;

@@ -268,6 +268,17 @@ __device__ __forceinline__ void apply_scales(const float* __restrict__ scales, i
     for (int c = 0; c < 4; ++c) v[c] *= (((f0 + c) >> 7) == g0) ? s0 : s1;
 }
 
+// Packed FP32 (two lanes per instruction, IEEE fma / mul per lane, so the
+// results equal the scalar ones bit for bit).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const uint64_t*>(&a)), "l"(*reinterpret_cast<const uint64_t*>(&b)),
+          "l"(*reinterpret_cast<const uint64_t*>(&c)));
+    return *reinterpret_cast<const float2*>(&d);
+}
+
 // How the consumer warps get their tile rows.
 enum LoadMode : int { LOAD_TMA = 0, LOAD_VEC = 1, LOAD_SCALAR = 2 };
 
@@ -332,8 +343,8 @@ __global__ void __launch_bounds__(MODE == LOAD_TMA ? 288 : 256, 1)
         }
     }
 
-    float acc[ROWS][4];
-    float uB4[4];
+    float2 acc[ROWS][2];
+    float2 uB2[2];
     float uAr[ROWS];
     int64_t cur_t = -1;
     int64_t ta = 0, tb = 0;
@@ -344,7 +355,7 @@ __global__ void __launch_bounds__(MODE == LOAD_TMA ? 288 : 256, 1)
         float* dst = a.hp + ((size_t)(c * 2 + seg) * FA) * FB;
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
-            float4 q = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+            float4 q = make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y);
             *reinterpret_cast<float4*>(dst + (size_t)(warp * ROWS + r) * FB + 4 * lane) = q;
         }
     };
@@ -359,25 +370,29 @@ __global__ void __launch_bounds__(MODE == LOAD_TMA ? 288 : 256, 1)
             cur_t = t;
             ta = t / a.TB;
             tb = t - ta * a.TB;
+            float ub[4];
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
                 const int64_t b = tb * FB + 4 * lane + cc;
-                uB4[cc] = b < a.B ? a.uB[b] : 0.f;
+                ub[cc] = b < a.B ? a.uB[b] : 0.f;
             }
+            uB2[0] = make_float2(ub[0], ub[1]);
+            uB2[1] = make_float2(ub[2], ub[3]);
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) {
                 const int64_t ar = ta * FA + warp * ROWS + r;
                 uAr[r] = ar < a.A ? a.uA[ar] : 0.f;
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) acc[r][cc] = 0.f;
+                acc[r][0] = make_float2(0.f, 0.f);
+                acc[r][1] = make_float2(0.f, 0.f);
             }
         }
         const float wo = __ldg(a.w + o);
+        const float2 wo2 = make_float2(wo, wo);
         constexpr int RP = ROWS <= 8 ? 8 : (ROWS <= 16 ? 16 : 32);
         float y1[RP];
 #pragma unroll
         for (int r = ROWS; r < RP; ++r) y1[r] = 0.f;
-        float y2[4] = {0.f, 0.f, 0.f, 0.f};
+        float2 y2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         const int s = TMA ? (int)(k % nstage) : 0;
         if (TMA) {
             const uint32_t par = (uint32_t)((k / nstage) & 1);
@@ -411,14 +426,14 @@ __global__ void __launch_bounds__(MODE == LOAD_TMA ? 288 : 256, 1)
             }
             if (std::is_same<E, fp8_t>::value && ar < a.A && b0 < a.B)
                 apply_scales(a.scales, ((int64_t)o * a.A + ar) * a.B + b0, v);
-            float d1 = 0.f;
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                acc[r][cc] = fmaf(wo, v[cc], acc[r][cc]);
-                d1 = fmaf(v[cc], uB4[cc], d1);
-                y2[cc] = fmaf(v[cc], uAr[r], y2[cc]);
-            }
-            y1[r] = d1;
+            const float2 v0 = make_float2(v[0], v[1]), v1 = make_float2(v[2], v[3]);
+            acc[r][0] = ffma2(wo2, v0, acc[r][0]);
+            acc[r][1] = ffma2(wo2, v1, acc[r][1]);
+            const float2 ua2 = make_float2(uAr[r], uAr[r]);
+            y2[0] = ffma2(v0, ua2, y2[0]);
+            y2[1] = ffma2(v1, ua2, y2[1]);
+            const float2 dd = ffma2(v1, uB2[1], make_float2(v0.x * uB2[0].x, v0.y * uB2[0].y));
+            y1[r] = dd.x + dd.y;
         }
         if (TMA) {
             __syncwarp();
@@ -433,7 +448,7 @@ __global__ void __launch_bounds__(MODE == LOAD_TMA ? 288 : 256, 1)
         }
         // column sums over the 8 warps -> y2 partial of this a-tile
         float* sy = s_y2 + (size_t)(k & 1) * 8 * FB;
-        *reinterpret_cast<float4*>(sy + warp * FB + 4 * lane) = make_float4(y2[0], y2[1], y2[2], y2[3]);
+        *reinterpret_cast<float4*>(sy + warp * FB + 4 * lane) = make_float4(y2[0].x, y2[0].y, y2[1].x, y2[1].y);
         asm volatile("bar.sync 1, 256;" ::: "memory");
         if (tid < FB) {
             float sum = 0.f;
