@@ -72,6 +72,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Asynchronous global->shared copy of N = 4, 8 or 16 bytes; `valid` false
+// zero-fills the destination without reading the source.
+template <int N>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+    if (N == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)),
+                     "l"(src), "r"(valid ? 16 : 0)
+                     : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_addr(dst)),
+                     "l"(src), "n"(N), "r"(valid ? N : 0)
+                     : "memory");
+    }
+}
+
+// The barrier receives one arrival (counted in its init count) once every
+// cp.async this thread issued before has landed.
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
 // Wait for an mbarrier phase with a wall-clock bound.  Returns false (and
 // leaves the caller to record the timeout) when the bound passes.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,

@@ -58,15 +58,51 @@ struct PassPlan {
     int rows = 8;             // rows per consumer warp; FA = 8 * rows
     int FA = 64, FB = 128;
     int64_t TA = 1, TB = 1, TT = 1, items = 0, W = 0;
+    int64_t P = 0;            // outer-index chunks per tile (0: stream-K split)
     int grid = 0;
-    int nstage = 0;
+    int nstage = 0;           // slots of each warp's load ring (0: direct loads)
+    int group = 0;            // items per column-sum exchange
     size_t smem = 0;
     // workspace offsets (bytes)
-    size_t off_w = 0, off_hp = 0, off_y1p = 0, off_y2p = 0, off_y1 = 0, off_y2 = 0, off_r = 0;
+    size_t off_w = 0, off_hp = 0, off_y1p = 0, off_y2p = 0, off_y1 = 0, off_y2 = 0, off_r = 0,
+           off_wx = 0;
     size_t bytes = 0;
 };
 
 bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p);
+
+#ifdef __CUDACC__
+#define HOSCF_HD __host__ __device__
+#else
+#define HOSCF_HD
+#endif
+
+// Shared-memory layout of the tiled pass kernel, from a 1024-byte aligned
+// base: each of the 8 warps owns S ring slots of rows x 128 elements, one
+// mbarrier per slot and (FP8) two group scales per slot row; then the
+// double-buffered column-sum exchange [2][G][8][128] floats and its item
+// table (y2 offset, valid columns).
+struct TiledSmem {
+    size_t bars, scl, y2, off, cnt, total;
+};
+
+HOSCF_HD inline TiledSmem tiled_smem(int S, int G, int rows, int es, bool fp8) {
+    TiledSmem L;
+    size_t o = (size_t)8 * S * rows * 128 * es;
+    L.bars = o;
+    o += (size_t)8 * S * 8;
+    L.scl = o;
+    o += fp8 ? (size_t)8 * S * rows * 2 * 4 : 0;
+    o = (o + 15) & ~(size_t)15;
+    L.y2 = o;
+    o += (size_t)2 * G * 8 * 128 * 4;
+    L.off = o;
+    o += (size_t)2 * G * 8;
+    L.cnt = o;
+    o += (size_t)2 * G * 4;
+    L.total = o;
+    return L;
+}
 
 
 

@@ -87,14 +87,20 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
         p.bytes = off;
         return true;
     }
-    // rows per warp: the candidate whose tiles waste the fewest rows of A
+    // CTAs per SM (see TiledOcc): 2 for the narrow formats, which then get
+    // half the shared memory and at most 13 rows per warp.
+    const int occ = es == 4 ? 1 : 2;
+    // rows per warp: the candidate whose tiles waste the fewest rows of A,
+    // the taller tile on ties (fewer column partials, per-item work spread
+    // over more rows)
     {
         const int cand[3] = {8, 13, 16};
         int best = 8;
         double bw = 1e30;
         for (int r : cand) {
+            if (occ == 2 && r > 13) continue;
             const int64_t fa = 8 * r, ta = (s.A + fa - 1) / fa;
-            const double waste = (double)(ta * fa) / (double)s.A + (r == 8 ? 0.0 : 1e-3 * r);
+            const double waste = (double)(ta * fa) / (double)s.A - 1e-4 * r;
             if (waste < bw - 1e-9) {
                 bw = waste;
                 best = r;
@@ -111,22 +117,68 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
     // TMA needs 16-byte row and slab pitches and coordinates below 2^31.
     p.tma = tma_ok && (s.B * es) % 16 == 0 && s.O < (int64_t(1) << 31);
     p.vec = (s.B % 4) == 0;
-    int64_t grid = std::max<int64_t>(nsm, p.TT);
-    if (!p.tma) grid = std::max<int64_t>(grid, 4 * (int64_t)nsm);
+    // Work split.  Stream-K: CTA c takes items [c W, (c+1) W) of the
+    // tile-major item list, W <= O, so it meets at most two tiles.  Per tile:
+    // CTA c takes chunk c % P of tile c / P's outer indices, so the CTAs of
+    // the column tiles of one row band walk the same outer indices at the
+    // same time and share the DRAM lines where a row crosses from one
+    // column tile to the next.  Per tile is used when it finishes no later
+    // (in items per CTA times waves of resident CTAs) than stream-K.
+    const int64_t R = (int64_t)occ * nsm;
+    int64_t grid = std::max<int64_t>(R, p.TT);
     grid = std::min<int64_t>(grid, p.items);
     p.W = (p.items + grid - 1) / grid;
-    // W <= O keeps every CTA within two consecutive tiles.
     if (p.W > s.O) {
         p.W = s.O;
     }
     p.grid = (int)((p.items + p.W - 1) / p.W);
-    const size_t stage = (size_t)p.FA * p.FB * es;
-    if (p.tma) {
-        p.nstage = (int)std::min<size_t>(16, std::max<size_t>(2, (192 * 1024) / stage));
-        p.smem = 1024 + p.nstage * stage + 2 * p.nstage * 8 + 2 * 8 * p.FB * sizeof(float) + 64;
-    } else {
-        p.nstage = 0;
-        p.smem = 2 * 8 * p.FB * sizeof(float);
+    p.P = 0;
+    {
+        const int64_t sk_span = p.W * ((p.grid + R - 1) / R);
+        int64_t best_span = -1, best_P = 0, best_W = 0;
+        const int64_t pmax = std::min<int64_t>(s.O, 2 * R / p.TT + 1);
+        for (int64_t P = 1; P <= pmax; ++P) {
+            const int64_t W = (s.O + P - 1) / P;
+            const int64_t Pn = (s.O + W - 1) / W;   // no empty chunk
+            const int64_t span = W * ((p.TT * Pn + R - 1) / R);
+            if (best_span < 0 || span < best_span) {
+                best_span = span;
+                best_P = Pn;
+                best_W = W;
+            }
+        }
+        if (best_span >= 0 && best_span * 100 <= sk_span * 102 && p.TT * best_P < (int64_t(1) << 31)) {
+            p.P = best_P;
+            p.W = best_W;
+            p.grid = (int)(p.TT * best_P);
+        }
+    }
+    // Ring depth S (>= 3) and exchange group G: a group of up to 4 items
+    // first, then a deeper ring (up to 8), then a larger group.
+    {
+        const size_t cap = occ == 1 ? 227 * 1024 - 1024 : 112 * 1024;
+        const bool fp8 = dtype == HOSCF_F8E4M3;
+        int S = 0, G = 0, best = -1;
+        for (int g = 8; g >= 1; g /= 2) {
+            int sg = 16;
+            while (sg >= 3 && tiled_smem(sg, g, p.rows, es, fp8).total > cap) --sg;
+            if (sg < 3) continue;
+            const int score = std::min(g, 4) * 100 + std::min(sg, 8) * 10 + g;
+            if (score > best) {
+                best = score;
+                S = sg;
+                G = g;
+            }
+        }
+        if (G < 1) return false;
+        p.group = G;
+        if (p.tma || p.vec) {
+            p.nstage = S;
+            p.smem = 1024 + tiled_smem(S, G, p.rows, es, fp8).total;
+        } else {
+            p.nstage = 0;
+            p.smem = 1024 + tiled_smem(0, G, p.rows, es, fp8).total;
+        }
     }
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -142,6 +194,7 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
         p.off_y1 = take(sizeof(float) * (size_t)s.O * s.A);
         p.off_y2 = take(sizeof(float) * (size_t)s.O * s.B);
         p.off_r = take(sizeof(float) * (size_t)s.O);
+        p.off_wx = take(sizeof(float) * (size_t)s.D * s.O);
     }
     p.bytes = off;
     return true;
@@ -183,6 +236,9 @@ struct TiledArgs {
     int* err;
     uint64_t timeout_ns;
     const float* scales;   // FP8 only: one per 128 flat elements
+    int nstage;            // ring slots per warp
+    int group;             // items per column-sum exchange
+    int64_t P;             // outer-index chunks per tile (0: stream-K split)
 };
 
 // Reduce-scatter of NV per-lane row partials over the 32 lanes; returns the
@@ -237,11 +293,6 @@ __device__ __forceinline__ void load4_smem(const E* row, int col, float (&v)[4])
 }
 
 template <typename E>
-__device__ __forceinline__ void load4_global_vec(const E* p, float (&v)[4]) {
-    unpack4(__ldcs(reinterpret_cast<const typename Pack4<E>::T*>(p)), v);
-}
-
-template <typename E>
 __device__ __forceinline__ float load1_global(const E* p);
 template <>
 __device__ __forceinline__ float load1_global<float>(const float* p) { return __ldcs(p); }
@@ -279,76 +330,138 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     return *reinterpret_cast<const float2*>(&d);
 }
 
-// How the consumer warps get their tile rows.
-enum LoadMode : int { LOAD_TMA = 0, LOAD_VEC = 1, LOAD_SCALAR = 2 };
+// How each warp gets its tile rows.
+enum LoadMode : int { LOAD_TMA = 0, LOAD_ASYNC = 1, LOAD_SCALAR = 2 };
 
-// The streaming kernel.  Threads 0..255 are 8 consumer warps; with TMA a
-// ninth warp issues the bulk tensor copies.  Consumer warp w owns rows
-// [w*ROWS, (w+1)*ROWS) of the FA x 128 tile, lane l owns columns 4l..4l+3.
-// Without TMA the consumers load their own rows (16-byte vector loads when
-// rows are aligned, else element by element).
+// CTAs per SM of the streaming kernel: one for FP32 (HBM-bound with 8 warps),
+// two for the narrow formats, whose per-element instruction count needs
+// more warps in flight to keep up with HBM.
+template <typename E>
+struct TiledOcc {
+    static constexpr int value = sizeof(E) == 4 ? 1 : 2;
+};
+
+// The streaming kernel: 8 warps, warp w owns rows [w*ROWS, (w+1)*ROWS) of
+// the FA x 128 face tile and lane l its columns 4l..4l+3.  Every warp runs
+// its own ring of S slots (its rows of one item each): a TMA box of ROWS x
+// 128 issued by lane 0, or per-lane cp.async of the lane's four elements;
+// FP8 group scales ride along as per-lane cp.async.  One mbarrier per slot
+// tracks both, so warps proceed independently; they meet only every G items
+// to sum their column partials (double-buffered, one barrier per group).
+// LOAD_SCALAR (rows not a multiple of 4 elements) reads global memory
+// directly, element by element.  Items of a CTA are consecutive outer
+// indices of at most two tiles, so per-item offsets advance by constant
+// strides and are recomputed only when the tile changes.
 template <typename E, int MODE, int ROWS>
-__global__ void __launch_bounds__(MODE == LOAD_TMA ? 288 : 256, 1)
-    ttvc_tiled_kernel(const __grid_constant__ CUtensorMap tmap, const TiledArgs a, int nstage) {
-    constexpr bool TMA = MODE == LOAD_TMA;
+__global__ void __launch_bounds__(256, TiledOcc<E>::value)
+    ttvc_tiled_kernel(const __grid_constant__ CUtensorMap tmap, const TiledArgs a) {
     constexpr int FA = 8 * ROWS;
     constexpr int FB = 128;
-    constexpr int STAGE = FA * FB;   // elements
+    constexpr int SLOT = ROWS * FB;   // elements of one warp slot
+    constexpr bool F8 = std::is_same<E, fp8_t>::value;
+    constexpr bool RING = MODE != LOAD_SCALAR;
+    constexpr bool CPA = MODE == LOAD_ASYNC || (F8 && RING);   // lanes issue cp.async
+    using P4 = typename Pack4<E>::T;
+    const int S = RING ? a.nstage : 0;
+    const int G = a.group;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~uintptr_t(1023));
-    E* stages = reinterpret_cast<E*>(smem);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (TMA ? (size_t)nstage * STAGE * sizeof(E) : 0));
-    uint64_t* empty = full + (TMA ? nstage : 0);
-    float* s_y2 = reinterpret_cast<float*>(empty + (TMA ? nstage : 0));   // [2][8][FB]
+    const TiledSmem L = tiled_smem(S, G, ROWS, (int)sizeof(E), F8);
+    float* s_y2 = reinterpret_cast<float*>(smem + L.y2);          // [2][G][8][FB]
+    int64_t* s_off = reinterpret_cast<int64_t*>(smem + L.off);    // [2][G]
+    int* s_cnt = reinterpret_cast<int*>(smem + L.cnt);            // [2][G]
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int64_t c = blockIdx.x;
-    const int64_t i0 = c * a.W;
-    const int64_t i1 = min(i0 + a.W, a.items);
+    int64_t i0, i1;
+    if (a.P > 0) {
+        const int64_t t = c / a.P, o0 = (c - t * a.P) * a.W;
+        i0 = t * a.O + o0;
+        i1 = t * a.O + min(o0 + a.W, a.O);
+    } else {
+        i0 = c * a.W;
+        i1 = min(i0 + a.W, a.items);
+    }
     if (i0 >= i1) return;
-    const int64_t nloc = i1 - i0;
+    const int nloc = (int)(i1 - i0);   // W <= O < 2^31
+    const int64_t AB = a.A * a.B;
 
-    if (TMA) {
-        if (tid == 0) {
-            for (int s = 0; s < nstage; ++s) {
-                mbar_init(&full[s], 1);
-                mbar_init(&empty[s], 8);
-            }
+    E* ring = reinterpret_cast<E*>(smem) + (size_t)warp * S * SLOT;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars) + warp * S;
+    float* sscl = reinterpret_cast<float*>(smem + L.scl) + (size_t)warp * S * ROWS * 2;
+    if (RING) {
+        if (lane == 0) {
+            for (int q = 0; q < S; ++q)
+                mbar_init(&full[q], (MODE == LOAD_TMA ? 1u : 0u) + (CPA ? 32u : 0u));
             fence_mbar_init();
         }
-        __syncthreads();
-        if (warp == 8) {
-            if (lane == 0) {
-                prefetch_tmap(&tmap);
-                for (int64_t k = 0; k < nloc; ++k) {
-                    const int64_t item = i0 + k;
-                    const int64_t t = item / a.O;
-                    const int64_t o = item - t * a.O;
-                    const int s = (int)(k % nstage);
-                    if (k >= nstage) {
-                        const uint32_t par = (uint32_t)(((k / nstage) - 1) & 1);
-                        if (!mbar_wait_bounded(&empty[s], par, a.timeout_ns)) {
-                            atomicCAS(a.err, 0, (int)DEV_TIMEOUT);
-                            break;
-                        }
-                    }
-                    mbar_arrive_expect_tx(&full[s], STAGE * sizeof(E));
-                    tma_load_3d(stages + (size_t)s * STAGE, &tmap, (int)((t % a.TB) * FB),
-                                (int)((t / a.TB) * FA), (int)o, &full[s]);
-                }
-            }
-            return;
-        }
+        __syncwarp();
     }
 
+    // ---- issue side: item position and the flat offset of its first element
+    int64_t ii_o, ii_t, ii_ta, ii_tb, ii_flat;   // flat = (o*A + ar0)*B + tb*FB
+    auto ii_tile = [&]() {
+        ii_ta = ii_t / a.TB;
+        ii_tb = ii_t - ii_ta * a.TB;
+        ii_flat = (ii_o * a.A + ii_ta * FA + warp * ROWS) * a.B + ii_tb * FB;
+    };
+    ii_t = i0 / a.O;
+    ii_o = i0 - ii_t * a.O;
+    ii_tile();
+    auto ii_next = [&]() {
+        if (++ii_o == a.O) {
+            ii_o = 0;
+            ++ii_t;
+            ii_tile();
+        } else {
+            ii_flat += AB;
+        }
+    };
+    auto issue = [&](int slot) {
+        const int64_t ar0 = ii_ta * FA + warp * ROWS;
+        if (MODE == LOAD_TMA) {
+            if (lane == 0) {
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&full[slot], SLOT * sizeof(E));
+                tma_load_3d(ring + (size_t)slot * SLOT, &tmap, (int)(ii_tb * FB), (int)ar0,
+                            (int)ii_o, &full[slot]);
+            }
+        } else {
+            const bool colok = ii_tb * FB + 4 * lane < a.B;
+            const E* rowp = reinterpret_cast<const E*>(a.T) + ii_flat + 4 * lane;
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const bool ok = colok && ar0 + r < a.A;
+                cp_async<(int)sizeof(P4)>(ring + (size_t)slot * SLOT + r * FB + 4 * lane,
+                                          ok ? (const void*)(rowp + r * a.B) : a.T, ok);
+            }
+        }
+        if (F8) {
+            // scales of the first and last 128-element group each row window touches
+            if (lane < 2 * ROWS) {
+                const int r = lane >> 1;
+                const bool ok = ar0 + r < a.A;
+                const int64_t last = min(ii_tb * FB + FB, a.B) - 1 - ii_tb * FB;
+                const int64_t g = (ii_flat + r * a.B + ((lane & 1) ? last : 0)) >> 7;
+                cp_async<4>(sscl + ((size_t)slot * ROWS + r) * 2 + (lane & 1),
+                            ok ? (const void*)(a.scales + g) : (const void*)a.scales, ok);
+            }
+        }
+        if (CPA) cp_async_arrive_noinc(&full[slot]);
+    };
+
+    // ---- consume side
     float2 acc[ROWS][2];
     float2 uB2[2];
     float uAr[ROWS];
-    int64_t cur_t = -1;
-    int64_t ta = 0, tb = 0;
     const int64_t t_first = i0 / a.O;
+    int64_t cc_o = i0 - t_first * a.O, cc_t = t_first - 1;   // tile set up on first item
+    int64_t ar0 = 0, b0 = 0, y2off = 0, sflat = 0;
+    const float* wp = a.w + cc_o;
+    float* y1p = nullptr;
+    int ncol = 0;
 
     auto flush = [&](int64_t t) {
         const int seg = (int)(t - t_first);
@@ -359,73 +472,92 @@ __global__ void __launch_bounds__(MODE == LOAD_TMA ? 288 : 256, 1)
             *reinterpret_cast<float4*>(dst + (size_t)(warp * ROWS + r) * FB + 4 * lane) = q;
         }
     };
+    auto new_tile = [&](int64_t t) {
+        const int64_t ta = t / a.TB, tb = t - (t / a.TB) * a.TB;
+        ar0 = ta * FA + warp * ROWS;
+        b0 = tb * FB + 4 * lane;
+        y1p = a.y1p + (tb * a.O + cc_o) * a.A + ar0;
+        y2off = (ta * a.O + cc_o) * a.B + tb * FB;
+        sflat = (cc_o * a.A + ar0) * a.B + tb * FB;
+        ncol = (int)min((int64_t)FB, a.B - tb * FB);
+        float ub[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ub[q] = b0 + q < a.B ? a.uB[b0 + q] : 0.f;
+        uB2[0] = make_float2(ub[0], ub[1]);
+        uB2[1] = make_float2(ub[2], ub[3]);
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            uAr[r] = ar0 + r < a.A ? a.uA[ar0 + r] : 0.f;
+            acc[r][0] = make_float2(0.f, 0.f);
+            acc[r][1] = make_float2(0.f, 0.f);
+        }
+    };
+
+    // prologue: the first S-1 items in flight
+    int si = 0;      // slot of the next issue
+    int nis = 0;     // items issued
+    if (RING) {
+        for (; nis < S - 1 && nis < nloc; ++nis) {
+            issue(si);
+            ii_next();
+            si = si + 1 == S ? 0 : si + 1;
+        }
+    }
 
     bool ok = true;
-    for (int64_t k = 0; k < nloc; ++k) {
-        const int64_t item = i0 + k;
-        const int64_t t = item / a.O;
-        const int64_t o = item - t * a.O;
-        if (t != cur_t) {
-            if (cur_t >= 0) flush(cur_t);
-            cur_t = t;
-            ta = t / a.TB;
-            tb = t - ta * a.TB;
-            float ub[4];
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const int64_t b = tb * FB + 4 * lane + cc;
-                ub[cc] = b < a.B ? a.uB[b] : 0.f;
-            }
-            uB2[0] = make_float2(ub[0], ub[1]);
-            uB2[1] = make_float2(ub[2], ub[3]);
-#pragma unroll
-            for (int r = 0; r < ROWS; ++r) {
-                const int64_t ar = ta * FA + warp * ROWS + r;
-                uAr[r] = ar < a.A ? a.uA[ar] : 0.f;
-                acc[r][0] = make_float2(0.f, 0.f);
-                acc[r][1] = make_float2(0.f, 0.f);
-            }
+    int kfail = nloc;
+    int cs = 0;          // slot being consumed
+    uint32_t cph = 0;    // its phase parity
+    int gbuf = 0, gj = 0;
+    for (int k = 0; k < nloc; ++k) {
+        if (RING && ok && nis < nloc) {
+            issue(si);
+            ii_next();
+            si = si + 1 == S ? 0 : si + 1;
+            ++nis;
         }
-        const float wo = __ldg(a.w + o);
+        if (k == 0 || cc_o == 0) {
+            if (k > 0) flush(cc_t);
+            ++cc_t;
+            new_tile(cc_t);
+        }
+        const float wo = __ldg(wp);
         const float2 wo2 = make_float2(wo, wo);
         constexpr int RP = ROWS <= 8 ? 8 : (ROWS <= 16 ? 16 : 32);
         float y1[RP];
 #pragma unroll
         for (int r = ROWS; r < RP; ++r) y1[r] = 0.f;
         float2 y2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        const int s = TMA ? (int)(k % nstage) : 0;
-        if (TMA) {
-            const uint32_t par = (uint32_t)((k / nstage) & 1);
-            if (ok && !mbar_wait_bounded(&full[s], par, a.timeout_ns)) {
-                atomicCAS(a.err, 0, (int)DEV_TIMEOUT);
-                ok = false;
-            }
+        if (RING && ok && !mbar_wait_bounded(&full[cs], cph, a.timeout_ns)) {
+            atomicCAS(a.err, 0, (int)DEV_TIMEOUT);
+            ok = false;
+            kfail = k;
         }
+        // FP8: offset of the row window's first column within its scale group
+        int g_lo = F8 && RING ? (int)(sflat & 127) : 0;
+        const int g_step = (int)(a.B & 127);
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
             float v[4];
-            const int64_t ar = ta * FA + warp * ROWS + r;
-            const int64_t b0 = tb * FB + 4 * lane;
-            if (TMA) {
-                load4_smem<E>(stages + (size_t)s * STAGE + (size_t)(warp * ROWS + r) * FB,
-                              4 * lane, v);
-            } else if (MODE == LOAD_VEC) {
-                const E* rowp = reinterpret_cast<const E*>(a.T) + ((size_t)o * a.A + ar) * a.B;
-                if (ar < a.A && b0 < a.B) {
-                    load4_global_vec<E>(rowp + b0, v);   // B % 4 == 0: all four in range
-                } else {
-                    v[0] = v[1] = v[2] = v[3] = 0.f;
+            if (RING) {
+                unpack4(*reinterpret_cast<const P4*>(ring + (size_t)cs * SLOT + r * FB + 4 * lane), v);
+                if (F8) {
+                    const float* sp = sscl + ((size_t)cs * ROWS + r) * 2;
+                    const float sc = ((g_lo + 4 * lane) & ~127) ? sp[1] : sp[0];
+                    g_lo = (g_lo + g_step) & 127;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v[q] *= sc;
                 }
             } else {
-                const E* rowp = reinterpret_cast<const E*>(a.T) + ((size_t)o * a.A + ar) * a.B;
+                const int64_t ar = ar0 + r;
+                const E* rowp = reinterpret_cast<const E*>(a.T) + (cc_o * a.A + ar) * a.B;
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    const int64_t b = b0 + cc;
-                    v[cc] = (ar < a.A && b < a.B) ? load1_global<E>(rowp + b) : 0.f;
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t b = b0 + q;
+                    v[q] = (ar < a.A && b < a.B) ? load1_global<E>(rowp + b) : 0.f;
                 }
+                if (F8 && ar < a.A && b0 < a.B) apply_scales(a.scales, (cc_o * a.A + ar) * a.B + b0, v);
             }
-            if (std::is_same<E, fp8_t>::value && ar < a.A && b0 < a.B)
-                apply_scales(a.scales, ((int64_t)o * a.A + ar) * a.B + b0, v);
             const float2 v0 = make_float2(v[0], v[1]), v1 = make_float2(v[2], v[3]);
             acc[r][0] = ffma2(wo2, v0, acc[r][0]);
             acc[r][1] = ffma2(wo2, v1, acc[r][1]);
@@ -435,55 +567,80 @@ __global__ void __launch_bounds__(MODE == LOAD_TMA ? 288 : 256, 1)
             const float2 dd = ffma2(v1, uB2[1], make_float2(v0.x * uB2[0].x, v0.y * uB2[0].y));
             y1[r] = dd.x + dd.y;
         }
-        if (TMA) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
+        if (RING) {
+            __syncwarp();   // every lane is done with slot cs before it is refilled
+            if (++cs == S) {
+                cs = 0;
+                cph ^= 1u;
+            }
         }
         // row sums -> y1 partial of this b-tile
         int row;
         const float ys = rs_reduce<RP>(y1, lane, row);
-        if ((lane & ((32 / RP) - 1)) == 0 && row < ROWS) {
-            const int64_t ar = ta * FA + warp * ROWS + row;
-            if (ar < a.A) a.y1p[((size_t)tb * a.O + o) * a.A + ar] = ys;
+        if ((lane & ((32 / RP) - 1)) == 0 && row < ROWS && ar0 + row < a.A) y1p[row] = ys;
+        // column partials -> exchange ring; summed over the 8 warps every G items
+        float* sy = s_y2 + ((size_t)(gbuf * G + gj) * 8 + warp) * FB;
+        *reinterpret_cast<float4*>(sy + 4 * lane) = make_float4(y2[0].x, y2[0].y, y2[1].x, y2[1].y);
+        if (tid == 0) {
+            s_off[gbuf * G + gj] = y2off;
+            s_cnt[gbuf * G + gj] = ncol;
         }
-        // column sums over the 8 warps -> y2 partial of this a-tile
-        float* sy = s_y2 + (size_t)(k & 1) * 8 * FB;
-        *reinterpret_cast<float4*>(sy + warp * FB + 4 * lane) = make_float4(y2[0].x, y2[0].y, y2[1].x, y2[1].y);
-        asm volatile("bar.sync 1, 256;" ::: "memory");
-        if (tid < FB) {
-            float sum = 0.f;
+        if (gj == G - 1 || k == nloc - 1) {
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            const float* gb = s_y2 + (size_t)gbuf * G * 8 * FB;
+            const int n = (gj + 1) * FB;
+            for (int e = tid; e < n; e += 256) {
+                const int jj = e >> 7, b = e & (FB - 1);
+                if (b < s_cnt[gbuf * G + jj]) {
+                    float sum = 0.f;
 #pragma unroll
-            for (int w8 = 0; w8 < 8; ++w8) sum += sy[w8 * FB + tid];
-            const int64_t b = tb * FB + tid;
-            if (b < a.B) a.y2p[((size_t)ta * a.O + o) * a.B + b] = sum;
+                    for (int w8 = 0; w8 < 8; ++w8) sum += gb[((size_t)jj * 8 + w8) * FB + b];
+                    a.y2p[s_off[gbuf * G + jj] + b] = sum;
+                }
+            }
+            gbuf ^= 1;
+            gj = 0;
+        } else {
+            ++gj;
+        }
+        // next outer index
+        ++wp;
+        y1p += a.A;
+        y2off += a.B;
+        sflat += AB;
+        if (++cc_o == a.O) {
+            cc_o = 0;
+            wp = a.w;
         }
     }
-    if (cur_t >= 0) flush(cur_t);
-    if (TMA && !ok) {
-        // a wait gave up: let copies already issued land before the CTA exits
-        for (int64_t k = (nloc > nstage ? nloc - nstage : 0); k < nloc; ++k)
-            mbar_wait_bounded(&full[k % nstage], (uint32_t)((k / nstage) & 1), a.timeout_ns);
+    flush(cc_t);
+    if (RING && !ok) {
+        // a wait gave up: let every copy already issued land before the CTA exits
+        for (int k = kfail; k < nis; ++k)
+            mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1), a.timeout_ns);
     }
 }
 
 // H_{D,D+1}[a][b] = sum of the face partials of every CTA that touched the
 // tile, in CTA order.
+// CTA (tile t, row rr) sums each column thread's face partials over the CTAs
+// whose item ranges meet tile t, in CTA order.  Per-tile split: CTAs t P ..
+// t P + P - 1.  Stream-K: only the first of them can have started in tile
+// t-1 (its partial sits in segment 1).
 __global__ void reduce_face_kernel(const float* __restrict__ hp, float* __restrict__ out,
                                    int64_t A, int64_t B, int FA, int FB, int64_t TB, int64_t O,
-                                   int64_t W) {
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < A * B;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t aa = idx / B, bb = idx - (idx / B) * B;
-        const int64_t ta = aa / FA, tb = bb / FB;
-        const int64_t t = ta * TB + tb;
-        const int64_t c_lo = (t * O) / W, c_hi = ((t + 1) * O - 1) / W;
-        float s = 0.f;
-        for (int64_t c = c_lo; c <= c_hi; ++c) {
-            const int64_t seg = t - (c * W) / O;
-            s += hp[((size_t)(c * 2 + seg) * FA + (aa - ta * FA)) * FB + (bb - tb * FB)];
-        }
-        out[idx] = s;
-    }
+                                   int64_t W, int64_t P) {
+    const int64_t t = blockIdx.x;
+    const int rr = blockIdx.y;
+    const int64_t ta = t / TB, tb = t - (t / TB) * TB;
+    const int64_t aa = ta * FA + rr, bb = tb * FB + threadIdx.x;
+    if (aa >= A || threadIdx.x >= FB || bb >= B) return;
+    const int64_t c_lo = P > 0 ? t * P : (t * O) / W;
+    const int64_t c_hi = P > 0 ? t * P + P - 1 : ((t + 1) * O - 1) / W;
+    const size_t inner = (size_t)rr * FB + threadIdx.x;
+    float s = hp[((size_t)c_lo * 2 + (P == 0 && c_lo * W < t * O ? 1 : 0)) * FA * FB + inner];
+    for (int64_t c = c_lo + 1; c <= c_hi; ++c) s += hp[(size_t)c * 2 * FA * FB + inner];
+    out[aa * B + bb] = s;
 }
 
 // out[i] = sum_{p < np} part[p * stride + i]
@@ -497,15 +654,36 @@ __global__ void reduce_parts_kernel(const float* __restrict__ part, float* __res
     }
 }
 
-// Cross blocks H_{m,face}[i][col] = sum_{o: o_m = i} prod_{k!=m} u_k[o_k] y[o][col]
-// for every outer mode m; one CTA row per (m, i), columns over threads.
+// wx[m][o] = prod_{k != m} u_k[o_k]: the outer weight of o without mode m.
+__global__ void outer_weights_excl_kernel(const float* __restrict__ u, OuterInfo oi, int64_t O,
+                                          float* __restrict__ wx) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < O;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        float f[kMaxOrder];
+        for (int k = 0; k < oi.D; ++k) f[k] = u[oi.uoff[k] + outer_digit(oi, o, k)];
+        for (int m = 0; m < oi.D; ++m) {
+            float p = 1.f;
+            for (int k = 0; k < oi.D; ++k)
+                if (k != m) p *= f[k];
+            wx[m * O + o] = p;
+        }
+    }
+}
+
+// Cross blocks H_{m,face}[i][col] = sum_{o: o_m = i} wx[m][o] y[o][col] for
+// every outer mode m.  The outer indices with o_m = i are, in increasing
+// order, o(q) = (q / st_m) * I_m st_m + i st_m + q % st_m for q < O / I_m.
+// CTA (m, i, 32-column chunk): warp w sums a contiguous range of q with four
+// independent accumulators; the 8 warp sums are added in warp order.
 struct ModeOffs {
     int64_t off[kMaxOrder];
 };
 
-__global__ void fold_cross_kernel(const float* __restrict__ y, int64_t C, const float* __restrict__ u,
-                                  OuterInfo oi, int64_t O, float* __restrict__ H,
-                                  const ModeOffs row_block_off) {
+__global__ void __launch_bounds__(256) fold_cross_kernel(const float* __restrict__ y, int64_t C,
+                                                         const float* __restrict__ wx, OuterInfo oi,
+                                                         int64_t O, float* __restrict__ H,
+                                                         const ModeOffs row_block_off) {
+    __shared__ float part[8][32];
     // blockIdx.x enumerates (m, i) rows: rows of mode m start at sum_{k<m} I_k
     int m = 0;
     int64_t row = blockIdx.x;
@@ -514,22 +692,54 @@ __global__ void fold_cross_kernel(const float* __restrict__ y, int64_t C, const 
         ++m;
     }
     const int i = (int)row;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t Im = oi.dims[m];
     const int64_t stm = oi.st[m];
-    const int64_t pre = O / (Im * stm);
-    const int64_t col = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
-    if (col >= C) return;
-    float acc = 0.f;
-    for (int64_t p = 0; p < pre; ++p) {
-        for (int64_t s = 0; s < stm; ++s) {
-            const int64_t o = (p * Im + i) * stm + s;
-            float pi = 1.f;
-            for (int k = 0; k < oi.D; ++k)
-                if (k != m) pi *= __ldg(u + oi.uoff[k] + outer_digit(oi, o, k));
-            acc = fmaf(pi, __ldg(y + o * C + col), acc);
+    const int64_t Q = O / Im;
+    const int64_t col = blockIdx.y * 32 + lane;
+    const bool colok = col < C;
+    const float* wm = wx + m * O;
+    const int64_t q0 = (Q * warp) / 8, q1 = (Q * (warp + 1)) / 8;
+    int64_t s = q0 % stm;
+    int64_t o = (q0 / stm) * Im * stm + i * stm + s;
+    const int64_t jump = (Im - 1) * stm;   // from the end of one st_m run to the next
+    auto step = [&]() {
+        ++o;
+        if (++s == stm) {
+            s = 0;
+            o += jump;
         }
+    };
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int64_t q = q0;
+    for (; q + 4 <= q1; q += 4) {
+        int64_t oo[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            oo[k] = o;
+            step();
+        }
+        float yv[4], wv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            yv[k] = colok ? __ldg(y + oo[k] * C + col) : 0.f;
+            wv[k] = __ldg(wm + oo[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] = fmaf(wv[k], yv[k], acc[k]);
     }
-    H[row_block_off.off[m] + (int64_t)i * C + col] = acc;
+    for (; q < q1; ++q) {
+        acc[0] = fmaf(__ldg(wm + o), colok ? __ldg(y + o * C + col) : 0.f, acc[0]);
+        step();
+    }
+    part[warp][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    __syncthreads();
+    if (warp == 0 && colok) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += part[w][lane];
+        H[row_block_off.off[m] + (int64_t)i * C + col] = t;
+    }
 }
 
 // r[o] = sum_a y1[o][a] uA[a]   (one warp per o)
@@ -640,27 +850,31 @@ template <typename E, int MODE, int ROWS>
 static cudaError_t launch_tiled_k(const PassPlan& p, const CUtensorMap& map, const TiledArgs& a,
                                   cudaStream_t st) {
     auto kern = ttvc_tiled_kernel<E, MODE, ROWS>;
-    const size_t smem = MODE == LOAD_TMA ? p.smem : (size_t)2 * 8 * 128 * sizeof(float);
+    const size_t smem = 1024 + tiled_smem(MODE == LOAD_SCALAR ? 0 : p.nstage, p.group, ROWS,
+                                          (int)sizeof(E), std::is_same<E, fp8_t>::value)
+                                   .total;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<p.grid, MODE == LOAD_TMA ? 288 : 256, smem, st>>>(map, a, p.nstage);
+    kern<<<p.grid, 256, smem, st>>>(map, a);
     return cudaGetLastError();
 }
 
 template <typename E, int MODE>
 static cudaError_t launch_tiled_rows(const PassPlan& p, const CUtensorMap& map, const TiledArgs& a,
                                      cudaStream_t st) {
-    if (MODE == LOAD_SCALAR || p.rows == 8) return launch_tiled_k<E, MODE, 8>(p, map, a, st);
-    if (p.rows == 13) return launch_tiled_k<E, MODE, 13>(p, map, a, st);
-    return launch_tiled_k<E, MODE, 16>(p, map, a, st);
+    if (p.rows == 8) return launch_tiled_k<E, MODE, 8>(p, map, a, st);
+    if constexpr (TiledOcc<E>::value == 1) {
+        if (p.rows == 16) return launch_tiled_k<E, MODE, 16>(p, map, a, st);
+    }
+    return launch_tiled_k<E, MODE, 13>(p, map, a, st);
 }
 
 template <typename E>
 static cudaError_t launch_tiled(const PassPlan& p, int mode, const CUtensorMap& map,
                                 const TiledArgs& a, cudaStream_t st) {
     if (mode == LOAD_TMA) return launch_tiled_rows<E, LOAD_TMA>(p, map, a, st);
-    if (mode == LOAD_VEC) return launch_tiled_rows<E, LOAD_VEC>(p, map, a, st);
+    if (mode == LOAD_ASYNC) return launch_tiled_rows<E, LOAD_ASYNC>(p, map, a, st);
     return launch_tiled_rows<E, LOAD_SCALAR>(p, map, a, st);
 }
 
@@ -732,6 +946,9 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
     a.err = dev_err;
     a.timeout_ns = timeout_ns;
     a.scales = scales;
+    a.nstage = p.nstage;
+    a.group = p.group;
+    a.P = p.P;
 
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
@@ -741,19 +958,25 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         const int es = elem_size(dtype);
         cuuint64_t gdim[3] = {(cuuint64_t)s.B, (cuuint64_t)s.A, (cuuint64_t)s.O};
         cuuint64_t gstr[2] = {(cuuint64_t)(s.B * es), (cuuint64_t)(s.A * s.B * es)};
-        cuuint32_t box[3] = {(cuuint32_t)p.FB, (cuuint32_t)p.FA, 1};
+        cuuint32_t box[3] = {(cuuint32_t)p.FB, (cuuint32_t)p.rows, 1};   // one warp's rows
         cuuint32_t estr[3] = {1, 1, 1};
+        // Promote L2 fetches to 256 B only when rows start on 256-byte lines;
+        // otherwise every row window would drag in a partial line twice.
+        const int64_t pitch = s.B * es;
+        const CUtensorMapL2promotion prom = pitch % 256 == 0   ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+                                            : pitch % 128 == 0 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                                               : CU_TENSOR_MAP_L2_PROMOTION_NONE;
         CUtensorMapDataType dt = dtype == HOSCF_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : dtype == HOSCF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                        : CU_TENSOR_MAP_DATA_TYPE_UINT8;
         if (!enc || (reinterpret_cast<uintptr_t>(data) & 15) != 0 ||
             enc(&map, dt, 3, const_cast<void*>(data), gdim, gstr, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, prom,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             use_tma = false;
     }
     const int mode = use_tma ? LOAD_TMA
-                     : (p.vec && (reinterpret_cast<uintptr_t>(data) & 15) == 0) ? LOAD_VEC
+                     : (p.vec && (reinterpret_cast<uintptr_t>(data) & 15) == 0) ? LOAD_ASYNC
                                                                                 : LOAD_SCALAR;
     if (dtype == HOSCF_F32) {
         HOSCF_CK(launch_tiled<float>(p, mode, map, a, st));
@@ -764,8 +987,8 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
     }
     // face block (d-2, d-1)
     float* Hface = H + s.boff[block_index(s.d, s.d - 2, s.d - 1)];
-    reduce_face_kernel<<<grid_for(s.A * s.B, 256, 8192), 256, 0, st>>>(
-        a.hp, Hface, s.A, s.B, p.FA, p.FB, p.TB, s.O, p.W);
+    reduce_face_kernel<<<dim3((unsigned)p.TT, (unsigned)p.FA), p.FB, 0, st>>>(
+        a.hp, Hface, s.A, s.B, p.FA, p.FB, p.TB, s.O, p.W, p.P);
     HOSCF_CK(cudaGetLastError());
     if (s.d == 3) {
         // y1 = H_{0,1} (I_0 x A), y2 = H_{0,2} (I_0 x B)
@@ -793,10 +1016,12 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         off2.off[m] = s.boff[block_index(s.d, m, s.d - 1)];
     }
     {
-        dim3 g1((unsigned)rows, (unsigned)((s.A + 255) / 256));
-        fold_cross_kernel<<<g1, 256, 0, st>>>(y1, s.A, u, oi, s.O, H, off1);
-        dim3 g2((unsigned)rows, (unsigned)((s.B + 255) / 256));
-        fold_cross_kernel<<<g2, 256, 0, st>>>(y2, s.B, u, oi, s.O, H, off2);
+        float* wx = reinterpret_cast<float*>(ws + p.off_wx);
+        outer_weights_excl_kernel<<<grid_for(s.O, 256, 4096), 256, 0, st>>>(u, oi, s.O, wx);
+        dim3 g1((unsigned)rows, (unsigned)((s.A + 31) / 32));
+        fold_cross_kernel<<<g1, 256, 0, st>>>(y1, s.A, wx, oi, s.O, H, off1);
+        dim3 g2((unsigned)rows, (unsigned)((s.B + 31) / 32));
+        fold_cross_kernel<<<g2, 256, 0, st>>>(y2, s.B, wx, oi, s.O, H, off2);
         HOSCF_CK(cudaGetLastError());
     }
     if (s.D >= 2) {
