@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) leg")
     ap.add_argument("--dims", default=None,
                     help="comma-separated dims: same planted rank-5 recipe at another size")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"],
+                    help="storage format the timed pass reads (bf16 / fp8 e4m3 with one FP32 "
+                         "scale per 128 elements are quantized from the FP32 workload)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -139,6 +142,49 @@ def pass_bytes(dims, elem_bytes=4):
     n = sum(dims)
     P = sum(dims[m] * dims[k] for m in range(len(dims)) for k in range(m + 1, len(dims)))
     return N * elem_bytes + 4 * n + 4 * P
+
+
+def max_over_ranks(ms, dist=None, device=None):
+    """The timed region's milliseconds, MAX over the ranks of the process
+    group (each rank runs an independent replica of the step)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(nbytes, steps, world, ms):
+    """Whole-job throughput: every rank streamed `nbytes` per step."""
+    return nbytes * steps * world / (ms / 1e3) / 1e9
+
+
+def launches_per_step(dims):
+    """Kernels the library launches for one step (pass + eigen step).
+    Pass: d = 2 copies the matrix (1); a face A*B <= 1024 takes the
+    small-face path (kernel + reduce: 2, if its plan fits shared memory);
+    otherwise the streaming kernel and its reduction (2), plus for d >= 4
+    the outer weights, the per-mode weights, two cross folds (5) and, with
+    two or more outer modes, the pair folds (2).  Eigen step: Jr build +
+    Lanczos (2)."""
+    d = len(dims)
+    if d == 2:
+        npass = 1
+    elif dims[-1] * dims[-2] <= 1024:
+        npass = 2
+    else:
+        npass = 2 if d == 3 else 2 + 4 + (2 if d - 2 >= 2 else 0)
+    return npass + 2
+
+
+def traffic_bytes(dims, dtype):
+    """DRAM bytes (read + write) of one launch of the streaming kernel, from
+    an ncu capture of the same kernel build (dram__bytes_read.sum +
+    dram__bytes_write.sum; profiles/ttvc_tiled_fp32_1024cube.md); None for
+    workloads that capture does not cover."""
+    measured = {((1024, 1024, 1024), "f32"): 4295204608 + 80013824}
+    return measured.get((tuple(dims), dtype))
 
 
 # ------------------------------------------------------------------ CPU baseline
@@ -346,7 +392,15 @@ def run_ours(args, rank, world, local_rank):
     T, u0 = make_workload(args.workload, seed=rank, device=dev, dims=dims_arg)
     dims = tuple(T.shape)
     d = len(dims)
-    nb = pass_bytes(dims, T.element_size())
+    T32, scales = T, None
+    if args.dtype != "f32":
+        T, scales = P.hoscf_quantize(T32, args.dtype)
+        if args.no_extras:
+            del T32
+            T32 = None
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    nb = pass_bytes(dims, T.element_size()) + (scales.numel() * 4 if scales is not None else 0)
     stream = torch.cuda.current_stream()
     H = torch.empty(P.n_blocks(dims), device=dev, dtype=torch.float32)
 
@@ -369,7 +423,7 @@ def run_ours(args, rank, world, local_rank):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-        P.hoscf_ttvc_blocks(T, u, H)
+        P.hoscf_ttvc_blocks(T, u, H, scales=scales)
         if record:
             e1.record(stream)
             pass_ev.append((e0, e1))
@@ -389,23 +443,24 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    P.hoscf_profile_enable(local_rank, True)
     t_start.record(stream)
     for _ in range(args.steps):
         step(record=True)
     t_end.record(stream)
     torch.cuda.synchronize()
+    P.hoscf_profile_enable(local_rank, False)
+    n_kern, kern_ms = P.hoscf_profile_read(local_rank)
+    kern_avg = kern_ms / max(1, n_kern)
     if dist:
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
     clocks = clk.stop()
     pass_ms = [a.elapsed_time(b) for a, b in pass_ev]
     pass_avg = sum(pass_ms) / len(pass_ms)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
-    value = nb * args.steps * world / (ms / 1e3) / 1e9
+    value = whole_job_gbs(nb, args.steps, world, ms)
 
     # ---- end to end: tensor copied from pinned host memory every step
     e2e = None
@@ -421,47 +476,56 @@ def run_ours(args, rank, world, local_rank):
         e1 = torch.cuda.Event(enable_timing=True)
         k_e2e = max(1, min(args.steps, 3))
         e0.record(stream)
+        sc_host = scales.cpu().pin_memory() if scales is not None else None
+        sc_dev = torch.empty_like(scales) if scales is not None else None
         for _ in range(k_e2e):
             Td.copy_(host, non_blocking=True)
+            if sc_dev is not None:
+                sc_dev.copy_(sc_host, non_blocking=True)
             ue.copy_(u_host, non_blocking=True)
-            P.hoscf_ttvc_blocks(Td, ue, H)
+            P.hoscf_ttvc_blocks(Td, ue, H, scales=sc_dev)
             _, un, lam = P.hoscf_eig_step(dims, H, P.balanced(ue, dims))
             res_host.copy_(un, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = e0.elapsed_time(e1) / k_e2e
         e2e = {"value": nb / (ms_e2e / 1e3) / 1e9, "unit": "GB/s",
-               "h2d_bytes_per_step": T.numel() * T.element_size() + 4 * sum(dims),
+               "h2d_bytes_per_step": T.numel() * T.element_size() + 4 * sum(dims)
+                                     + (scales.numel() * 4 if scales is not None else 0),
                "d2h_bytes_per_step": 4 * sum(dims), "ms_per_step": ms_e2e, "steps": k_e2e}
         del host, Td
 
     extras = {}
     if not args.no_extras and rank == 0:
-        extras = run_extras(P, T, u0, dev)
+        extras = run_extras(P, T32, u0, dev)
     peak, peak_kind = load_peaks()
-    achieved = nb / (pass_avg / 1e3) / 1e9
+    achieved = nb / (kern_avg / 1e3) / 1e9
     if rank == 0:
         line = {
             "metric": "TTVc pass HBM GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if T.dtype == torch.float32 else str(T.dtype),
+            "dtype": {"f32": "f32", "bf16": "bf16", "fp8": "fp8e4m3+f32 scales"}[args.dtype],
             "data": "synthetic",
             "config": {"workload": args.workload if not args.dims else "planted rank-5 + 5% noise",
                        "dims": list(dims), "order": d,
                        "step": "one HOSCF iteration from the seeded x0: TTVc pass + reduce + "
                                "Lanczos eigen step + block normalisation",
-                       "l2": "inputs larger than L2 (4 GiB tensor), no flush",
+                       "l2": (f"inputs larger than L2 ({T.numel() * T.element_size() / 2**30:.2f} "
+                              "GiB tensor), no flush") if T.numel() * T.element_size() > 129e6
+                             else "tensor fits in L2: steps are not L2-flushed (not a headline)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "TTVc pass (streaming kernel + its reduce kernels), "
-                                   f"avg {pass_avg:.4f} ms over the timed steps",
+                         "frac": achieved / peak, "traffic": traffic_bytes(dims, args.dtype),
+                         "kernel": "TTVc streaming kernel (ttvc_tiled_kernel), avg "
+                                   f"{kern_avg:.4f} ms over {n_kern} timed launches (events "
+                                   "recorded by the library on the launch stream)",
                          "peak_kind": peak_kind},
             "pass_ms_avg": pass_avg,
+            "pass_GBs": nb / (pass_avg / 1e3) / 1e9,
             "e2e": e2e,
             "clocks": clocks,
-            "gpu_launches": args.steps * (4 + 2 if d == 3 else 8),
+            "gpu_launches": args.steps * launches_per_step(dims),
         }
         if extras:
             line["extras"] = extras

@@ -221,6 +221,42 @@ hoscf_status hoscf_quantize(hoscf_handle* h, const float* x, int64_t n, int dtyp
                             float* scales, void* stream);
 
 /*
+ * hoscf_profile_enable / hoscf_profile_read - a measurement aid with no
+ * counterpart in the paper: device time of the pass's streaming kernel alone
+ * (the tiled, small-face or copy kernel, without the partial-sum reductions
+ * that follow it), for roofline figures.
+ *   enable   nonzero: from now on every hoscf_ttvc_blocks call on this handle
+ *            records a CUDA event pair on its stream around that kernel
+ *            (the first 65536 calls; earlier records are discarded);
+ *            zero: stop recording (records are kept for reading).
+ *   count    host: number of recorded calls.
+ *   total_ms host: sum of their kernel durations in milliseconds; the call
+ *            waits for the recorded events to complete.
+ * Errors: EINVAL (NULL handle or pointer), ECUDA.
+ */
+hoscf_status hoscf_profile_enable(hoscf_handle* h, int enable);
+hoscf_status hoscf_profile_read(hoscf_handle* h, int* count, double* total_ms);
+
+/*
+ * hoscf_selftest_timeout - exercises the library's failure path for device
+ * waits (no counterpart in the paper).  Every spin-wait in the library's
+ * kernels is bounded; when a bound passes, the kernel records a timeout in
+ * the handle's device status word and returns, and the host call reports
+ * HOSCF_TIMEOUT.  This call runs such a wait on a condition nothing can
+ * satisfy, so the bound always passes:
+ *   kind 0   an mbarrier phase that no thread or copy completes (the wait
+ *            the streaming kernel uses for its TMA copies);
+ *   kind 1   the software grid barrier of the eigen step with one arrival
+ *            missing (2 CTAs).
+ *   timeout_ns   the bound, 1 .. 10^10.
+ * Synchronous; nothing else is in flight in these kernels, so the context
+ * stays usable.  Returns HOSCF_TIMEOUT when the failure was detected and
+ * reported (the expected outcome), EINVAL for bad arguments, ECUDA
+ * otherwise.
+ */
+hoscf_status hoscf_selftest_timeout(hoscf_handle* h, int kind, int64_t timeout_ns);
+
+/*
  * hoscf_ttvc_blocks_static - hoscf_ttvc_blocks without any allocation.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc - for example a plugin whose host application

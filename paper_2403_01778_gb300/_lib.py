@@ -25,7 +25,8 @@ MAX_ORDER = 8
 EXPORTS = ("hoscf_create", "hoscf_destroy", "hoscf_last_error", "hoscf_opts_default",
            "hoscf_workspace_size", "hoscf_ttvc_blocks", "hoscf_eig_step", "hoscf_solve",
            "hoscf_solve_batched", "hoscf_backward", "hoscf_quantize",
-           "hoscf_ttvc_blocks_static")
+           "hoscf_ttvc_blocks_static", "hoscf_profile_enable", "hoscf_profile_read",
+           "hoscf_selftest_timeout")
 
 
 class TensorDesc(ctypes.Structure):
@@ -82,6 +83,9 @@ def load():
     lib.hoscf_quantize.argtypes = [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_void_p,
                                    c_void_p]
     lib.hoscf_ttvc_blocks_static.argtypes = [P(TensorDesc), c_void_p, c_void_p, c_void_p]
+    lib.hoscf_profile_enable.argtypes = [c_void_p, c_int]
+    lib.hoscf_profile_read.argtypes = [c_void_p, P(c_int), P(c_double)]
+    lib.hoscf_selftest_timeout.argtypes = [c_void_p, c_int, c_int64]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name != "hoscf_last_error":

@@ -122,6 +122,30 @@ def hoscf_ttvc_blocks(T: torch.Tensor, u: torch.Tensor, H: torch.Tensor | None =
     return H
 
 
+def hoscf_profile_enable(device: int = 0, enable: bool = True) -> None:
+    """Start (clearing earlier records) or stop timing the pass's streaming
+    kernel in every hoscf_ttvc_blocks call on this device's handle."""
+    h = handle(device)
+    _check(_lib.load().hoscf_profile_enable(h, 1 if enable else 0), h)
+
+
+def hoscf_profile_read(device: int = 0) -> tuple[int, float]:
+    """(number of timed calls, total streaming-kernel milliseconds)."""
+    h = handle(device)
+    n, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(_lib.load().hoscf_profile_read(h, ctypes.byref(n), ctypes.byref(ms)), h)
+    return n.value, ms.value
+
+
+def hoscf_selftest_timeout(kind: int, timeout_ns: int = 1_000_000, device: int = 0) -> int:
+    """Run a bounded device wait that can never be satisfied (kind 0: an
+    mbarrier phase, 1: the grid barrier with an arrival missing) and return
+    the library's status for it (HOSCF_TIMEOUT = 6 when the failure path
+    works)."""
+    h = handle(device)
+    return int(_lib.load().hoscf_selftest_timeout(h, int(kind), int(timeout_ns)))
+
+
 def hoscf_ttvc_blocks_static(T: torch.Tensor, u: torch.Tensor, H: torch.Tensor | None = None,
                              stream=None) -> torch.Tensor:
     """hoscf_ttvc_blocks without allocation inside the library: scratch comes

@@ -24,6 +24,11 @@ struct hoscf_handle {
     void* pinned_big = nullptr;   // descriptor / result staging of the batched solve
     size_t pinned_big_bytes = 0;
     cudaStream_t own = nullptr;   // private stream (graph capture)
+    // measurement aid: events around the streaming kernel of each
+    // hoscf_ttvc_blocks call while enabled
+    bool prof_on = false;
+    size_t prof_n = 0;
+    std::vector<KernelEvents> prof;
     char msg[512] = {0};
 };
 
@@ -60,6 +65,8 @@ hoscf_status cuda_fail(hoscf_handle* h, cudaError_t e, const char* what) {
         cudaError_t _e = (call);                                   \
         if (_e != cudaSuccess) return cuda_fail(h, _e, #call);     \
     } while (0)
+
+constexpr size_t kProfMax = 65536;   // timed calls kept by the measurement aid
 
 // Fixed head of the workspace: device error word, grid barrier, scalars.
 constexpr size_t kHeadBytes = 4096;
@@ -222,6 +229,24 @@ hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const 
 }  // namespace
 
 // ====================================================================== ABI
+// Failure-path self-test kernels: waits that nothing can ever satisfy.
+__global__ void selftest_mbar_kernel(int* err, uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // no thread ever arrives on `bar` and no copy targets it
+    const bool got = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (!got && threadIdx.x == 0) atomicCAS(err, 0, (int)DEV_TIMEOUT);
+}
+
+__global__ void selftest_grid_kernel(unsigned* state, int* err, uint64_t limit_ns) {
+    // one arrival short of the count: the barrier can never open
+    grid_barrier(state, gridDim.x + 1, err, limit_ns);
+}
+
 extern "C" {
 
 hoscf_status hoscf_create(hoscf_handle** out, int device) {
@@ -257,6 +282,10 @@ hoscf_status hoscf_destroy(hoscf_handle* h) {
         if (h->h_pinned) cudaFreeHost(h->h_pinned);
         if (h->pinned_big) cudaFreeHost(h->pinned_big);
         if (h->own) cudaStreamDestroy(h->own);
+        for (KernelEvents& e : h->prof) {
+            cudaEventDestroy(e.begin);
+            cudaEventDestroy(e.end);
+        }
     }
     delete h;
     return HOSCF_OK;
@@ -275,7 +304,7 @@ hoscf_status hoscf_opts_default(hoscf_opts* o) {
     o->eig_adapt = 1e-3;
     o->refine = nullptr;
     o->switch_tol = 1e-3;
-    o->timeout_ns = 0;
+    o->timeout_ns = 2000000000;   // 2 s per bounded device wait
     o->batch_threads = 0;
     return HOSCF_OK;
 }
@@ -312,9 +341,41 @@ hoscf_status hoscf_ttvc_blocks(hoscf_handle* h, const hoscf_tensor_desc* T, cons
     if (st) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Err err;
+    const KernelEvents* kev = nullptr;
+    if (h->prof_on && h->prof_n < kProfMax) {
+        if (h->prof_n == h->prof.size()) {
+            KernelEvents e;
+            CK(cudaEventCreate(&e.begin));
+            CK(cudaEventCreate(&e.end));
+            h->prof.push_back(e);
+        }
+        kev = &h->prof[h->prof_n++];
+    }
     st = run_ttvc(L.s, L.pp, T->dtype, T->data, T->scales, u, H, h->ws + L.off_pass, dev_err(h),
-                  2000000000ull, s, err);
+                  2000000000ull, s, err, kev);
     if (st) return fail(h, st, "%s", err.msg);
+    return HOSCF_OK;
+}
+
+hoscf_status hoscf_profile_enable(hoscf_handle* h, int enable) {
+    if (!h) return HOSCF_EINVAL;
+    h->prof_on = enable != 0;
+    if (h->prof_on) h->prof_n = 0;
+    return HOSCF_OK;
+}
+
+hoscf_status hoscf_profile_read(hoscf_handle* h, int* count, double* total_ms) {
+    if (!h || !count || !total_ms) return HOSCF_EINVAL;
+    DeviceGuard g(h->device);
+    double tot = 0.0;
+    for (size_t i = 0; i < h->prof_n; ++i) {
+        float ms = 0.f;
+        CK(cudaEventSynchronize(h->prof[i].end));
+        CK(cudaEventElapsedTime(&ms, h->prof[i].begin, h->prof[i].end));
+        tot += ms;
+    }
+    *count = (int)h->prof_n;
+    *total_ms = tot;
     return HOSCF_OK;
 }
 
@@ -669,6 +730,35 @@ hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const f
     CK(launch_grad_write(S, u, aptr, grad_sigma, coef, grad_T, s));
     CK(cudaStreamSynchronize(s));
     return result;
+}
+
+hoscf_status hoscf_selftest_timeout(hoscf_handle* h, int kind, int64_t timeout_ns) {
+    if (!h || (kind != 0 && kind != 1) || timeout_ns <= 0 || timeout_ns > 10000000000ll)
+        return HOSCF_EINVAL;
+    DeviceGuard g(h->device);
+    const size_t need = kHeadBytes;
+    hoscf_status st = ensure_ws(h, need);
+    if (st) return st;
+    if (!h->own) CK(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
+    cudaStream_t s = h->own;
+    st = reset_dev_state(h, s);
+    if (st) return st;
+    if (kind == 0) {
+        selftest_mbar_kernel<<<1, 32, 0, s>>>(dev_err(h), (uint64_t)timeout_ns);
+    } else {
+        selftest_grid_kernel<<<2, 64, 0, s>>>(reinterpret_cast<unsigned*>(h->ws + kOffBar),
+                                             dev_err(h), (uint64_t)timeout_ns);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_pinned + 32, h->ws + kOffErr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int code;
+    memcpy(&code, h->h_pinned + 32, sizeof(int));
+    st = reset_dev_state(h, s);   // leave the barrier state clean for the next launch
+    if (st) return st;
+    CK(cudaStreamSynchronize(s));
+    if (code) return dev_status(h, code);
+    return fail(h, HOSCF_ECUDA, "self-test wait did not report its timeout");
 }
 
 hoscf_status hoscf_quantize(hoscf_handle* h, const float* x, int64_t n, int dtype, void* q,

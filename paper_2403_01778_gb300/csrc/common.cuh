@@ -87,6 +87,12 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid)
     }
 }
 
+// Wait until every cp.async this thread issued has landed (they always
+// complete: sources are valid addresses).
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // The barrier receives one arrival (counted in its init count) once every
 // cp.async this thread issued before has landed.
 __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {

@@ -8,10 +8,16 @@
 
 namespace hoscf {
 
+// A pair of events recorded around a pass's streaming kernel (measurement).
+struct KernelEvents {
+    cudaEvent_t begin = nullptr, end = nullptr;
+};
+
 // ttvc.cu
 hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* data,
                       const float* scales, const float* u, float* H, char* ws, int* dev_err,
-                      uint64_t timeout_ns, cudaStream_t st, Err& err);
+                      uint64_t timeout_ns, cudaStream_t st, Err& err,
+                      const KernelEvents* kev = nullptr);
 
 // batched.cu
 hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* const* u0,
@@ -31,7 +37,8 @@ cudaError_t launch_quantize(const float* x, int64_t n, int dtype, void* q, float
 
 // small.cu
 cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const void* data,
-                      const float* scales, const float* u, float* H, char* ws, cudaStream_t st);
+                      const float* scales, const float* u, float* H, char* ws, cudaStream_t st,
+                      const KernelEvents* kev = nullptr);
 
 // eig.cu
 struct LanczosLaunch {

@@ -60,6 +60,7 @@ struct PassPlan {
     int64_t TA = 1, TB = 1, TT = 1, items = 0, W = 0;
     int64_t P = 0;            // outer-index chunks per tile (0: stream-K split)
     int grid = 0;
+    int nsm = 0;              // SMs the plan was made for
     int nstage = 0;           // slots of each warp's load ring (0: direct loads)
     int group = 0;            // items per column-sum exchange
     size_t smem = 0;

@@ -351,7 +351,7 @@ bool make_small_plan(const Shape& s, int nsm, SmallPlanInfo& sp) {
 
 template <typename E>
 static cudaError_t launch_small_t(const Shape& s, const SmallPlanInfo& sp, const SmallArgs& a,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const KernelEvents* kev) {
     const int jf = small_jf((int)(s.A * s.B));
     void (*k)(const SmallArgs) = nullptr;
     switch (jf) {
@@ -364,12 +364,15 @@ static cudaError_t launch_small_t(const Shape& s, const SmallPlanInfo& sp, const
     }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
     if (e != cudaSuccess) return e;
+    if (kev) cudaEventRecord(kev->begin, st);
     k<<<sp.G, 256, sp.smem, st>>>(a);
+    if (kev) cudaEventRecord(kev->end, st);
     return cudaGetLastError();
 }
 
 cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const void* data,
-                      const float* scales, const float* u, float* H, char* ws, cudaStream_t st) {
+                      const float* scales, const float* u, float* H, char* ws, cudaStream_t st,
+                      const KernelEvents* kev) {
     SmallArgs a;
     memset(&a, 0, sizeof(a));
     a.T = data;
@@ -402,9 +405,9 @@ cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const 
     a.patch = reinterpret_cast<float*>(ws + sp.off_patch);
     a.cover = reinterpret_cast<int*>(ws + sp.off_cover);
     a.scales = scales;
-    cudaError_t e = dtype == HOSCF_F32    ? launch_small_t<float>(s, sp, a, st)
-                    : dtype == HOSCF_BF16 ? launch_small_t<bf16_t>(s, sp, a, st)
-                                          : launch_small_t<fp8_t>(s, sp, a, st);
+    cudaError_t e = dtype == HOSCF_F32    ? launch_small_t<float>(s, sp, a, st, kev)
+                    : dtype == HOSCF_BF16 ? launch_small_t<bf16_t>(s, sp, a, st, kev)
+                                          : launch_small_t<fp8_t>(s, sp, a, st, kev);
     if (e != cudaSuccess) return e;
     SmallReduceArgs r;
     memset(&r, 0, sizeof(r));

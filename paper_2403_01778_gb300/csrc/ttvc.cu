@@ -72,6 +72,7 @@ static int elem_size(int dtype) { return dtype == HOSCF_F32 ? 4 : (dtype == HOSC
 
 bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p) {
     p = PassPlan();
+    p.nsm = nsm;
     if (s.d == 2) {
         p.copy_only = true;
         return true;
@@ -528,10 +529,14 @@ __global__ void __launch_bounds__(256, TiledOcc<E>::value)
 #pragma unroll
         for (int r = ROWS; r < RP; ++r) y1[r] = 0.f;
         float2 y2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        if (RING && ok && !mbar_wait_bounded(&full[cs], cph, a.timeout_ns)) {
-            atomicCAS(a.err, 0, (int)DEV_TIMEOUT);
-            ok = false;
-            kfail = k;
+        if (RING && ok) {
+            // warp-uniform: once any lane gives up, the whole warp stops issuing
+            const bool got = mbar_wait_bounded(&full[cs], cph, a.timeout_ns);
+            if (!__all_sync(HOSCF_FULLMASK, got)) {
+                if (lane == 0) atomicCAS(a.err, 0, (int)DEV_TIMEOUT);
+                ok = false;
+                kfail = k;
+            }
         }
         // FP8: offset of the row window's first column within its scale group
         int g_lo = F8 && RING ? (int)(sflat & 127) : 0;
@@ -615,42 +620,71 @@ __global__ void __launch_bounds__(256, TiledOcc<E>::value)
     }
     flush(cc_t);
     if (RING && !ok) {
-        // a wait gave up: let every copy already issued land before the CTA exits
+        // A wait gave up (results are void; the host reports the timeout).
+        // Every copy already issued must still land before the CTA's shared
+        // memory is released: wait for each, with a bound of at least 1 s
+        // whatever the caller's limit.
+        const uint64_t drain_ns = a.timeout_ns > 1000000000ull ? a.timeout_ns : 1000000000ull;
         for (int k = kfail; k < nis; ++k)
-            mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1), a.timeout_ns);
+            mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1), drain_ns);
     }
+    if (CPA) cp_async_wait_all();
 }
 
 // H_{D,D+1}[a][b] = sum of the face partials of every CTA that touched the
 // tile, in CTA order.
-// CTA (tile t, row rr) sums each column thread's face partials over the CTAs
-// whose item ranges meet tile t, in CTA order.  Per-tile split: CTAs t P ..
-// t P + P - 1.  Stream-K: only the first of them can have started in tile
-// t-1 (its partial sits in segment 1).
-__global__ void reduce_face_kernel(const float* __restrict__ hp, float* __restrict__ out,
-                                   int64_t A, int64_t B, int FA, int FB, int64_t TB, int64_t O,
-                                   int64_t W, int64_t P) {
-    const int64_t t = blockIdx.x;
-    const int rr = blockIdx.y;
-    const int64_t ta = t / TB, tb = t - (t / TB) * TB;
-    const int64_t aa = ta * FA + rr, bb = tb * FB + threadIdx.x;
-    if (aa >= A || threadIdx.x >= FB || bb >= B) return;
-    const int64_t c_lo = P > 0 ? t * P : (t * O) / W;
-    const int64_t c_hi = P > 0 ? t * P + P - 1 : ((t + 1) * O - 1) / W;
-    const size_t inner = (size_t)rr * FB + threadIdx.x;
-    float s = hp[((size_t)c_lo * 2 + (P == 0 && c_lo * W < t * O ? 1 : 0)) * FA * FB + inner];
-    for (int64_t c = c_lo + 1; c <= c_hi; ++c) s += hp[(size_t)c * 2 * FA * FB + inner];
-    out[aa * B + bb] = s;
-}
+// All reductions of the streaming kernel's partials in one launch, over
+// units of 128 outputs (two units per 256-thread CTA, grid-stride):
+//  * face units (tile t, row rr): H_face[a][b] = sum of the face partials of
+//    the CTAs whose item ranges meet tile t, in CTA order.  Per-tile split:
+//    CTAs t P .. t P + P - 1.  Stream-K: only the first of them can have
+//    started in tile t-1 (its partial sits in segment 1);
+//  * y1 units: y1[i] = sum_{p < TB} y1p[p n1 + i], i < n1 = O A;
+//  * y2 units: y2[i] = sum_{p < TA} y2p[p n2 + i], i < n2 = O B.
+struct ReduceArgs {
+    const float* hp;
+    float* face;
+    int64_t A, B, TB, O, W, P, TT;
+    int FA, FB;
+    const float* y1p;
+    float* y1;
+    int64_t n1, np1;
+    const float* y2p;
+    float* y2;
+    int64_t n2, np2;
+};
 
-// out[i] = sum_{p < np} part[p * stride + i]
-__global__ void reduce_parts_kernel(const float* __restrict__ part, float* __restrict__ out,
-                                    int64_t n, int64_t np, int64_t stride) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int64_t p = 0; p < np; ++p) s += part[p * stride + i];
-        out[i] = s;
+__global__ void __launch_bounds__(256) reduce_pass_kernel(const ReduceArgs r) {
+    const int col = threadIdx.x & 127;
+    const int64_t nuF = r.TT * r.FA;
+    const int64_t nu1 = (r.n1 + 127) / 128, nu2 = (r.n2 + 127) / 128;
+    const int64_t total = nuF + nu1 + nu2;
+    for (int64_t u = blockIdx.x * 2 + (threadIdx.x >> 7); u < total; u += (int64_t)gridDim.x * 2) {
+        if (u < nuF) {
+            const int64_t t = u / r.FA;
+            const int rr = (int)(u - t * r.FA);
+            const int64_t ta = t / r.TB, tb = t - (t / r.TB) * r.TB;
+            const int64_t aa = ta * r.FA + rr, bb = tb * r.FB + col;
+            if (aa >= r.A || col >= r.FB || bb >= r.B) continue;
+            const int64_t c_lo = r.P > 0 ? t * r.P : (t * r.O) / r.W;
+            const int64_t c_hi = r.P > 0 ? t * r.P + r.P - 1 : ((t + 1) * r.O - 1) / r.W;
+            const size_t inner = (size_t)rr * r.FB + col, tile = (size_t)r.FA * r.FB;
+            float acc = r.hp[((size_t)c_lo * 2 + (r.P == 0 && c_lo * r.W < t * r.O ? 1 : 0)) * tile + inner];
+            for (int64_t c = c_lo + 1; c <= c_hi; ++c) acc += r.hp[(size_t)c * 2 * tile + inner];
+            r.face[aa * r.B + bb] = acc;
+        } else if (u < nuF + nu1) {
+            const int64_t i = (u - nuF) * 128 + col;
+            if (i >= r.n1) continue;
+            float acc = 0.f;
+            for (int64_t p = 0; p < r.np1; ++p) acc += r.y1p[p * r.n1 + i];
+            r.y1[i] = acc;
+        } else {
+            const int64_t i = (u - nuF - nu1) * 128 + col;
+            if (i >= r.n2) continue;
+            float acc = 0.f;
+            for (int64_t p = 0; p < r.np2; ++p) acc += r.y2p[p * r.n2 + i];
+            r.y2[i] = acc;
+        }
     }
 }
 
@@ -848,7 +882,7 @@ static int grid_for(int64_t n, int threads, int cap) {
 
 template <typename E, int MODE, int ROWS>
 static cudaError_t launch_tiled_k(const PassPlan& p, const CUtensorMap& map, const TiledArgs& a,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const KernelEvents* kev) {
     auto kern = ttvc_tiled_kernel<E, MODE, ROWS>;
     const size_t smem = 1024 + tiled_smem(MODE == LOAD_SCALAR ? 0 : p.nstage, p.group, ROWS,
                                           (int)sizeof(E), std::is_same<E, fp8_t>::value)
@@ -856,26 +890,28 @@ static cudaError_t launch_tiled_k(const PassPlan& p, const CUtensorMap& map, con
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    if (kev) cudaEventRecord(kev->begin, st);
     kern<<<p.grid, 256, smem, st>>>(map, a);
+    if (kev) cudaEventRecord(kev->end, st);
     return cudaGetLastError();
 }
 
 template <typename E, int MODE>
 static cudaError_t launch_tiled_rows(const PassPlan& p, const CUtensorMap& map, const TiledArgs& a,
-                                     cudaStream_t st) {
-    if (p.rows == 8) return launch_tiled_k<E, MODE, 8>(p, map, a, st);
+                                     cudaStream_t st, const KernelEvents* kev) {
+    if (p.rows == 8) return launch_tiled_k<E, MODE, 8>(p, map, a, st, kev);
     if constexpr (TiledOcc<E>::value == 1) {
-        if (p.rows == 16) return launch_tiled_k<E, MODE, 16>(p, map, a, st);
+        if (p.rows == 16) return launch_tiled_k<E, MODE, 16>(p, map, a, st, kev);
     }
-    return launch_tiled_k<E, MODE, 13>(p, map, a, st);
+    return launch_tiled_k<E, MODE, 13>(p, map, a, st, kev);
 }
 
 template <typename E>
 static cudaError_t launch_tiled(const PassPlan& p, int mode, const CUtensorMap& map,
-                                const TiledArgs& a, cudaStream_t st) {
-    if (mode == LOAD_TMA) return launch_tiled_rows<E, LOAD_TMA>(p, map, a, st);
-    if (mode == LOAD_ASYNC) return launch_tiled_rows<E, LOAD_ASYNC>(p, map, a, st);
-    return launch_tiled_rows<E, LOAD_SCALAR>(p, map, a, st);
+                                const TiledArgs& a, cudaStream_t st, const KernelEvents* kev) {
+    if (mode == LOAD_TMA) return launch_tiled_rows<E, LOAD_TMA>(p, map, a, st, kev);
+    if (mode == LOAD_ASYNC) return launch_tiled_rows<E, LOAD_ASYNC>(p, map, a, st, kev);
+    return launch_tiled_rows<E, LOAD_SCALAR>(p, map, a, st, kev);
 }
 
 __global__ void fp8_to_f32_kernel(const uint8_t* __restrict__ src, const float* __restrict__ scales,
@@ -890,7 +926,7 @@ __global__ void fp8_to_f32_kernel(const uint8_t* __restrict__ src, const float* 
 // Runs the whole pass: blocks H (P floats, packed) from T and u.
 hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* data,
                       const float* scales, const float* u, float* H, char* ws, int* dev_err,
-                      uint64_t timeout_ns, cudaStream_t st, Err& err) {
+                      uint64_t timeout_ns, cudaStream_t st, Err& err, const KernelEvents* kev) {
     (void)scales;
     cudaError_t ce;
 #define HOSCF_CK(x)                                                                  \
@@ -903,6 +939,7 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         }                                                                            \
     } while (0)
     if (p.copy_only) {
+        if (kev) cudaEventRecord(kev->begin, st);
         if (dtype == HOSCF_F32) {
             copy_kernel<<<grid_for(s.N, 256, 4096), 256, 0, st>>>((const float*)data, H, s.N);
         } else if (dtype == HOSCF_BF16) {
@@ -912,11 +949,12 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
             fp8_to_f32_kernel<<<grid_for(s.N, 256, 4096), 256, 0, st>>>((const uint8_t*)data,
                                                                         scales, H, s.N);
         }
+        if (kev) cudaEventRecord(kev->end, st);
         HOSCF_CK(cudaGetLastError());
         return HOSCF_OK;
     }
     if (p.small) {
-        HOSCF_CK(run_small(s, p.sp, dtype, data, scales, u, H, ws, st));
+        HOSCF_CK(run_small(s, p.sp, dtype, data, scales, u, H, ws, st, kev));
         return HOSCF_OK;
     }
     const OuterInfo oi = make_outer(s);
@@ -979,34 +1017,44 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
                      : (p.vec && (reinterpret_cast<uintptr_t>(data) & 15) == 0) ? LOAD_ASYNC
                                                                                 : LOAD_SCALAR;
     if (dtype == HOSCF_F32) {
-        HOSCF_CK(launch_tiled<float>(p, mode, map, a, st));
+        HOSCF_CK(launch_tiled<float>(p, mode, map, a, st, kev));
     } else if (dtype == HOSCF_BF16) {
-        HOSCF_CK(launch_tiled<bf16_t>(p, mode, map, a, st));
+        HOSCF_CK(launch_tiled<bf16_t>(p, mode, map, a, st, kev));
     } else {
-        HOSCF_CK(launch_tiled<fp8_t>(p, mode, map, a, st));
+        HOSCF_CK(launch_tiled<fp8_t>(p, mode, map, a, st, kev));
     }
-    // face block (d-2, d-1)
-    float* Hface = H + s.boff[block_index(s.d, s.d - 2, s.d - 1)];
-    reduce_face_kernel<<<dim3((unsigned)p.TT, (unsigned)p.FA), p.FB, 0, st>>>(
-        a.hp, Hface, s.A, s.B, p.FA, p.FB, p.TB, s.O, p.W, p.P);
-    HOSCF_CK(cudaGetLastError());
-    if (s.d == 3) {
-        // y1 = H_{0,1} (I_0 x A), y2 = H_{0,2} (I_0 x B)
-        reduce_parts_kernel<<<grid_for(s.O * s.A, 256, 8192), 256, 0, st>>>(
-            a.y1p, H + s.boff[block_index(3, 0, 1)], s.O * s.A, p.TB, s.O * s.A);
-        reduce_parts_kernel<<<grid_for(s.O * s.B, 256, 8192), 256, 0, st>>>(
-            a.y2p, H + s.boff[block_index(3, 0, 2)], s.O * s.B, p.TA, s.O * s.B);
+    // face block (d-2, d-1) and the row / column sums y1 (O x A), y2 (O x B):
+    // for d == 3 these are H_{0,1} and H_{0,2} themselves
+    float* y1 = s.d == 3 ? H + s.boff[block_index(3, 0, 1)] : reinterpret_cast<float*>(ws + p.off_y1);
+    float* y2 = s.d == 3 ? H + s.boff[block_index(3, 0, 2)] : reinterpret_cast<float*>(ws + p.off_y2);
+    {
+        ReduceArgs ra;
+        ra.hp = a.hp;
+        ra.face = H + s.boff[block_index(s.d, s.d - 2, s.d - 1)];
+        ra.A = s.A;
+        ra.B = s.B;
+        ra.TB = p.TB;
+        ra.O = s.O;
+        ra.W = p.W;
+        ra.P = p.P;
+        ra.TT = p.TT;
+        ra.FA = p.FA;
+        ra.FB = p.FB;
+        ra.y1p = a.y1p;
+        ra.y1 = y1;
+        ra.n1 = s.O * s.A;
+        ra.np1 = p.TB;
+        ra.y2p = a.y2p;
+        ra.y2 = y2;
+        ra.n2 = s.O * s.B;
+        ra.np2 = p.TA;
+        const int64_t units = p.TT * p.FA + (ra.n1 + 127) / 128 + (ra.n2 + 127) / 128;
+        const int64_t g = std::min<int64_t>((units + 1) / 2, 8 * (int64_t)std::max(1, p.nsm));
+        reduce_pass_kernel<<<(unsigned)std::max<int64_t>(1, g), 256, 0, st>>>(ra);
         HOSCF_CK(cudaGetLastError());
-        return HOSCF_OK;
     }
-    float* y1 = reinterpret_cast<float*>(ws + p.off_y1);
-    float* y2 = reinterpret_cast<float*>(ws + p.off_y2);
+    if (s.d == 3) return HOSCF_OK;
     float* r = reinterpret_cast<float*>(ws + p.off_r);
-    reduce_parts_kernel<<<grid_for(s.O * s.A, 256, 8192), 256, 0, st>>>(a.y1p, y1, s.O * s.A, p.TB,
-                                                                       s.O * s.A);
-    reduce_parts_kernel<<<grid_for(s.O * s.B, 256, 8192), 256, 0, st>>>(a.y2p, y2, s.O * s.B, p.TA,
-                                                                       s.O * s.B);
-    HOSCF_CK(cudaGetLastError());
     // cross blocks (m, d-2) from y1 and (m, d-1) from y2
     int64_t rows = 0;
     for (int k = 0; k < s.D; ++k) rows += s.dims[k];

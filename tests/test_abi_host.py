@@ -1,0 +1,173 @@
+"""Host-side checks of the C ABI and of the bench's multi-rank logic (no GPU).
+
+* the library builds for sm_103a, loads, and exports every function that
+  include/hoscf.h declares (parsed from the header, not from the binding);
+* the entry points that need no device behave as documented: defaults,
+  rejection of NULL / invalid arguments, host-only workspace sizing;
+* a status code from the library becomes a typed Python exception (the
+  failure is made on the host, by a fake of the failing call);
+* the bench's max-over-ranks timing and whole-job throughput over a gloo
+  process group of world size 2, and the reference arm's rank gating."""
+import argparse
+import ctypes
+import multiprocessing as mp
+import os
+import re
+import socket
+
+import pytest
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hoscf.h")
+
+EINVAL = 1
+
+
+def header_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    pat = r"^\s*(?:hoscf_status|const\s+char\s*\*)\s*(hoscf_\w+)\s*\("
+    return sorted(set(re.findall(pat, txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_01778_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def test_header_and_binding_list_the_same_functions():
+    from paper_2403_01778_gb300 import _lib
+    declared = header_functions()
+    assert len(declared) >= 14
+    assert set(declared) == set(_lib.EXPORTS)
+
+
+def test_library_exports_every_declared_function(lib):
+    from paper_2403_01778_gb300 import build
+    handle = ctypes.CDLL(build.LIB)
+    missing = [n for n in header_functions() if not hasattr(handle, n)]
+    assert not missing, missing
+
+
+def test_opts_default_values(lib):
+    from paper_2403_01778_gb300 import _lib
+    o = _lib.Opts()
+    assert lib.hoscf_opts_default(ctypes.byref(o)) == 0
+    assert (o.tol, o.max_iter, o.variant) == (1e-6, 200, 0)
+    assert (o.eig_tol, o.eig_max_steps, o.eig_adapt) == (1e-10, 64, 1e-3)
+    assert not o.refine and o.switch_tol == 1e-3 and o.timeout_ns == 2_000_000_000
+
+
+def test_null_and_invalid_arguments_are_rejected_on_the_host(lib):
+    from paper_2403_01778_gb300 import _lib
+    assert lib.hoscf_opts_default(None) == EINVAL
+    assert lib.hoscf_destroy(None) == EINVAL
+    assert lib.hoscf_last_error(None) == b"null handle"
+    assert lib.hoscf_ttvc_blocks(None, None, None, None, None) == EINVAL
+    assert lib.hoscf_solve(None, None, None, None, None, None, None, None) == EINVAL
+    assert lib.hoscf_backward(None, None, None, 0.0, 0.0, None, None, None) == EINVAL
+    assert lib.hoscf_profile_enable(None, 1) == EINVAL
+    n, ms = ctypes.c_int(), ctypes.c_double()
+    assert lib.hoscf_profile_read(None, ctypes.byref(n), ctypes.byref(ms)) == EINVAL
+    assert lib.hoscf_ttvc_blocks_static(None, None, None, None) == EINVAL
+    # a descriptor of order 9 is rejected before any device call
+    dims = (ctypes.c_int64 * 9)(*([2] * 9))
+    desc = _lib.TensorDesc(9, dims, 0, ctypes.c_void_p(16), None)
+    buf = ctypes.c_void_p(16)
+    assert lib.hoscf_ttvc_blocks_static(ctypes.byref(desc), buf, buf, None) == EINVAL
+    size = ctypes.c_size_t()
+    for order, dd in [(3, (4, 0, 5)), (1, (4,)), (9, (2,) * 9)]:
+        arr = (ctypes.c_int64 * len(dd))(*dd)
+        assert lib.hoscf_workspace_size(order, arr, 0, ctypes.byref(size)) == EINVAL
+
+
+def test_workspace_size_is_host_only_and_grows_with_the_problem(lib):
+    sizes = []
+    for dd in [(16, 16, 16), (64, 64, 64), (256, 256, 256), (24, 20, 24, 20, 24, 20)]:
+        arr = (ctypes.c_int64 * len(dd))(*dd)
+        b = ctypes.c_size_t()
+        assert lib.hoscf_workspace_size(len(dd), arr, 0, ctypes.byref(b)) == 0
+        sizes.append(b.value)
+    assert sizes[0] > 0 and sizes[0] < sizes[1] < sizes[2]
+    # the FP8 form sizes for its FP32 refinement copy as well
+    arr = (ctypes.c_int64 * 4)(200, 200, 200, 200)
+    b8, b32 = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.hoscf_workspace_size(4, arr, 2, ctypes.byref(b8)) == 0
+    assert lib.hoscf_workspace_size(4, arr, 0, ctypes.byref(b32)) == 0
+    assert b8.value >= b32.value
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-device path")
+def test_create_without_a_device_fails_cleanly(lib):
+    h = ctypes.c_void_p(123)
+    assert lib.hoscf_create(ctypes.byref(h), 0) != 0
+    assert not h.value
+
+
+def test_status_codes_become_typed_errors(monkeypatch):
+    from paper_2403_01778_gb300 import _lib, api
+
+    class FakeLib:
+        def hoscf_last_error(self, h):
+            return b"a device-side wait exceeded its time limit"
+
+    monkeypatch.setattr(_lib, "load", lambda: FakeLib())
+    with pytest.raises(api.HoscfError) as e:
+        api._check(_lib.HOSCF_TIMEOUT, None)
+    assert e.value.status == _lib.HOSCF_TIMEOUT
+    assert str(e.value).startswith("TIMEOUT:") and "time limit" in str(e.value)
+    with pytest.raises(api.HoscfError) as e:
+        api._check(_lib.HOSCF_NONFINITE, None)
+    assert e.value.status == _lib.HOSCF_NONFINITE
+    assert api._check(_lib.HOSCF_NOT_CONVERGED, None,
+                      allow=(0, _lib.HOSCF_NOT_CONVERGED)) == _lib.HOSCF_NOT_CONVERGED
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2403_01778_gb300 import _lib
+    monkeypatch.setattr(_lib, "_LIB", None)
+    monkeypatch.setattr(_lib, "library_path", lambda: str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms = bench.max_over_ranks(10.0 + 5.0 * rank, dist, "cpu")
+    q.put((rank, ms, bench.whole_job_gbs(2e9, 4, world, ms)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_takes_the_slowest_rank_and_whole_job_bytes_over_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [g[1] for g in got] == [15.0, 15.0]
+    assert all(abs(g[2] - 2e9 * 4 * 2 / 0.015 / 1e9) < 1e-9 for g in got)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    import bench
+    args = argparse.Namespace(workload="cfg1_64cube", steps=1, warmup=0, gpus=2)
+    assert bench.run_reference(args, rank=1, world=2) == 0
+    assert bench.max_over_ranks(7.5) == 7.5

@@ -1,0 +1,76 @@
+"""Failure detection on the GPU without a fault, and the kernel-timing aid.
+
+Every spin-wait in the library's kernels is bounded.  A wait whose condition
+nothing can satisfy (an mbarrier phase no copy completes; the grid barrier
+with an arrival missing) must give up after its bound, record the timeout in
+the device status word and return, so that the host call reports
+HOSCF_TIMEOUT and the context stays usable: the next calls on it give
+correct results.  No kernel is made to fault, trap or hang."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_01778_gb300 import build
+    build.build()
+
+
+def P():
+    import paper_2403_01778_gb300 as pkg
+    return pkg
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_wait_that_runs_out_reports_timeout_and_context_survives(kind):
+    pkg = P()
+    assert pkg.hoscf_selftest_timeout(kind, 2_000_000) == 6      # HOSCF_TIMEOUT
+    torch.cuda.synchronize()
+    # same context: exact blocks on an integer-valued tensor, then a solve
+    dims = (40, 50, 136)
+    rng = np.random.default_rng(7)
+    Ti = rng.integers(-3, 4, size=dims).astype(np.float32)
+    ui = [rng.integers(-2, 3, size=n).astype(np.float64) for n in dims]
+    H = pkg.hoscf_ttvc_blocks(torch.from_numpy(Ti).cuda(),
+                              torch.from_numpy(np.concatenate(ui).astype(np.float32)).cuda())
+    assert np.array_equal(H.double().cpu().numpy(), oracle.blocks(Ti, ui))
+    T, _ = W.planted_cp((60, 70, 80), [4.0], seed=11, noise_abs=0.5)
+    u0 = torch.cat(W.unit_gaussian_vectors((60, 70, 80), 12)).cuda()
+    r = pkg.hoscf_solve(T.cuda(), u0, tol=1e-6, max_iter=300)   # its grid barriers work again
+    assert r.converged
+
+
+def test_selftest_rejects_bad_arguments():
+    pkg = P()
+    assert pkg.hoscf_selftest_timeout(2, 1000) == 1
+    assert pkg.hoscf_selftest_timeout(0, 0) == 1
+
+
+def test_kernel_timing_aid_counts_each_pass():
+    pkg = P()
+    dims = (128, 128, 256)
+    T = W.gaussian_tensor(dims, 8).cuda()
+    u = torch.cat(W.unit_gaussian_vectors(dims, 9)).cuda()
+    H = pkg.hoscf_ttvc_blocks(T, u)
+    pkg.hoscf_profile_enable(0, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        pkg.hoscf_ttvc_blocks(T, u, H)
+    e1.record()
+    pkg.hoscf_profile_enable(0, False)
+    pkg.hoscf_ttvc_blocks(T, u, H)          # not recorded
+    n, ms = pkg.hoscf_profile_read(0)
+    torch.cuda.synchronize()
+    assert n == 3
+    assert 0.0 < ms <= e0.elapsed_time(e1)
+    pkg.hoscf_profile_enable(0, True)       # re-enabling clears the records
+    pkg.hoscf_profile_enable(0, False)
+    assert pkg.hoscf_profile_read(0)[0] == 0
