@@ -654,6 +654,23 @@ struct ReduceArgs {
     int64_t n2, np2;
 };
 
+// sum_{p < n} x[p * stride]: four independent partial sums (loads in
+// flight together), combined in a fixed order.
+__device__ __forceinline__ float sum_strided(const float* __restrict__ x, size_t stride, int64_t n) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int64_t p = 0;
+    for (; p + 4 <= n; p += 4) {
+        const float v0 = __ldg(x + (size_t)p * stride), v1 = __ldg(x + (size_t)(p + 1) * stride),
+                    v2 = __ldg(x + (size_t)(p + 2) * stride), v3 = __ldg(x + (size_t)(p + 3) * stride);
+        a0 += v0;
+        a1 += v1;
+        a2 += v2;
+        a3 += v3;
+    }
+    for (; p < n; ++p) a0 += __ldg(x + (size_t)p * stride);
+    return (a0 + a1) + (a2 + a3);
+}
+
 __global__ void __launch_bounds__(256) reduce_pass_kernel(const ReduceArgs r) {
     const int col = threadIdx.x & 127;
     const int64_t nuF = r.TT * r.FA;
@@ -669,21 +686,18 @@ __global__ void __launch_bounds__(256) reduce_pass_kernel(const ReduceArgs r) {
             const int64_t c_lo = r.P > 0 ? t * r.P : (t * r.O) / r.W;
             const int64_t c_hi = r.P > 0 ? t * r.P + r.P - 1 : ((t + 1) * r.O - 1) / r.W;
             const size_t inner = (size_t)rr * r.FB + col, tile = (size_t)r.FA * r.FB;
-            float acc = r.hp[((size_t)c_lo * 2 + (r.P == 0 && c_lo * r.W < t * r.O ? 1 : 0)) * tile + inner];
-            for (int64_t c = c_lo + 1; c <= c_hi; ++c) acc += r.hp[(size_t)c * 2 * tile + inner];
-            r.face[aa * r.B + bb] = acc;
+            const float first =
+                r.hp[((size_t)c_lo * 2 + (r.P == 0 && c_lo * r.W < t * r.O ? 1 : 0)) * tile + inner];
+            r.face[aa * r.B + bb] =
+                first + sum_strided(r.hp + (size_t)(c_lo + 1) * 2 * tile + inner, 2 * tile, c_hi - c_lo);
         } else if (u < nuF + nu1) {
             const int64_t i = (u - nuF) * 128 + col;
             if (i >= r.n1) continue;
-            float acc = 0.f;
-            for (int64_t p = 0; p < r.np1; ++p) acc += r.y1p[p * r.n1 + i];
-            r.y1[i] = acc;
+            r.y1[i] = sum_strided(r.y1p + i, (size_t)r.n1, r.np1);
         } else {
             const int64_t i = (u - nuF - nu1) * 128 + col;
             if (i >= r.n2) continue;
-            float acc = 0.f;
-            for (int64_t p = 0; p < r.np2; ++p) acc += r.y2p[p * r.n2 + i];
-            r.y2[i] = acc;
+            r.y2[i] = sum_strided(r.y2p + i, (size_t)r.n2, r.np2);
         }
     }
 }
@@ -1049,7 +1063,7 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         ra.n2 = s.O * s.B;
         ra.np2 = p.TA;
         const int64_t units = p.TT * p.FA + (ra.n1 + 127) / 128 + (ra.n2 + 127) / 128;
-        const int64_t g = std::min<int64_t>((units + 1) / 2, 8 * (int64_t)std::max(1, p.nsm));
+        const int64_t g = std::min<int64_t>((units + 1) / 2, 16 * (int64_t)std::max(1, p.nsm));
         reduce_pass_kernel<<<(unsigned)std::max<int64_t>(1, g), 256, 0, st>>>(ra);
         HOSCF_CK(cudaGetLastError());
     }
