@@ -71,7 +71,7 @@ constexpr size_t kProfMax = 65536;   // timed calls kept by the measurement aid
 // Fixed head of the workspace: device error word, grid barrier, scalars.
 constexpr size_t kHeadBytes = 4096;
 constexpr size_t kOffErr = 0;        // int
-constexpr size_t kOffBar = 64;       // 2 unsigned
+constexpr size_t kOffBar = 64;       // grid-barrier arrival counter (unsigned)
 constexpr size_t kOffScal = 256;     // 32 doubles
 constexpr size_t kOffNorms = 1024;   // up to 16 doubles
 
@@ -192,7 +192,7 @@ hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const 
                         double tol_override = 0.0) {
     char* eb = h->ws + L.off_eig;
     float* Jr = reinterpret_cast<float*>(eb + L.ep.off_jr);
-    cudaError_t e = launch_build_jr(L.s, H, Jr, st);
+    cudaError_t e = launch_build_jr(L.s, H, Jr, reinterpret_cast<unsigned*>(h->ws + kOffBar), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "build_jr");
     LanczosLaunch ll;
     ll.Jr = Jr;
@@ -244,7 +244,8 @@ __global__ void selftest_mbar_kernel(int* err, uint64_t limit_ns) {
 
 __global__ void selftest_grid_kernel(unsigned* state, int* err, uint64_t limit_ns) {
     // one arrival short of the count: the barrier can never open
-    grid_barrier(state, gridDim.x + 1, err, limit_ns);
+    unsigned epoch = 0;
+    grid_barrier(state, gridDim.x + 1, epoch, err, limit_ns);
 }
 
 extern "C" {

@@ -142,27 +142,28 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ------------------------------------------------------------------ grid barrier
 // Software barrier across the co-resident CTAs of a cooperative launch.
-// `state[0]` counts arrivals, `state[1]` is the generation.  Every wait is
-// bounded by `limit_ns`; on timeout *err is set and false is returned (the
-// caller then leaves the kernel).
-__device__ __forceinline__ bool grid_barrier(unsigned* state, unsigned nblocks, int* err,
-                                             uint64_t limit_ns) {
+// `*count` is zero when the launch starts (the launcher's preceding kernel
+// on the same stream clears it) and only grows: every CTA adds one per
+// barrier with a fire-and-forget reduction, then polls until the count
+// reaches epoch x nblocks, `epoch` being the number of barriers this CTA has
+// passed (uniform over the CTA).  One round trip per barrier, no release
+// flag.  Every wait is bounded by `limit_ns`; on timeout *err is set and
+// false is returned (the caller then leaves the kernel).
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned nblocks, unsigned& epoch,
+                                             int* err, uint64_t limit_ns) {
     __syncthreads();
     __shared__ int s_ok;
+    ++epoch;
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = state + 1;
-        const unsigned gen = *vgen;
         __threadfence();
-        const unsigned arrived = atomicAdd(state, 1u);
+        atomicAdd(count, 1u);   // result unused: a reduction, no round trip
+        const unsigned target = epoch * nblocks;
+        volatile unsigned* vc = count;
         int ok = 1;
-        if (arrived == nblocks - 1) {
-            atomicExch(state, 0u);
-            __threadfence();
-            atomicAdd(state + 1, 1u);
-        } else {
+        if ((int)(*vc - target) < 0) {
             const uint64_t t0 = global_timer_ns();
             unsigned spins = 0;
-            while (*vgen == gen) {
+            while ((int)(*vc - target) < 0) {
                 __nanosleep(20);
                 if ((++spins & 255u) == 0) {
                     if (*(volatile int*)err) { ok = 0; break; }

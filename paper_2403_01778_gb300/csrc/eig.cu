@@ -98,7 +98,21 @@ __device__ void matvec_rows(const EigArgs& a, const float* __restrict__ vf, int 
             for (int j = lane; j < lo; j += 32) f = fmaf(srow[j], vf[j], f);
             for (int j = lo + lane; j < (int)len; j += 32) f = fmaf(srow[j], vhi[j], f);
         } else {
-            for (int j = lane; j < (int)len; j += 32) {
+            // four independent loads in flight per lane (rows stream from L2)
+            int j = lane;
+            for (; j + 96 < (int)len; j += 128) {
+                float h[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) h[t] = __ldg(grow + j + 32 * t);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int jj = j + 32 * t;
+                    if (srow) srow[jj] = h[t];
+                    f = fmaf(h[t], jj < lo ? vf[jj] : vhi[jj], f);
+                    s2 = fmaf(h[t], h[t], s2);
+                }
+            }
+            for (; j < (int)len; j += 32) {
                 const float h = __ldg(grow + j);
                 if (srow) srow[j] = h;
                 f = fmaf(h, j < lo ? vf[j] : vhi[j], f);
@@ -113,6 +127,119 @@ __device__ void matvec_rows(const EigArgs& a, const float* __restrict__ vf, int 
         }
     }
     if (sq && lane == 0) atomicAdd(sq, (double)sqacc);   // shared-memory scratch, per CTA
+}
+
+// Copies this CTA's rows of Jr into the shared-memory cache (rows of one mode
+// are contiguous in Jr and in the cache, so each mode segment is one block
+// copy), all threads with four independent loads in flight, and adds the
+// squared entries to *sq (FP32 per thread, FP64 per CTA: ||Jr||_F^2).
+__device__ void fill_cache_rows(const EigArgs& a, int r0, int r1, float* cache,
+                                const int64_t* crow, double* sq) {
+    constexpr int T = kEigThreads;
+    float s2a = 0.f, s2b = 0.f;
+    for (int q = r0; q < r1;) {
+        const int m = mode_of(a, q);
+        const int qe = min(r1, (int)a.moff[m + 1]);
+        const int64_t len = a.n - (a.moff[m + 1] - a.moff[m]);
+        const float* __restrict__ src = a.Jr + a.jroff[m] + (int64_t)(q - a.moff[m]) * len;
+        float* dst = cache + crow[q - r0];
+        const int64_t cnt = (int64_t)(qe - q) * len;
+        // scalar head up to a 16-byte boundary of the source, 16-byte loads for
+        // the middle (the cache side keeps scalar stores: its alignment differs)
+        const int64_t head = min(cnt, (int64_t)((16 - (reinterpret_cast<uintptr_t>(src) & 15)) & 15) / 4);
+        const int64_t nv = (cnt - head) / 4;
+        for (int64_t i = threadIdx.x; i < head; i += T) {
+            const float h = __ldcg(src + i);
+            dst[i] = h;
+            s2a = fmaf(h, h, s2a);
+        }
+        const float4* __restrict__ src4 = reinterpret_cast<const float4*>(src + head);
+        float* d4 = dst + head;
+        int64_t v = threadIdx.x;
+        for (; v + 3 * T < nv; v += 4 * T) {
+            float4 h[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) h[t] = __ldcg(src4 + v + t * T);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                float* o = d4 + 4 * (v + t * T);
+                o[0] = h[t].x;
+                o[1] = h[t].y;
+                o[2] = h[t].z;
+                o[3] = h[t].w;
+                s2a = fmaf(h[t].x, h[t].x, fmaf(h[t].y, h[t].y, s2a));
+                s2b = fmaf(h[t].z, h[t].z, fmaf(h[t].w, h[t].w, s2b));
+            }
+        }
+        for (; v < nv; v += T) {
+            const float4 h = __ldcg(src4 + v);
+            float* o = d4 + 4 * v;
+            o[0] = h.x;
+            o[1] = h.y;
+            o[2] = h.z;
+            o[3] = h.w;
+            s2a = fmaf(h.x, h.x, fmaf(h.y, h.y, s2a));
+            s2b = fmaf(h.z, h.z, fmaf(h.w, h.w, s2b));
+        }
+        for (int64_t i = head + 4 * nv + threadIdx.x; i < cnt; i += T) {
+            const float h = __ldcg(src + i);
+            dst[i] = h;
+            s2a = fmaf(h, h, s2a);
+        }
+        q = qe;
+    }
+    const float s2 = warp_sum(s2a + s2b);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sq, (double)s2);   // shared-memory scratch, per CTA
+    __syncthreads();
+}
+
+// The same mat-vec from the shared-memory cache of this CTA's rows: warp w
+// takes a contiguous chunk of rows and walks it in groups of up to four rows
+// of one mode (same column pattern), so each vector element read from
+// shared memory feeds four independent FMA chains; a reduce-scatter then
+// sums the four rows over the lanes with six shuffles.
+__device__ void matvec_rows_cached(const EigArgs& a, const float* __restrict__ vf, int r0, int r1,
+                                   const float* __restrict__ cache, const int64_t* crow,
+                                   float* yrow) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int RW = (r1 - r0 + kEigWarps - 1) / kEigWarps;
+    const int qb = r0 + warp * RW, qe = min(r1, qb + RW);
+    for (int q = qb; q < qe;) {
+        const int m = mode_of(a, q);
+        const int cnt = min(4, min(qe, (int)a.moff[m + 1]) - q);
+        const int64_t Im = a.moff[m + 1] - a.moff[m];
+        const int len = (int)(a.n - Im);
+        const int lo = (int)a.moff[m];
+        const float* vhi = vf + Im;
+        const float* rp[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rp[i] = cache + crow[q + min(i, cnt - 1) - r0];
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int j = lane; j < lo; j += 32) {
+            const float v = vf[j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fmaf(rp[i][j], v, acc[i]);
+        }
+        for (int j = lo + lane; j < len; j += 32) {
+            const float v = vhi[j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fmaf(rp[i][j], v, acc[i]);
+        }
+        // reduce-scatter: lanes with bit 4 set keep rows 2,3, bit 3 picks the odd row
+        const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+        const float s0 = (up16 ? acc[2] : acc[0]) +
+                         __shfl_xor_sync(HOSCF_FULLMASK, up16 ? acc[0] : acc[2], 16);
+        const float s1 = (up16 ? acc[3] : acc[1]) +
+                         __shfl_xor_sync(HOSCF_FULLMASK, up16 ? acc[1] : acc[3], 16);
+        float t = (up8 ? s1 : s0) + __shfl_xor_sync(HOSCF_FULLMASK, up8 ? s0 : s1, 8);
+        t += __shfl_xor_sync(HOSCF_FULLMASK, t, 4);
+        t += __shfl_xor_sync(HOSCF_FULLMASK, t, 2);
+        t += __shfl_xor_sync(HOSCF_FULLMASK, t, 1);
+        const int row = (up16 ? 2 : 0) + (up8 ? 1 : 0);
+        if ((lane & 7) == 0 && row < cnt)
+            yrow[q + row - r0] = t * a.scale + a.shift_add * vf[q + row];
+        q += cnt;
+    }
 }
 
 // out[i] = sum_{c < G} pb[c * ps + i] for i < cnt, every CTA computing the
@@ -145,12 +272,12 @@ __device__ __forceinline__ bool check_now(int k) {
 }
 
 // Grid-wide barrier; a single-CTA launch only needs __syncthreads.
-__device__ __forceinline__ bool eig_sync(const EigArgs& a, int G) {
+__device__ __forceinline__ bool eig_sync(const EigArgs& a, int G, unsigned& epoch) {
     if (G == 1) {
         __syncthreads();
         return true;
     }
-    return grid_barrier(a.bar, G, a.err, a.timeout_ns);
+    return grid_barrier(a.bar, G, epoch, a.err, a.timeout_ns);
 }
 
 // Lanczos with full reorthogonalisation.  Each CTA owns rows [r0, r1) of J:
@@ -174,6 +301,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     const int r0 = min(n, c * R), r1 = min(n, r0 + R);
     const int nr = r1 - r0;
     const int M1 = a.mmax + 1;
+    unsigned bar_epoch = 0;   // grid barriers passed (see grid_barrier)
 
     extern __shared__ __align__(16) uint8_t sm_raw[];
     double* hd = reinterpret_cast<double*>(sm_raw);                       // 16 (FP64 scalars)
@@ -202,6 +330,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     }
     __syncthreads();
     float* cache = (hd[15] != 0.0) ? jcache : nullptr;
+    if (cache) fill_cache_rows(a, r0, r1, cache, crow, &hd[0]);
     __shared__ double s_znorm;   // |z| of the last tridiagonal solve (solve modes)
 
     const int ps = a.pstride;
@@ -222,7 +351,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         Vl[q - r0] = v;
         vslot(0)[q] = v;
     }
-    if (!eig_sync(a, G)) return;
+    if (!eig_sync(a, G, bar_epoch)) return;
 
     int k = 0;
     double beta_last = 0.0;
@@ -235,7 +364,10 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         const float* src = vslot(j);
         for (int q = tid; q < n; q += kEigThreads) vf[q] = __ldcg(src + q);
         __syncthreads();
-        matvec_rows(a, vf, r0, r1, cache, crow, j == 0, j == 0 ? &hd[0] : nullptr, Yl);
+        if (cache)
+            matvec_rows_cached(a, vf, r0, r1, cache, crow, Yl);
+        else
+            matvec_rows(a, vf, r0, r1, nullptr, crow, false, j == 0 ? &hd[0] : nullptr, Yl);
         __syncthreads();
         if (j == 0) {
             // FP64 certificate of the start point x0 (unnormalised):
@@ -250,7 +382,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                     t = warp_sum_d(t);
                     if (lane == 0) pdd[(size_t)24 * G + (size_t)c * kMaxOrder + m] = t;
                 }
-                if (!eig_sync(a, G)) return;
+                if (!eig_sync(a, G, bar_epoch)) return;
                 reduce_partials<double>(pdd + (size_t)24 * G, kMaxOrder, G, a.d, mu_s);
                 for (int q = tid; q < nr; q += kEigThreads) {
                     const int m = mode_of(a, q + r0);
@@ -281,7 +413,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 pdd[(size_t)c * 4 + tid] = t;
             }
             if (tid == 3) pdd[(size_t)c * 4 + 3] = hd[0];
-            if (!eig_sync(a, G)) return;
+            if (!eig_sync(a, G, bar_epoch)) return;
             reduce_partials<double>(pdd, 4, G, 4, hd + 1);   // hd[1..4]
             const double xy = hd[1], xx = hd[2], yy = hd[3];
             if (!(xx > 0.0) || !isfinite(xx) || !isfinite(yy)) {
@@ -305,7 +437,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 for (int w8 = 0; w8 < kEigWarps; ++w8) t += red[0][w8];
                 pdd[(size_t)(G + c) * 4] = t;
             }
-            if (!eig_sync(a, G)) return;
+            if (!eig_sync(a, G, bar_epoch)) return;
             reduce_partials<double>(pdd + (size_t)G * 4, 4, G, 1, hd + 5);
             const double b0 = sqrt(fmax(hd[5], 0.0));
             const double jfro = sqrt(hd[4]) * (double)a.scale;
@@ -365,7 +497,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 s = warp_sum(s);
                 if (lane == 0) pbuf()[(size_t)c * ps + i] = s;
             }
-            if (!eig_sync(a, G)) return;
+            if (!eig_sync(a, G, bar_epoch)) return;
             reduce_partials<float>(pbuf(), ps, G, cnt, hsum);
             ++phase;
             if (nproj) {
@@ -402,7 +534,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                     s = warp_sum(s);
                     if (lane == 0) pbuf()[(size_t)c * ps + i] = s;
                 }
-                if (!eig_sync(a, G)) return;
+                if (!eig_sync(a, G, bar_epoch)) return;
                 reduce_partials<float>(pbuf(), ps, G, j + 2, hsum);
                 ++phase;
                 float ssq2 = 0.f;
@@ -415,7 +547,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                     Yl[q] = w;
                 }
             }
-            beta_last = sqrt(fmax((double)b2, 0.0));
+            beta_last = (double)sqrtf(fmaxf(b2, 0.f));
             if (tid == 0) {
                 alpha[j] = alj;
                 beta[j] = beta_last;
@@ -427,6 +559,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         const bool last = (k == a.mmax) || (k == n) || !(beta_last > 1e-30);
         if (check_now(k) || last) {
             __shared__ RitzOut s_ro;
+            __shared__ int s_acc;
             if (a.rqi) {
                 if (tid == 0) {
                     float* w = rscratch;
@@ -438,9 +571,15 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                     s_ro.resid = beta_last * rel;   // relative Galerkin residual of the solve
                 }
             } else if (k >= 2) {
+                // FP32 pair to decide; the FP64 refinement only once accepted
                 if (warp == 0) {
-                    RitzOut t = ritz_largest_magnitude(alpha, beta, k, beta_last, sv, rscratch);
-                    if (lane == 0) s_ro = t;
+                    RitzOut t = ritz_extreme_fp32(alpha, beta, k, beta_last, rscratch);
+                    const bool acc = t.resid <= a.eig_tol * fabs(t.theta) || last;
+                    if (acc) t = ritz_refine_fp64(alpha, beta, k, beta_last, sv, rscratch);
+                    if (lane == 0) {
+                        s_ro = t;
+                        s_acc = acc ? 1 : 0;
+                    }
                 }
             } else if (tid == 0) {
                 sv[0] = 1.0;
@@ -449,18 +588,22 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             }
             __syncthreads();
             ro = s_ro;
-            const double scale_t = a.rqi ? 1.0 : fabs(ro.theta);
-            if (ro.resid <= a.eig_tol * scale_t || last) done = true;
+            if (!a.rqi && k >= 2) {
+                if (s_acc) done = true;
+            } else {
+                const double scale_t = a.rqi ? 1.0 : fabs(ro.theta);
+                if (ro.resid <= a.eig_tol * scale_t || last) done = true;
+            }
         }
         if (!done) {
-            const float inv = (float)(1.0 / beta_last);
+            const float inv = 1.0f / (float)beta_last;
             float* dst = vslot(j + 1);
             for (int q = tid; q < nr; q += kEigThreads) {
                 const float v = Yl[q] * inv;
                 Vl[(size_t)(j + 1) * R + q] = v;
                 dst[r0 + q] = v;
             }
-            if (!eig_sync(a, G)) return;
+            if (!eig_sync(a, G, bar_epoch)) return;
         }
     }
     // ---- Ritz vector x = V[0..k-1] s for my rows (FP64 accumulation); block
@@ -501,7 +644,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         s = warp_sum_d(s);
         if (lane == 0) pdd[(size_t)8 * G + (size_t)c * (kMaxOrder + 1) + i] = s;
     }
-    if (!eig_sync(a, G)) return;
+    if (!eig_sync(a, G, bar_epoch)) return;
     reduce_partials<double>(pdd + (size_t)8 * G, kMaxOrder + 1, G, d + 1, hd + 6);
     const double* bn = hd + 6;
     double tot = 0.0;
@@ -539,8 +682,10 @@ struct JrBuildArgs {
     int64_t tstart[kMaxBlocks + 1];   // tile prefix
 };
 
-__global__ void build_jr_kernel(const float* __restrict__ H, float* __restrict__ Jr, JrBuildArgs a) {
+__global__ void build_jr_kernel(const float* __restrict__ H, float* __restrict__ Jr, JrBuildArgs a,
+                                unsigned* bar) {
     __shared__ float tile[32][33];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && bar) *bar = 0u;   // for the next Lanczos launch
     const int64_t tix = blockIdx.x;
     int b = 0;
     while (tix >= a.tstart[b + 1]) ++b;
@@ -752,7 +897,8 @@ static void jr_offsets(const Shape& s, int64_t* jroff) {
     for (int m = 0; m < s.d; ++m) jroff[m + 1] = jroff[m] + s.dims[m] * (s.n_tot - s.dims[m]);
 }
 
-cudaError_t launch_build_jr(const Shape& s, const float* H, float* Jr, cudaStream_t st) {
+cudaError_t launch_build_jr(const Shape& s, const float* H, float* Jr, unsigned* bar,
+                            cudaStream_t st) {
     JrBuildArgs a;
     memset(&a, 0, sizeof(a));
     a.d = s.d;
@@ -771,7 +917,7 @@ cudaError_t launch_build_jr(const Shape& s, const float* H, float* Jr, cudaStrea
         }
     a.nblk = b;
     const int64_t tiles = a.tstart[b];
-    build_jr_kernel<<<(unsigned)tiles, 256, 0, st>>>(H, Jr, a);
+    build_jr_kernel<<<(unsigned)tiles, 256, 0, st>>>(H, Jr, a, bar);
     return cudaGetLastError();
 }
 

@@ -189,10 +189,17 @@ struct RitzOut {
     double resid;   // |beta_k * s_k| / ||s||
 };
 
-// Largest-magnitude Ritz pair of T_k (alpha, beta in FP64, k >= 1); writes the
-// unit vector s (FP64) to s_out.  Called by one full warp.
-static __device__ RitzOut ritz_largest_magnitude(const double* alpha, const double* beta, int k,
-                                          double beta_k, double* s_out, float* scratch) {
+// Largest-magnitude Ritz pair of T_k (alpha, beta in FP64, k >= 1), FP32
+// part: the extreme eigenvalue (multisection on both ends, ties to the
+// positive end) and its eigenvector by inverse iteration, left (unit max
+// norm) in scratch[3k'..] (k' = kMaxLanczos); resid = |beta_k s_k| / ||s||.
+// The trailing component of a converged Ritz vector is far below what an
+// FP32 eigenvalue resolves through the pivots of T - theta I, so it is read
+// off the inverse-iteration vector.  Enough to decide convergence; the FP64
+// refined pair comes from ritz_refine_fp64 on the same scratch.  Called by
+// one full warp.
+static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* beta, int k,
+                                            double beta_k, float* scratch) {
     const int lane = threadIdx.x & 31;
     float* al = scratch;
     float* be = al + kMaxLanczos;
@@ -238,7 +245,22 @@ static __device__ RitzOut ritz_largest_magnitude(const double* alpha, const doub
         }
     }
     __syncwarp();
-    // FP64 Rayleigh quotient of s, lane-parallel
+    float ss = 0.f;
+    for (int i = lane; i < k; i += 32) ss = fmaf(sv[i], sv[i], ss);
+    ss = warp_sum(ss);
+    RitzOut ro;
+    ro.theta = theta32;
+    ro.resid = fabs(beta_k) * (double)(fabsf(sv[k - 1]) * rsqrtf(ss));
+    return ro;
+}
+
+// FP64 refinement of the pair ritz_extreme_fp32 left in scratch: Rayleigh
+// quotient theta = s^T T s / s^T s, residual |beta_k s_k| / ||s||, and the
+// unit vector s (FP64) in s_out.  Called by one full warp.
+static __device__ RitzOut ritz_refine_fp64(const double* alpha, const double* beta, int k,
+                                           double beta_k, double* s_out, const float* scratch) {
+    const int lane = threadIdx.x & 31;
+    const float* sv = scratch + 3 * kMaxLanczos;
     double num = 0.0, den = 0.0;
     for (int i = lane; i < k; i += 32) {
         const double si = sv[i];
@@ -258,5 +280,11 @@ static __device__ RitzOut ritz_largest_magnitude(const double* alpha, const doub
     return ro;
 }
 
+// Both parts: the refined largest-magnitude Ritz pair.
+static __device__ RitzOut ritz_largest_magnitude(const double* alpha, const double* beta, int k,
+                                                 double beta_k, double* s_out, float* scratch) {
+    ritz_extreme_fp32(alpha, beta, k, beta_k, scratch);
+    return ritz_refine_fp64(alpha, beta, k, beta_k, s_out, scratch);
+}
 
 }  // namespace hoscf
