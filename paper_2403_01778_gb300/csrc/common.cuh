@@ -100,14 +100,31 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
                  : "memory");
 }
 
+// The same test with a suspend-time hint: a thread whose phase is not
+// complete sleeps until it completes or about `hint_ns` pass, instead of
+// returning at once (waiting warps then do not take issue slots).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity,
+                                                   uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for an mbarrier phase with a wall-clock bound.  Returns false (and
 // leaves the caller to record the timeout) when the bound passes.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
+    const uint32_t hint = (uint32_t)(limit_ns < 100000ull ? limit_ns : 100000ull);
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_hint(bar, parity, hint)) return true;
         if (global_timer_ns() - t0 > limit_ns) return false;
     }
 }

@@ -80,12 +80,17 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
 
 // Shared-memory layout of the tiled pass kernel, from a 1024-byte aligned
 // base: each of the 8 warps owns S ring slots of rows x 128 elements, one
-// mbarrier per slot and (FP8) two group scales per slot row; then the
-// double-buffered column-sum exchange [2][G][8][128] floats and its item
-// table (y2 offset, valid columns).
+// mbarrier per slot, (FP8) two group scales per slot row and (FP8 or no
+// ring) a rows x 36 float transpose for its row sums - otherwise the row
+// sums go through the warp's just-consumed slot; then the per-warp u_A
+// entries, the double-buffered column-sum
+// exchange [2][G][8][128] floats and its item table (y2 offset, valid
+// columns).
 struct TiledSmem {
-    size_t bars, scl, y2, off, cnt, total;
+    size_t bars, scl, ysc, ua, y2, off, cnt, total;
 };
+
+constexpr int kRowSumStride = 36;   // floats per row of the row-sum transpose
 
 HOSCF_HD inline TiledSmem tiled_smem(int S, int G, int rows, int es, bool fp8) {
     TiledSmem L;
@@ -95,6 +100,12 @@ HOSCF_HD inline TiledSmem tiled_smem(int S, int G, int rows, int es, bool fp8) {
     L.scl = o;
     o += fp8 ? (size_t)8 * S * rows * 2 * 4 : 0;
     o = (o + 15) & ~(size_t)15;
+    // per warp: rows x kRowSumStride floats for the row-sum transpose, unless
+    // the warp's just-consumed ring slot holds it (rows of >= 144 bytes)
+    L.ysc = o;
+    if (fp8 || S == 0 || 128 * es < kRowSumStride * 4) o += (size_t)8 * rows * kRowSumStride * 4;
+    L.ua = o;    // per warp: its rows' factor entries u_{d-1}[a]
+    o += (size_t)8 * 16 * 4;
     L.y2 = o;
     o += (size_t)2 * G * 8 * 128 * 4;
     L.off = o;

@@ -366,10 +366,17 @@ __global__ void __launch_bounds__(256, TiledOcc<E>::value)
     const int S = RING ? a.nstage : 0;
     const int G = a.group;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                               ~uintptr_t(1023));
+    // 1024-byte alignment by an offset into the shared array itself, so the
+    // compiler keeps shared-space (32-bit) addressing for everything below
+    uint8_t* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const TiledSmem L = tiled_smem(S, G, ROWS, (int)sizeof(E), F8);
     float* s_y2 = reinterpret_cast<float*>(smem + L.y2);          // [2][G][8][FB]
+    // row-sum transpose: the warp's just-consumed ring slot when its rows are
+    // wide enough (FP32, BF16), else a dedicated per-warp region
+    constexpr bool RS_IN_SLOT = RING && !F8 && 128 * sizeof(E) >= kRowSumStride * 4;
+    float* s_rs_own = reinterpret_cast<float*>(smem + L.ysc) +
+                      (size_t)(threadIdx.x >> 5) * ROWS * kRowSumStride;
+    float* s_ua = reinterpret_cast<float*>(smem + L.ua) + (threadIdx.x >> 5) * 16;   // its rows' u_A
     int64_t* s_off = reinterpret_cast<int64_t*>(smem + L.off);    // [2][G]
     int* s_cnt = reinterpret_cast<int*>(smem + L.cnt);            // [2][G]
 
@@ -456,7 +463,6 @@ __global__ void __launch_bounds__(256, TiledOcc<E>::value)
     // ---- consume side
     float2 acc[ROWS][2];
     float2 uB2[2];
-    float uAr[ROWS];
     const int64_t t_first = i0 / a.O;
     int64_t cc_o = i0 - t_first * a.O, cc_t = t_first - 1;   // tile set up on first item
     int64_t ar0 = 0, b0 = 0, y2off = 0, sflat = 0;
@@ -486,9 +492,11 @@ __global__ void __launch_bounds__(256, TiledOcc<E>::value)
         for (int q = 0; q < 4; ++q) ub[q] = b0 + q < a.B ? a.uB[b0 + q] : 0.f;
         uB2[0] = make_float2(ub[0], ub[1]);
         uB2[1] = make_float2(ub[2], ub[3]);
+        __syncwarp();
+        if (lane < ROWS) s_ua[lane] = ar0 + lane < a.A ? a.uA[ar0 + lane] : 0.f;
+        __syncwarp();
 #pragma unroll
         for (int r = 0; r < ROWS; ++r) {
-            uAr[r] = ar0 + r < a.A ? a.uA[ar0 + r] : 0.f;
             acc[r][0] = make_float2(0.f, 0.f);
             acc[r][1] = make_float2(0.f, 0.f);
         }
@@ -524,10 +532,7 @@ __global__ void __launch_bounds__(256, TiledOcc<E>::value)
         }
         const float wo = __ldg(wp);
         const float2 wo2 = make_float2(wo, wo);
-        constexpr int RP = ROWS <= 8 ? 8 : (ROWS <= 16 ? 16 : 32);
-        float y1[RP];
-#pragma unroll
-        for (int r = ROWS; r < RP; ++r) y1[r] = 0.f;
+        float y1[ROWS];
         float2 y2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         if (RING && ok) {
             // warp-uniform: once any lane gives up, the whole warp stops issuing
@@ -566,23 +571,41 @@ __global__ void __launch_bounds__(256, TiledOcc<E>::value)
             const float2 v0 = make_float2(v[0], v[1]), v1 = make_float2(v[2], v[3]);
             acc[r][0] = ffma2(wo2, v0, acc[r][0]);
             acc[r][1] = ffma2(wo2, v1, acc[r][1]);
-            const float2 ua2 = make_float2(uAr[r], uAr[r]);
+            const float ua = s_ua[r];
+            const float2 ua2 = make_float2(ua, ua);
             y2[0] = ffma2(v0, ua2, y2[0]);
             y2[1] = ffma2(v1, ua2, y2[1]);
             const float2 dd = ffma2(v1, uB2[1], make_float2(v0.x * uB2[0].x, v0.y * uB2[0].y));
             y1[r] = dd.x + dd.y;
         }
+        float* s_rs = RS_IN_SLOT ? reinterpret_cast<float*>(ring + (size_t)cs * SLOT) : s_rs_own;
         if (RING) {
-            __syncwarp();   // every lane is done with slot cs before it is refilled
+            __syncwarp();   // every lane is done with slot cs (refilled at the next issue)
             if (++cs == S) {
                 cs = 0;
                 cph ^= 1u;
             }
         }
-        // row sums -> y1 partial of this b-tile
-        int row;
-        const float ys = rs_reduce<RP>(y1, lane, row);
-        if ((lane & ((32 / RP) - 1)) == 0 && row < ROWS && ar0 + row < a.A) y1p[row] = ys;
+        // row sums -> y1 partial of this b-tile: the lanes' partials go through
+        // a shared-memory transpose (row r, lane l at r*36 + l: conflict-free
+        // both ways), then lanes 2r and 2r+1 each add 16 of row r's 32
+        // partials with four 16-byte loads and combine with one shuffle.
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) s_rs[r * kRowSumStride + lane] = y1[r];
+        __syncwarp();
+        {
+            const int row = lane >> 1;
+            float ys = 0.f;
+            if (row < ROWS) {
+                const float4* src = reinterpret_cast<const float4*>(s_rs + row * kRowSumStride + 16 * (lane & 1));
+                const float4 q0 = src[0], q1 = src[1], q2 = src[2], q3 = src[3];
+                ys = ((q0.x + q0.y) + (q0.z + q0.w)) + ((q1.x + q1.y) + (q1.z + q1.w)) +
+                     (((q2.x + q2.y) + (q2.z + q2.w)) + ((q3.x + q3.y) + (q3.z + q3.w)));
+            }
+            ys += __shfl_xor_sync(HOSCF_FULLMASK, ys, 1);
+            if ((lane & 1) == 0 && row < ROWS && ar0 + row < a.A) y1p[row] = ys;
+        }
+        __syncwarp();   // transpose read before the slot is refilled / rewritten
         // column partials -> exchange ring; summed over the 8 warps every G items
         float* sy = s_y2 + ((size_t)(gbuf * G + gj) * 8 + warp) * FB;
         *reinterpret_cast<float4*>(sy + 4 * lane) = make_float4(y2[0].x, y2[0].y, y2[1].x, y2[1].y);
