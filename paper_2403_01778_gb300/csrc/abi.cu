@@ -510,10 +510,16 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
         resid = sc[SC_KKT];
         r41 = sc[SC_R41];
         // precision form: move to the FP32 tensor once the residual reaches
-        // switch_tol or stops improving (the low-precision floor)
+        // switch_tol, stops improving (the low-precision floor), or is
+        // predicted to reach switch_tol at the next iterate (the observed
+        // contraction r_k / r_{k-1} applied once more) - so that the pass at
+        // that iterate is already an FP32 pass
         const bool stalled = Tr && !use_ref && iters > 0 && resid > 0.5 * prev_resid;
+        const bool predicted = Tr && !use_ref && iters > 0 && prev_resid > 0.0 &&
+                               std::isfinite(prev_resid) && resid * (resid / prev_resid) <= o.switch_tol;
         prev_resid = resid;
-        if (Tr && !use_ref && (resid <= o.switch_tol || stalled || sc[SC_CONVERGED] != 0.0)) {
+        if (Tr && !use_ref &&
+            (resid <= o.switch_tol || stalled || predicted || sc[SC_CONVERGED] != 0.0)) {
             // precision form: the low-precision tensor has done its part; the
             // remaining passes and the certificate use the FP32 tensor
             use_ref = true;
