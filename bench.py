@@ -299,7 +299,7 @@ def run_extras(P, T, u0, dev):
     import workloads as W
     ex = {}
     # headline workload: HOSCF vs iHOSCF to KKT residual 1e-6
-    for variant in ("hoscf", "ihoscf"):
+    for variant in ("hoscf", "ihoscf", "jacobi_hopm"):
         t, r = _timed(lambda: P.hoscf_solve(T, u0, tol=1e-6, max_iter=200, variant=variant))
         ex[f"time_to_residual_1e-6_{variant}"] = {
             "seconds": t, "iters": r.iters, "passes": r.passes, "resid": r.resid,

@@ -56,7 +56,9 @@ typedef enum {
 typedef enum {
     HOSCF_VARIANT_HOSCF = 0,   /* Algorithm 1 */
     HOSCF_VARIANT_IHOSCF = 1,  /* Sec. 4.4: RQI with J built at the new point x_k (one more pass) */
-    HOSCF_VARIANT_IHOSCF_PREV = 2 /* Sec. 4.4 read with J_{k-1} (tracks plain HOSCF) */
+    HOSCF_VARIANT_IHOSCF_PREV = 2, /* Sec. 4.4 read with J_{k-1} (tracks plain HOSCF) */
+    HOSCF_VARIANT_JACOBI_HOPM = 3  /* Sec. 1 / 6.1 comparison method: every factor at once,
+                                      u^(n) <- A x_{k!=n} u^(k) / ||.||, from the same blocks */
 } hoscf_variant;
 
 typedef struct hoscf_handle hoscf_handle;

@@ -363,12 +363,16 @@ def hoscf(T, u0_list, tol: float = 1e-8, max_iter: int = 200, variant: str = "ho
         used); y is kept if certified or |sigma(y)| >= |sigma(x_{k-1})|, else
         x_k is restored with one extra pass.  (One RQI step from x~_k with
         J_{k-1} returns x_k up to third-order terms, so this variant tracks
-        plain HOSCF.)"""
+        plain HOSCF.)
+    variant = "jacobi_hopm": the Jacobi form of HOPM the paper compares with
+        (Sec. 1, Sec. 6.1): every factor at once from the previous iterate,
+        u^(n) <- A x_{k!=n} u^(k) / ||.|| = g_n / ||g_n||, g_n read off the
+        blocks; same certificate and stopping rule as HOSCF."""
     dims = list(T.shape)
     d = len(dims)
     if d < 2:
         raise ValueError("order must be >= 2")
-    if variant not in ("hoscf", "ihoscf", "ihoscf_prev"):
+    if variant not in ("hoscf", "ihoscf", "ihoscf_prev", "jacobi_hopm"):
         raise ValueError(variant)
     u = _unit_blocks(u0_list)
     hist = []
@@ -385,6 +389,15 @@ def hoscf(T, u0_list, tol: float = 1e-8, max_iter: int = 200, variant: str = "ho
 
     Hp, sigma, r = build(u)
     while not (r <= tol or iters >= max_iter):
+        if variant == "jacobi_hopm":
+            g, _, _ = kkt_from_blocks(Hp, dims, u)
+            nrm = [np.linalg.norm(gn) for gn in g]
+            if min(nrm) == 0.0:
+                raise ZeroDivisionError("a factor's update A x_{k!=n} u^(k) is zero")
+            u = [gn / nn for gn, nn in zip(g, nrm)]
+            iters += 1
+            Hp, sigma, r = build(u)
+            continue
         J = nepv_matrix(Hp, dims)
         _, x = largest_magnitude_eigpair(J, concat(u) / np.sqrt(d))   # line 5
         u_k = normalise_blocks(x, dims)                   # lines 6-9

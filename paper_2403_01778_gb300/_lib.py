@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "NOT_CONVERGED
                 5: "NONFINITE", 6: "TIMEOUT", 7: "EUNSUPPORTED"}
 
 HOSCF_F32, HOSCF_BF16, HOSCF_F8E4M3 = 0, 1, 2
-VARIANTS = {"hoscf": 0, "ihoscf": 1, "ihoscf_prev": 2}
+VARIANTS = {"hoscf": 0, "ihoscf": 1, "ihoscf_prev": 2, "jacobi_hopm": 3}
 MAX_ORDER = 8
 
 # Every entry point the header declares (checked by the ABI test).

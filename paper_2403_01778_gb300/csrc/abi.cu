@@ -189,7 +189,7 @@ hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const 
                         const hoscf_opts* o, int check, double kkt_tol, cudaStream_t st,
                         double adapt = 0.0, int rqi = 0, float shift_add = 0.f,
                         const float* proj_u = nullptr, float scale_override = 0.f,
-                        double tol_override = 0.0) {
+                        double tol_override = 0.0, int hopm = 0) {
     char* eb = h->ws + L.off_eig;
     float* Jr = reinterpret_cast<float*>(eb + L.ep.off_jr);
     cudaError_t e = launch_build_jr(L.s, H, Jr, reinterpret_cast<unsigned*>(h->ws + kOffBar), st);
@@ -219,6 +219,7 @@ hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const 
     ll.shift_add = shift_add;
     ll.proj_u = proj_u;
     ll.scale_override = scale_override;
+    ll.hopm = hopm;
     if (tol_override > 0.0) ll.eig_tol = tol_override;
     ll.smem = L.ep.smem;
     e = launch_lanczos(L.s, ll, st);
@@ -413,7 +414,7 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
     if (opts) o = *opts;
     if (o.max_iter < 0 || !(o.tol >= 0)) return fail(h, HOSCF_EINVAL, "bad tol / max_iter");
     if (o.variant != HOSCF_VARIANT_HOSCF && o.variant != HOSCF_VARIANT_IHOSCF &&
-        o.variant != HOSCF_VARIANT_IHOSCF_PREV)
+        o.variant != HOSCF_VARIANT_IHOSCF_PREV && o.variant != HOSCF_VARIANT_JACOBI_HOPM)
         return fail(h, HOSCF_EINVAL, "unknown variant %d", o.variant);
     const hoscf_tensor_desc* Tr = o.refine;
     if (Tr) {
@@ -480,7 +481,8 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
     auto do_step = [&](const float* Hsrc, const float* u, float* u_res, int rqi, double* out,
                        int check = 1) -> hoscf_status {
         hoscf_status q = eig_launch(h, L, Hsrc, nullptr, u, nullptr, u_res, nullptr, &o, check,
-                                    o.tol, s, o.eig_adapt, rqi);
+                                    o.tol, s, o.eig_adapt, rqi, 0.f, nullptr, 0.f, 0.0,
+                                    o.variant == HOSCF_VARIANT_JACOBI_HOPM && rqi == 0 ? 1 : 0);
         if (q) return q;
         cudaError_t e = cudaMemcpyAsync(h->h_pinned, scal, sizeof(double) * SC_COUNT,
                                         cudaMemcpyDeviceToHost, s);
@@ -537,7 +539,7 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
         }
         if (iters >= o.max_iter) break;
         ++iters;
-        if (o.variant == HOSCF_VARIANT_HOSCF) {
+        if (o.variant == HOSCF_VARIANT_HOSCF || o.variant == HOSCF_VARIANT_JACOBI_HOPM) {
             std::swap(ucur, unext);
             st = do_pass(ucur, Hcur);
             if (st) return st;

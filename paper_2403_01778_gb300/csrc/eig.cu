@@ -58,6 +58,8 @@ struct EigArgs {
     float shift_add;        // operator: y = scale * Jr v + shift_add * v
     const float* proj_u;    // non-NULL: operator projected blockwise orthogonal to these unit
                             //    vectors (the tangent space of the factors)
+    int hopm;               // 1: after the certificate return the blocks of J x0 normalised
+                            //    (the Jacobi-HOPM update g_n / ||g_n||) instead of an eigenpair
     unsigned* bar;
     int* err;
     uint64_t timeout_ns;
@@ -359,6 +361,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     ro.theta = 0.0;
     ro.resid = 0.0;
     bool done = false;
+    bool hopm_out = false;
     for (int j = 0; j < a.mmax && !done; ++j) {
         // every CTA gets the whole current vector
         const float* src = vslot(j);
@@ -462,6 +465,14 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                     a.scal[SC_RITZRES] = b0;
                 }
                 return;
+            }
+            if (a.hopm) {
+                // Jacobi-HOPM: y = J x0 has blocks g_n / sqrt(d) (g_n = A x_{k!=n} u^(k))
+                for (int q = tid; q < nr; q += kEigThreads) xrow[q] = (double)Yl[q];
+                ro.theta = rho;
+                ro.resid = b0;
+                hopm_out = true;
+                break;
             }
             if (a.adapt > 0.0 && rho != 0.0) a.eig_tol = fmax(a.eig_tol, fmin(1e-5, a.adapt * r));
             // Lanczos start: v0 = x0/|x0|, w = J v0 - rho v0 (FP32)
@@ -625,10 +636,12 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         }
         return;
     }
-    for (int q = tid; q < nr; q += kEigThreads) {
-        double x = 0.0;
-        for (int i = 0; i < k; ++i) x += sv[i] * (double)Vl[(size_t)i * R + q];
-        xrow[q] = x;
+    if (!hopm_out) {
+        for (int q = tid; q < nr; q += kEigThreads) {
+            double x = 0.0;
+            for (int i = 0; i < k; ++i) x += sv[i] * (double)Vl[(size_t)i * R + q];
+            xrow[q] = x;
+        }
     }
     __syncthreads();
     auto xval = [&](int q) -> double { return xrow[q]; };
@@ -649,7 +662,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     const double* bn = hd + 6;
     double tot = 0.0;
     for (int m = 0; m < d; ++m) tot += bn[m];
-    const double sgn = (bn[d] < 0.0) ? -1.0 : 1.0;
+    const double sgn = (!hopm_out && bn[d] < 0.0) ? -1.0 : 1.0;   // HOPM keeps g's sign
     const double invx = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
     for (int q = r0 + tid; q < r1; q += kEigThreads) {
         const double x = xval(q - r0) * sgn;
@@ -930,6 +943,7 @@ cudaError_t launch_lanczos(const Shape& s, const LanczosLaunch& l, cudaStream_t 
     for (int k = 0; k <= s.d; ++k) a.moff[k] = s.moff[k];
     jr_offsets(s, a.jroff);
     a.scale = 1.0f / (float)(s.d - 1);
+    a.hopm = l.hopm;
     a.x0 = l.x0;
     a.u0 = l.u0;
     a.V = l.V;

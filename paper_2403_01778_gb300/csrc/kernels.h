@@ -67,6 +67,7 @@ struct LanczosLaunch {
     float shift_add = 0.f;        // operator: scale * Jr v + shift_add * v
     const float* proj_u = nullptr;   // project the operator onto the factors' tangent space
     float scale_override = 0.f;   // non-zero: mat-vec scale instead of 1/(d-1)
+    int hopm = 0;                 // 1: return the Jacobi-HOPM update instead of an eigenpair
 };
 
 enum EigScal {

@@ -209,6 +209,24 @@ def test_ihoscf_matches_oracle_on_example2(name, variant):
         assert r.passes <= 2 * r.iters + 1
 
 
+@pytest.mark.parametrize("dims,seed", [((20, 30, 25), 41), ((8, 9, 10, 11), 42), ((30, 20), 43)])
+def test_jacobi_hopm_matches_oracle(dims, seed):
+    """The paper's Jacobi-HOPM comparison method (every factor at once from
+    the same blocks) reaches the oracle's Jacobi-HOPM point; HOSCF needs no
+    more iterations (Table 1's direction)."""
+    T, _ = W.planted_cp(dims, [4.0, 1.0], seed=seed, noise_abs=0.3)
+    u0 = W.unit_gaussian_vectors(dims, seed + 1)
+    ref = oracle.hoscf(T.numpy(), [v.numpy() for v in u0], tol=1e-9, max_iter=5000,
+                       variant="jacobi_hopm")
+    assert ref.converged
+    r = P().hoscf_solve(T.cuda(), torch.cat(u0).cuda(), tol=1e-6, max_iter=5000,
+                        variant="jacobi_hopm")
+    assert r.converged
+    compare_solution(r, ref)
+    h = P().hoscf_solve(T.cuda(), torch.cat(u0).cuda(), tol=1e-6, max_iter=5000)
+    assert h.iters <= r.iters
+
+
 def test_solve_reports_kkt_consistent_with_oracle():
     """The residual and sigma the GPU certifies at its returned point agree
     with the oracle's direct KKT vectors at that same point."""

@@ -198,6 +198,47 @@ def test_hopm_cross_check():
     assert abs(s1.sigma - s2) < 1e-10 * s2
 
 
+# ------------------------------------------------------------- Jacobi-HOPM
+def test_jacobi_hopm_order2_is_power_iteration_to_top_singular_pair():
+    """d = 2: the Jacobi update (u1 <- A u2, u2 <- A^T u1, both from the old
+    pair, normalised) is a power iteration that converges to the top singular
+    triplet (Eckart-Young-Mirsky)."""
+    A = W.gaussian_tensor((30, 20), 15).numpy().astype(np.float64)
+    U, S, Vt = np.linalg.svd(A)
+    res = oracle.hoscf(A, rand_unit((30, 20), 16), tol=1e-11, max_iter=5000,
+                       variant="jacobi_hopm")
+    assert res.converged and res.iters > 1
+    assert abs(res.sigma - S[0]) < 1e-10 * S[0]
+    assert abs(abs(res.u[0] @ U[:, 0]) - 1) < 1e-10
+    assert abs(abs(res.u[1] @ Vt[0]) - 1) < 1e-10
+
+
+@pytest.mark.parametrize("dims", [(6, 7, 8), (5, 4, 6, 3)])
+def test_jacobi_hopm_noiseless_rank_one_in_one_step(dims):
+    """T = s a1 o ... o ad: A x_{k!=n} u^(k) = s prod_{k!=n} <a_k, u_k> a_n, so
+    one Jacobi step lands on the planted factors exactly."""
+    f = [v / np.linalg.norm(v) for v in rand_unit(dims, 23)]
+    T = 2.5 * W.outer([torch.from_numpy(v) for v in f]).numpy()
+    res = oracle.hoscf(T, rand_unit(dims, 24), tol=1e-13, max_iter=10, variant="jacobi_hopm")
+    assert res.converged and res.iters == 1
+    assert abs(res.sigma - 2.5) < 1e-12 * 2.5
+    for n in range(len(dims)):
+        assert abs(abs(res.u[n] @ f[n]) - 1) < 1e-12
+
+
+def test_jacobi_hopm_reaches_the_gauss_seidel_hopm_point():
+    dims = (8, 6, 7)
+    T, _ = W.planted_cp(dims, [5.0, 1.0], seed=51, noise_abs=0.5)
+    T = T.numpy()
+    u0 = rand_unit(dims, 52)
+    res = oracle.hoscf(T, u0, tol=1e-12, max_iter=2000, variant="jacobi_hopm")
+    s2, u2 = oracle.hopm(T, u0, tol=1e-12)
+    assert res.converged
+    assert abs(res.sigma - s2) < 1e-10 * s2
+    for a, b in zip(res.u, u2):
+        assert abs(abs(a @ b) - 1) < 1e-9
+
+
 # ------------------------------------------------------------- Tables 1-3
 @pytest.mark.parametrize("name", ["EXP", "ARCSIN"])
 def test_example2_table2_rho_and_table3_iterations(name):
