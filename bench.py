@@ -304,6 +304,16 @@ def run_extras(P, T, u0, dev):
         ex[f"time_to_residual_1e-6_{variant}"] = {
             "seconds": t, "iters": r.iters, "passes": r.passes, "resid": r.resid,
             "sigma": r.sigma, "converged": r.converged}
+    # greedy rank-5 (Sec. 1, Example 3) on the headline tensor: implicit
+    # deflation, every term from its own seeded start
+    u5 = torch.stack([torch.cat(W.unit_gaussian_vectors(T.shape, 100 + r, device=dev))
+                      for r in range(5)])
+    P.hoscf_solve_greedy(T, 5, u5, tol=1e-6, max_iter=200)     # warm
+    tg, gr = _timed(lambda: P.hoscf_solve_greedy(T, 5, u5, tol=1e-6, max_iter=200))
+    ex["greedy_rank5"] = {"seconds": tg, "sigmas": gr.sigmas, "res": gr.res,
+                          "iters": [i[0] for i in gr.infos], "passes": [i[1] for i in gr.infos],
+                          "converged": gr.converged,
+                          "planted_weights": [2.0 ** -r for r in range(5)]}
     # precision form: 200^4 planted rank one (sigma 100) + noise of norm 10
     T3 = W.config_tensor("cfg3_200p4", seed=0, device=dev)
     u3 = torch.cat(W.unit_gaussian_vectors(T3.shape, 1, device=dev))

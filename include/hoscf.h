@@ -224,6 +224,32 @@ hoscf_status hoscf_quantize(hoscf_handle* h, const float* x, int64_t n, int dtyp
                             float* scales, void* stream);
 
 /*
+ * hoscf_solve_greedy - rank-R approximation by the greedy rank-one update
+ * (Sec. 1, Example 3): for r = 1..R, B^(r) = sigma_r u_1^(r) o ... o u_d^(r)
+ * is the best rank-one approximation of A^(r) (hoscf_solve), and
+ * A^(r+1) = A^(r) - B^(r), A^(1) = A.  The tensor is never rewritten: every
+ * pass builds the blocks of A (eq. 3.3) and subtracts the earlier terms'
+ * contributions sigma_s prod_{k != m,n} <u_k^(s), u_k> u_m^(s) u_n^(s)^T.
+ *   T       as for hoscf_solve (opts->refine and the variants apply to every
+ *           term).
+ *   R       1 .. 32.
+ *   u0      device, R x n_tot floats: initial guess of each term.
+ *   u_out   device, R x n_tot floats: the terms' factors (row r is term r+1;
+ *           the rows already written are read back as the deflation list).
+ *   sigma_out  host, R doubles.  info host, R entries, or NULL.
+ *   res_out    host, R + 1 doubles, or NULL: ||A^(r)||_F / ||A||_F for
+ *           r = 1 .. R+1, from ||A^(r+1)||^2 = ||A^(r)||^2 - sigma_r^2 (the
+ *           identity at a KKT point) and ||A||_F (one extra read of the tensor
+ *           the certificates use).
+ * Synchronous.  Returns NOT_CONVERGED if any term did not converge (all
+ * terms are still computed), else the first error; EINVAL for R out of range.
+ */
+hoscf_status hoscf_solve_greedy(hoscf_handle* h, const hoscf_tensor_desc* T, int R,
+                                const float* u0, const hoscf_opts* opts, float* u_out,
+                                double* sigma_out, hoscf_info* info, double* res_out,
+                                void* stream);
+
+/*
  * hoscf_profile_enable / hoscf_profile_read - a measurement aid with no
  * counterpart in the paper: device time of the pass's streaming kernel alone
  * (the tiled, small-face or copy kernel, without the partial-sum reductions

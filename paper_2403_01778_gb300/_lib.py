@@ -26,7 +26,7 @@ EXPORTS = ("hoscf_create", "hoscf_destroy", "hoscf_last_error", "hoscf_opts_defa
            "hoscf_workspace_size", "hoscf_ttvc_blocks", "hoscf_eig_step", "hoscf_solve",
            "hoscf_solve_batched", "hoscf_backward", "hoscf_quantize",
            "hoscf_ttvc_blocks_static", "hoscf_profile_enable", "hoscf_profile_read",
-           "hoscf_selftest_timeout")
+           "hoscf_selftest_timeout", "hoscf_solve_greedy")
 
 
 class TensorDesc(ctypes.Structure):
@@ -86,6 +86,8 @@ def load():
     lib.hoscf_profile_enable.argtypes = [c_void_p, c_int]
     lib.hoscf_profile_read.argtypes = [c_void_p, P(c_int), P(c_double)]
     lib.hoscf_selftest_timeout.argtypes = [c_void_p, c_int, c_int64]
+    lib.hoscf_solve_greedy.argtypes = [c_void_p, P(TensorDesc), c_int, c_void_p, P(Opts),
+                                       c_void_p, P(c_double), P(Info), P(c_double), c_void_p]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name != "hoscf_last_error":

@@ -259,6 +259,52 @@ def hoscf_solve(T: torch.Tensor, u0: torch.Tensor, tol=1e-6, max_iter=200, varia
                        info.rqi_accepts, info.resid, info.resid_4_1, info.sigma_raw, st == 0)
 
 
+@dataclass
+class GreedyResult:
+    sigmas: list             # sigma_r of each rank-one term
+    u: torch.Tensor          # R x n_tot factors, float32
+    dims: tuple
+    infos: list              # per-term (iters, passes, resid, converged)
+    res: list                # ||A^(r)||_F / ||A||_F, r = 1 .. R+1
+    converged: bool
+
+    def factors(self, r):
+        out, o = [], 0
+        for n in self.dims:
+            out.append(self.u[r, o:o + n])
+            o += n
+        return out
+
+
+def hoscf_solve_greedy(T: torch.Tensor, R: int, u0: torch.Tensor, tol=1e-6, max_iter=200,
+                       variant="hoscf", scales=None, refine: torch.Tensor | None = None,
+                       switch_tol=None, eig_tol=None, eig_max_steps=None, eig_adapt=None,
+                       timeout_ns=None, stream=None) -> GreedyResult:
+    """Greedy rank-R approximation (Sec. 1, Example 3) with implicit deflation.
+    u0: R x n_tot float32 initial guesses.  Synchronous."""
+    d = _Desc(T, scales)
+    n = n_tot(d.shape)
+    u0 = u0.contiguous()
+    if u0.dtype != torch.float32 or u0.shape != (R, n):
+        raise ValueError("u0 must be float32 of shape (R, sum(dims))")
+    rd = _Desc(refine) if refine is not None else None
+    o = _opts(tol, max_iter, variant, eig_tol, eig_max_steps,
+              rd.desc if rd is not None else None, switch_tol, timeout_ns, eig_adapt)
+    u_out = torch.empty(R, n, device=T.device, dtype=torch.float32)
+    sig = (ctypes.c_double * R)()
+    infos = (Info * R)()
+    res = (ctypes.c_double * (R + 1))()
+    h = handle(T.device.index)
+    st = _lib.load().hoscf_solve_greedy(h, ctypes.byref(d.desc), int(R),
+                                        ctypes.c_void_p(u0.data_ptr()), ctypes.byref(o),
+                                        ctypes.c_void_p(u_out.data_ptr()), sig, infos, res,
+                                        _stream_ptr(stream))
+    _check(st, h, allow=(0, _lib.HOSCF_NOT_CONVERGED))
+    return GreedyResult([sig[i] for i in range(R)], u_out, d.shape,
+                        [(infos[i].iters, infos[i].passes, infos[i].resid) for i in range(R)],
+                        [res[i] for i in range(R + 1)], st == 0)
+
+
 def hoscf_quantize(x: torch.Tensor, dtype: str, stream=None):
     """FP32 -> ("bf16": bfloat16 tensor) or ("fp8": uint8 e4m3 codes, float32 scales)."""
     x = x.contiguous()

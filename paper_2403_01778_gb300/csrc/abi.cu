@@ -24,6 +24,10 @@ struct hoscf_handle {
     void* pinned_big = nullptr;   // descriptor / result staging of the batched solve
     size_t pinned_big_bytes = 0;
     cudaStream_t own = nullptr;   // private stream (graph capture)
+    // greedy rank-R: the terms found so far (factors, device) whose rank-one
+    // tensors every pass subtracts from the blocks (sigmas in the workspace head)
+    const float* defl_u = nullptr;
+    int defl_count = 0;
     // measurement aid: events around the streaming kernel of each
     // hoscf_ttvc_blocks call while enabled
     bool prof_on = false;
@@ -69,11 +73,18 @@ hoscf_status cuda_fail(hoscf_handle* h, cudaError_t e, const char* what) {
 constexpr size_t kProfMax = 65536;   // timed calls kept by the measurement aid
 
 // Fixed head of the workspace: device error word, grid barrier, scalars.
-constexpr size_t kHeadBytes = 4096;
+constexpr size_t kHeadBytes = 8192;
 constexpr size_t kOffErr = 0;        // int
 constexpr size_t kOffBar = 64;       // grid-barrier arrival counter (unsigned)
 constexpr size_t kOffScal = 256;     // 32 doubles
 constexpr size_t kOffNorms = 1024;   // up to 16 doubles
+constexpr int kMaxGreedy = 32;       // greedy terms: sigmas + <u^(s)_k, u_k> in the head
+constexpr size_t kOffDeflSigma = 1280;                               // kMaxGreedy doubles
+constexpr size_t kOffDeflDots = kOffDeflSigma + 8 * kMaxGreedy;      // kMaxGreedy x 8 doubles
+constexpr size_t kOffSumsq = 4096;                                   // 1 + kSumsqParts doubles
+constexpr int kSumsqParts = 256;
+static_assert(kOffDeflDots + 8 * kMaxGreedy * 8 <= kOffSumsq, "workspace head overflow");
+static_assert(kOffSumsq + 8 * (1 + kSumsqParts) <= kHeadBytes, "workspace head overflow");
 
 struct Layout {
     Shape s;
@@ -472,6 +483,14 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
         hoscf_status q = run_ttvc(S, pp, TT->dtype, TT->data, TT->scales, u, Hdst,
                                   h->ws + L.off_pass, dev_err(h), tmo, s, err);
         if (q) return fail(h, q, "%s", err.msg);
+        if (h->defl_count > 0) {
+            // greedy rank-R: blocks of the deflated tensor at u
+            cudaError_t e = launch_deflate(S, Hdst, u, h->defl_u,
+                                           reinterpret_cast<double*>(h->ws + kOffDeflSigma),
+                                           h->defl_count,
+                                           reinterpret_cast<double*>(h->ws + kOffDeflDots), s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "deflate");
+        }
         ++passes;
         if (use_ref) ++passes_ref;
         return HOSCF_OK;
@@ -738,6 +757,63 @@ hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const f
     float* coef = reinterpret_cast<float*>(h->ws + L.off_extra);
     CK(launch_grad_write(S, u, aptr, grad_sigma, coef, grad_T, s));
     CK(cudaStreamSynchronize(s));
+    return result;
+}
+
+hoscf_status hoscf_solve_greedy(hoscf_handle* h, const hoscf_tensor_desc* T, int R,
+                                const float* u0, const hoscf_opts* opts, float* u_out,
+                                double* sigma_out, hoscf_info* info, double* res_out,
+                                void* stream) {
+    if (!h) return HOSCF_EINVAL;
+    hoscf_status st = check_desc(h, T);
+    if (st) return st;
+    if (R < 1 || R > kMaxGreedy) return fail(h, HOSCF_EINVAL, "R must be 1..%d", kMaxGreedy);
+    if (!u0 || !u_out || !sigma_out) return fail(h, HOSCF_EINVAL, "NULL pointer argument");
+    Shape S;
+    if (!make_shape(T->order, T->dims, S)) return fail(h, HOSCF_EINVAL, "bad shape");
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the deflation state lives only for the duration of this call
+    struct Reset {
+        hoscf_handle* h;
+        ~Reset() {
+            h->defl_u = nullptr;
+            h->defl_count = 0;
+        }
+    } reset{h};
+    st = ensure_ws(h, kHeadBytes);
+    if (st) return st;
+    hoscf_status result = HOSCF_OK;
+    for (int r = 0; r < R; ++r) {
+        h->defl_u = u_out;        // rows 0 .. r-1 hold the terms found so far
+        h->defl_count = r;
+        if (r > 0)
+            CK(cudaMemcpyAsync(h->ws + kOffDeflSigma, sigma_out, sizeof(double) * r,
+                               cudaMemcpyHostToDevice, s));
+        double sig = 0.0;
+        st = hoscf_solve(h, T, u0 + (size_t)r * S.n_tot, opts, u_out + (size_t)r * S.n_tot, &sig,
+                         info ? &info[r] : nullptr, stream);
+        if (st != HOSCF_OK && st != HOSCF_NOT_CONVERGED) return st;
+        if (st == HOSCF_NOT_CONVERGED) result = HOSCF_NOT_CONVERGED;
+        sigma_out[r] = sig;
+    }
+    if (res_out) {
+        // ||A^(r+1)||^2 = ||A^(r)||^2 - sigma_r^2 (<A^(r), B^(r)> = sigma_r^2 at a
+        // KKT point); ||A||_F from the tensor the certificates use
+        const hoscf_tensor_desc* TA = (opts && opts->refine) ? opts->refine : T;
+        double* part = reinterpret_cast<double*>(h->ws + kOffSumsq) + 1;
+        double* tot = reinterpret_cast<double*>(h->ws + kOffSumsq);
+        CK(launch_sumsq(TA->dtype, TA->data, TA->scales, S.N, part, kSumsqParts, tot, s));
+        CK(cudaMemcpyAsync(h->h_pinned, tot, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double a2 = h->h_pinned[0];
+        double acc = 0.0;
+        res_out[0] = 1.0;
+        for (int r = 0; r < R; ++r) {
+            acc += sigma_out[r] * sigma_out[r];
+            res_out[r + 1] = a2 > 0.0 ? std::sqrt(std::max(0.0, a2 - acc) / a2) : 0.0;
+        }
+    }
     return result;
 }
 

@@ -35,6 +35,12 @@ cudaError_t launch_grad_write(const Shape& s, const float* u, const double* a, d
 cudaError_t launch_quantize(const float* x, int64_t n, int dtype, void* q, float* scales,
                             cudaStream_t st);
 
+// defl.cu
+cudaError_t launch_deflate(const Shape& s, float* H, const float* u, const float* uprev,
+                           const double* sigma, int R, double* dots, cudaStream_t st);
+cudaError_t launch_sumsq(int dtype, const void* data, const float* scales, int64_t n,
+                         double* part, int nparts, double* out, cudaStream_t st);
+
 // small.cu
 cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const void* data,
                       const float* scales, const float* u, float* H, char* ws, cudaStream_t st,

@@ -239,6 +239,52 @@ def test_jacobi_hopm_reaches_the_gauss_seidel_hopm_point():
         assert abs(abs(a @ b) - 1) < 1e-9
 
 
+# ------------------------------------------------------------- greedy rank-R
+def test_greedy_order2_is_truncated_svd():
+    """d = 2: each rank-one step takes the top singular triplet of the
+    deflated matrix, so R steps give the R leading singular triplets
+    (Eckart-Young-Mirsky) and ||A^(r)||_F^2 = sum_{i >= r} s_i^2."""
+    A = W.gaussian_tensor((12, 9), 31).numpy().astype(np.float64)
+    U, S, Vt = np.linalg.svd(A)
+    g = oracle.greedy(A, 4, [rand_unit((12, 9), 40 + r) for r in range(4)], tol=1e-12)
+    for r in range(4):
+        assert abs(g.sigmas[r] - S[r]) < 1e-10 * S[0]
+        assert abs(abs(g.factors[r][0] @ U[:, r]) - 1) < 1e-8
+        assert abs(abs(g.factors[r][1] @ Vt[r]) - 1) < 1e-8
+    nrm = np.linalg.norm(A)
+    for r in range(5):
+        assert abs(g.res[r] - np.sqrt(np.sum(S[r:] ** 2)) / nrm) < 1e-10
+
+
+def test_greedy_orthogonal_cp_exact_recovery():
+    """A sum of rank-one terms with mutually orthogonal factors in every mode
+    and distinct weights: greedy recovers the terms in decreasing order and
+    the residual vanishes after the last one."""
+    dims, w = (6, 7, 5), [5.0, 3.0, 1.5]
+    Q = [np.linalg.qr(np.random.default_rng(60 + n).standard_normal((m, 3)))[0] for n, m in enumerate(dims)]
+    T = sum(wr * np.einsum("i,j,k->ijk", Q[0][:, r], Q[1][:, r], Q[2][:, r]) for r, wr in enumerate(w))
+    g = oracle.greedy(T, 3, [rand_unit(dims, 70 + r) for r in range(3)], tol=1e-13)
+    for r in range(3):
+        assert abs(g.sigmas[r] - w[r]) < 1e-11 * w[0]
+        for n in range(3):
+            assert abs(abs(g.factors[r][n] @ Q[n][:, r]) - 1) < 1e-10
+    assert g.res[3] < 1e-12
+
+
+def test_greedy_residual_norm_identity():
+    """At a KKT point <A, B> = sigma^2 = ||B||^2, so the deflation removes
+    exactly sigma^2 of squared norm: ||A^(r+1)||^2 = ||A^(r)||^2 - sigma_r^2."""
+    dims = (7, 6, 5, 4)
+    T, _ = W.planted_cp(dims, [3.0, 2.0, 1.0], seed=81, noise_abs=0.3)
+    T = T.numpy().astype(np.float64)
+    g = oracle.greedy(T, 3, [rand_unit(dims, 90 + r) for r in range(3)], tol=1e-12)
+    n0 = np.linalg.norm(T)
+    for r in range(3):
+        lhs = (g.res[r + 1] * n0) ** 2
+        rhs = (g.res[r] * n0) ** 2 - g.sigmas[r] ** 2
+        assert abs(lhs - rhs) < 1e-9 * n0 ** 2
+
+
 # ------------------------------------------------------------- Tables 1-3
 @pytest.mark.parametrize("name", ["EXP", "ARCSIN"])
 def test_example2_table2_rho_and_table3_iterations(name):
