@@ -285,6 +285,17 @@ def test_greedy_residual_norm_identity():
         assert abs(lhs - rhs) < 1e-9 * n0 ** 2
 
 
+def test_example2_device_generator_matches_the_pinned_formulas():
+    """The on-device Example 2 generator (torch FP64) evaluates the same
+    closed forms as the numpy one the Table 2 / 3 pins use (run here on the
+    CPU through the same torch code)."""
+    for name in ("EXP", "ARCSIN", "TAN"):
+        a = W.example2(name).numpy()
+        b = W._example2_torch(name, "cpu").numpy()
+        assert a.shape == b.shape
+        np.testing.assert_allclose(b, a, rtol=1e-6, atol=1e-6)
+
+
 # ------------------------------------------------------------- Tables 1-3
 @pytest.mark.parametrize("name", ["EXP", "ARCSIN"])
 def test_example2_table2_rho_and_table3_iterations(name):

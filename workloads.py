@@ -98,8 +98,11 @@ def planted_cp(dims, weights, seed: int, noise_rel=None, noise_abs=None, device=
     return L, factors
 
 
-def example2(name: str):
-    """Closed-form tensors of the paper's Example 2 (Table 2), float32."""
+def example2(name: str, device="cpu"):
+    """Closed-form tensors of the paper's Example 2 (Table 2), float32.  On a
+    CUDA device the same formulas are evaluated there (FP64, then rounded)."""
+    if str(device) != "cpu":
+        return _example2_torch(name, device)
     name = name.upper()
     if name == "EXP":
         d, I = 3, 30
@@ -120,6 +123,26 @@ def example2(name: str):
     else:
         A = np.tan(np.sum(((-1.0) ** (j + 1)) * idx / j, axis=0))
     return torch.from_numpy(A.astype(np.float32))
+
+
+def _example2_torch(name: str, device):
+    """example2() with torch FP64 element-wise functions on `device`."""
+    name = name.upper()
+    d, I = {"EXP": (3, 30), "ARCSIN": (4, 20), "TAN": (5, 10)}[name]
+    ar = torch.arange(1, I + 1, dtype=torch.float64, device=device)
+    idx = torch.stack(torch.meshgrid(*([ar] * d), indexing="ij"))      # 1-based i_j
+    j = torch.arange(1, d + 1, dtype=torch.float64, device=device).reshape([d] + [1] * d)
+    sgn_j = torch.where(j % 2 == 1, 1.0, -1.0)                          # (-1)^(j+1)
+    if name == "EXP":
+        A = torch.sum(sgn_j * j * torch.exp(-idx), dim=0)
+    elif name == "ARCSIN":
+        ok = torch.all(idx >= j, dim=0)
+        sgn_i = torch.where(idx % 2 == 0, 1.0, -1.0)                    # (-1)^(i_j)
+        arg = torch.where(idx >= j, sgn_i * j / idx, torch.zeros_like(idx))
+        A = torch.where(ok, torch.sum(torch.asin(arg), dim=0), torch.zeros_like(ok, dtype=torch.float64))
+    else:
+        A = torch.tan(torch.sum(sgn_j * idx / j, dim=0))
+    return A.to(torch.float32).contiguous()
 
 
 def batched_dims(seed: int, count3: int = 768, count4: int = 256,
