@@ -181,9 +181,11 @@ def launches_per_step(dims):
 def traffic_bytes(dims, dtype):
     """DRAM bytes (read + write) of one launch of the streaming kernel, from
     an ncu capture of the same kernel build (dram__bytes_read.sum +
-    dram__bytes_write.sum; profiles/ttvc_tiled_fp32_1024cube.md); None for
-    workloads that capture does not cover."""
-    measured = {((1024, 1024, 1024), "f32"): 4295134976 + 79651328}
+    dram__bytes_write.sum; profiles/ttvc_tiled_fp32_1024cube_traffic.md,
+    profiles/ttvc_tiled_bf16_200p4_traffic.md); None for workloads no
+    capture covers."""
+    measured = {((1024, 1024, 1024), "f32"): 4295359488 + 79851776,
+                ((200, 200, 200, 200), "bf16"): 3382682880 + 136482304}
     return measured.get((tuple(dims), dtype))
 
 
