@@ -79,7 +79,7 @@ typedef struct {
     double eig_tol;            /* Lanczos stop: Ritz residual <= eig_tol * |theta| */
     int eig_max_steps;         /* Lanczos basis size limit (<= 128) */
     double eig_adapt;          /* hoscf_solve: eigen steps stop at the looser
-                                  max(eig_tol, min(1e-5, eig_adapt * r)), r the
+                                  max(eig_tol, min(1e-3, eig_adapt * r)), r the
                                   residual just certified (inexact SCF); 0 = off */
     const hoscf_tensor_desc* refine; /* precision form: FP32 copy of the same tensor, or NULL */
     double switch_tol;         /* precision form: residual at which passes move to `refine` */
@@ -137,7 +137,7 @@ hoscf_status hoscf_ttvc_blocks(hoscf_handle* h, const hoscf_tensor_desc* T, cons
  *   lambda_out    device, 1 double: the eigenvalue (ties between +l and -l
  *                 resolve to +l).
  * Lanczos with full reorthogonalisation (stop: Ritz residual <= tol*|theta|
- * with tol = max(eig_tol, min(1e-5, eig_adapt * sqrt(d) * r0)), r0 the
+ * with tol = max(eig_tol, min(1e-3, eig_adapt * sqrt(d) * r0)), r0 the
  * relative residual ||J x - rho x|| / |rho| of the normalised x_prev, or
  * tol = eig_tol when eig_adapt = 0; at most eig_max_steps; opts may be NULL
  * for defaults).  The start-point certificate, the tridiagonal matrix, the

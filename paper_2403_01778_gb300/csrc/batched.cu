@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
             ++iters;
             // ---- Lanczos for the largest-magnitude eigenpair (warm start at x)
             double etol = a.eig_tol;
-            if (a.eig_adapt > 0.0) etol = fmax(etol, fmin(1e-5, a.eig_adapt * resid));
+            if (a.eig_adapt > 0.0) etol = fmax(etol, fmin(1e-3, a.eig_adapt * resid));
             const float finv = (float)inv, frho = (float)rho;
             for (int q = tid; q < n; q += nt) {
                 V[q] *= finv;

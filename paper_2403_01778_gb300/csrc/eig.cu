@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 hopm_out = true;
                 break;
             }
-            if (a.adapt > 0.0 && rho != 0.0) a.eig_tol = fmax(a.eig_tol, fmin(1e-5, a.adapt * r));
+            if (a.adapt > 0.0 && rho != 0.0) a.eig_tol = fmax(a.eig_tol, fmin(1e-3, a.adapt * r));
             // Lanczos start: v0 = x0/|x0|, w = J v0 - rho v0 (FP32)
             const float finv = (float)inv, frho = (float)rho;
             for (int q = tid; q < nr; q += kEigThreads) {
