@@ -43,8 +43,8 @@ cudaError_t launch_sumsq(int dtype, const void* data, const float* scales, int64
 
 // small.cu
 cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const void* data,
-                      const float* scales, const float* u, float* H, char* ws, cudaStream_t st,
-                      const KernelEvents* kev = nullptr);
+                      const float* scales, const float* u, float* H, char* ws, int* dev_err,
+                      uint64_t timeout_ns, cudaStream_t st, const KernelEvents* kev = nullptr);
 
 // eig.cu
 struct LanczosLaunch {

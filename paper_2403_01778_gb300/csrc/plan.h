@@ -32,20 +32,40 @@ inline int block_index(int d, int m, int n) { return m * d - m * (m + 1) / 2 + (
 
 bool make_shape(int d, const int64_t* dims, Shape& s);
 
-// Small-face pass (A*B <= 1024): contiguous outer ranges per CTA, in-CTA fold.
+// Small-face pass (B <= 32, A*B <= 1024): groups of K consecutive faces
+// staged by bulk copies, contiguous outer ranges per CTA, in-CTA folds into a
+// per-CTA patch, then one reduce over the patches.
+constexpr int kSmallThreads = 256;
+constexpr int kSmallMaxK = 32;     // faces per group
+constexpr int kSmallMaxB = 32;     // face columns (row registers per thread)
+constexpr int kSmallMaxNm = kMaxOrder - 3;                    // outer modes but the fastest
+constexpr int kSmallMaxNq = kSmallMaxNm * (kSmallMaxNm - 1) / 2;
+
 struct SmallPlanInfo {
-    int G = 0;
-    int64_t L = 0;
+    int G = 0;                 // CTAs
+    int64_t L = 0;             // faces per CTA (a multiple of K)
+    int K = 0;                 // faces per group
+    int K1 = 0;                // faces per pass of the threads (K <= 2 K1)
+    int nstage = 0;            // bulk-copy ring slots
+    uint32_t stage_bytes = 0;  // bytes per slot (a multiple of 16)
+    int occ = 0;               // CTAs per SM the plan was made for
     int Rmax[kMaxOrder] = {0};
     int64_t x1off[kMaxOrder] = {0}, x2off[kMaxOrder] = {0}, poff[kMaxBlocks] = {0};
     int npairs = 0;
     int pm[kMaxBlocks] = {0}, pn[kMaxBlocks] = {0};
     int64_t patch_floats = 0;
+    int nsmax = 0;             // most runs of the fastest outer mode in one group
+    // shared-memory layout (bytes from a 128-byte aligned base)
+    uint32_t o_bars = 0, o_ring = 0, o_uA = 0, o_uB = 0, o_y1 = 0, o_y2 = 0, o_r = 0, o_S = 0,
+             o_meta = 0, o_first = 0, o_patch = 0, o_ur = 0, o_tab = 0;
+    int NR = 0;                // runs of the fastest outer mode a range touches
+    int uro[kMaxOrder] = {0};  // staged factor rows of outer mode m (offsets)
+    uint32_t meta_words = 0;   // per metadata slot
     size_t smem = 0;
     size_t off_patch = 0, off_cover = 0;   // workspace offsets (bytes)
 };
 
-bool make_small_plan(const Shape& s, int nsm, SmallPlanInfo& sp);
+bool make_small_plan(const Shape& s, int dtype, int nsm, SmallPlanInfo& sp);
 
 // Tiled pass configuration (face tiles of FA x FB, stream-K over
 // (tile, outer index) items).

@@ -1,225 +1,34 @@
 // All-pairs TTVc for tensors whose face (the two fastest modes, A x B) is
-// small (A*B <= 1024), e.g. 24x20x24x20x24x20 or 8^8 (paper Sec. 6.2 shapes).
+// small (B <= 32, A*B <= 1024), e.g. 24x20x24x20x24x20 or 8^8 (the shapes of
+// the paper's Sec. 6.2).
 //
 // The same factorisation as the tiled pass (eq. 3.3 split into a face block,
-// row sums y1, column sums y2 and their outer-mode contractions), but nothing
-// of size N/A or N/B goes back to memory: each CTA streams a contiguous range
-// of outer indices, one face per warp, keeps the face accumulator in
-// registers, and folds y1, y2 and r_o = <y1, u_A> straight into a
-// shared-memory patch of every other block (rows limited to the digits its
-// range covers).  Warps of a group of 8 faces hand their per-face results to
-// the CTA through shared memory and the fold walks them in warp order, so the
-// result is deterministic.  One reduce kernel then sums, for each output
-// entry, the patches of the CTAs that cover it, in CTA order.
+// row sums y1 = T_o u_B, column sums y2 = T_o^T u_A, r_o = <y1, u_A> and
+// their outer-mode contractions), organised for faces too small to tile:
+//
+// * Each CTA owns a contiguous range of outer indices (faces), which is one
+//   contiguous slab of the tensor.  It streams the slab in groups of K faces
+//   through a ring of shared-memory slots filled by bulk copies
+//   (cp.async.bulk, one elected thread, mbarrier transaction counts).
+// * Element work: thread (k, r) reads row r of face k (vector loads) and
+//   forms y1 and the face-block accumulation w_o T_o in registers; thread
+//   (k, b) reads column (pair) b of face k and forms y2.  Packed FP32x2 FMAs.
+// * Folds, two-level: the fastest outer mode c gets every face's y1, y2 and
+//   r; the other outer modes only the run sums over c (faces that share all
+//   other digits), sum_j u_c[j] y1(o_j), which carry the same information for
+//   them.  All folds go into a shared-memory patch of the CTA (rows limited to
+//   the digits its range covers), each patch entry updated by one thread in
+//   face order, so the result is deterministic.
+// * Per-face digits and factor products are advanced incrementally by one
+//   warp a group ahead (no 64-bit divisions in the loop).
+// One reduce kernel then sums, for each output entry, the patches of the CTAs
+// that cover it, in CTA order.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
-#include <type_traits>
-
-#include <cuda_fp16.h>
-#include <cuda_fp8.h>
-
-#include "common.cuh"
-#include "kernels.h"
-#include "plan.h"
+#include "small_kernel.cuh"
 
 namespace hoscf {
-
-struct SmallArgs {
-    const void* T;
-    int64_t O;
-    int A, B, F, Bp, D;
-    int dims[kMaxOrder];      // outer mode sizes
-    int64_t st[kMaxOrder];    // outer strides
-    int uoff[kMaxOrder];      // factor offsets of outer modes
-    int npairs;
-    int pm[kMaxBlocks], pn[kMaxBlocks];
-    const float* u;
-    int uAoff, uBoff;
-    int64_t L;                // outer indices per CTA
-    int G;
-    int Rmax[kMaxOrder];      // patch rows per outer mode
-    int64_t x1off[kMaxOrder], x2off[kMaxOrder], poff[kMaxBlocks];
-    int64_t patch_floats;     // per CTA: F + X1 + X2 + pairs
-    float* patch;             // G x patch_floats
-    int* cover;               // G x D x 2: first digit, row count
-    const float* scales;      // FP8 only: one per 128 flat elements
-};
-
-template <typename E>
-__device__ __forceinline__ float ld_elem(const E* p);
-template <>
-__device__ __forceinline__ float ld_elem<float>(const float* p) { return __ldcs(p); }
-template <>
-__device__ __forceinline__ float ld_elem<bf16_t>(const bf16_t* p) {
-    return __uint_as_float(static_cast<uint32_t>(__ldcs(reinterpret_cast<const unsigned short*>(p))) << 16);
-}
-template <>
-__device__ __forceinline__ float ld_elem<fp8_t>(const fp8_t* p) {
-    const __half_raw h = __nv_cvt_fp8_to_halfraw(
-        (__nv_fp8_storage_t)__ldcs(reinterpret_cast<const unsigned char*>(p)), __NV_E4M3);
-    return __half2float(*reinterpret_cast<const __half*>(&h));
-}
-
-constexpr int kSmallWarps = 8;
-
-template <typename E, int JF>
-__global__ void __launch_bounds__(256) ttvc_small_kernel(const SmallArgs a) {
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t c = blockIdx.x;
-    const int64_t o_lo = c * a.L;
-    const int64_t o_hi = min(a.O, o_lo + a.L);
-    const int A = a.A, B = a.B, F = a.F, Bp = a.Bp, D = a.D;
-    extern __shared__ __align__(16) float sm[];
-    float* uA = sm;                                        // A
-    float* uB = uA + ((A + 3) & ~3);                       // B
-    float* scratch = uB + ((B + 3) & ~3);                  // 8 x A*Bp (per-warp face)
-    const int tile = A * Bp;
-    float* gy1 = scratch + (size_t)kSmallWarps * tile;     // 8 x A
-    float* gy2 = gy1 + kSmallWarps * A;                    // 8 x B
-    float* gr = gy2 + kSmallWarps * B;                     // 8
-    float* gpi = gr + kSmallWarps;                         // 8 x D
-    float* gpi2 = gpi + kSmallWarps * kMaxOrder;           // 8 x npairs
-    int* grow = reinterpret_cast<int*>(gpi2 + kSmallWarps * kMaxBlocks);   // 8 x D
-    int* first = grow + kSmallWarps * kMaxOrder;           // D
-    float* patch = reinterpret_cast<float*>(first + kMaxOrder);   // X1, X2, pairs (local part)
-    const int64_t ploc = a.patch_floats - F;               // local patch floats (no face)
-
-    for (int i = tid; i < A; i += blockDim.x) uA[i] = a.u[a.uAoff + i];
-    for (int i = tid; i < B; i += blockDim.x) uB[i] = a.u[a.uBoff + i];
-    for (int64_t i = tid; i < ploc; i += blockDim.x) patch[i] = 0.f;
-    if (tid < D) {
-        const int m = tid;
-        const int64_t q0 = o_lo / a.st[m], q1 = (o_hi - 1) / a.st[m];
-        first[m] = (int)(q0 % a.dims[m]);
-        const int64_t rows = (q1 - q0 + 1 < (int64_t)a.dims[m]) ? q1 - q0 + 1 : (int64_t)a.dims[m];
-        a.cover[(c * D + m) * 2 + 0] = first[m];
-        a.cover[(c * D + m) * 2 + 1] = (int)rows;
-    }
-    // smem position of each of my face elements (row pitch Bp avoids bank conflicts)
-    int sidx[JF];
-#pragma unroll
-    for (int j = 0; j < JF; ++j) {
-        const int f = lane + 32 * j;
-        sidx[j] = f < F ? (f / B) * Bp + (f % B) : -1;
-    }
-    float hacc[JF];
-#pragma unroll
-    for (int j = 0; j < JF; ++j) hacc[j] = 0.f;
-    __syncthreads();
-    float* my = scratch + (size_t)warp * tile;
-    const E* Tp = reinterpret_cast<const E*>(a.T);
-
-    for (int64_t og = o_lo; og < o_hi; og += kSmallWarps) {
-        const int64_t o = og + warp;
-        if (o < o_hi) {
-            // outer digits and factor values (lane k < D owns mode k)
-            int dig = 0;
-            float val = 1.f;
-            if (lane < D) {
-                dig = (int)((o / a.st[lane]) % a.dims[lane]);
-                val = __ldg(a.u + a.uoff[lane] + dig);
-            }
-            float v[kMaxOrder];
-            float wo = 1.f;
-#pragma unroll
-            for (int k = 0; k < kMaxOrder; ++k) {
-                v[k] = __shfl_sync(HOSCF_FULLMASK, val, k);
-                if (k < D) wo *= v[k];
-            }
-            const E* face = Tp + (size_t)o * F;
-            float t[JF];
-#pragma unroll
-            for (int j = 0; j < JF; ++j) {
-                t[j] = sidx[j] >= 0 ? ld_elem<E>(face + lane + 32 * j) : 0.f;
-                if (std::is_same<E, fp8_t>::value && sidx[j] >= 0)
-                    t[j] *= __ldg(a.scales + ((o * F + lane + 32 * j) >> 7));
-            }
-#pragma unroll
-            for (int j = 0; j < JF; ++j) {
-                hacc[j] = fmaf(wo, t[j], hacc[j]);
-                if (sidx[j] >= 0) my[sidx[j]] = t[j];
-            }
-            __syncwarp();
-            float rpart = 0.f;
-            for (int r = lane; r < A; r += 32) {
-                float s = 0.f;
-                const float* row = my + r * Bp;
-                for (int b = 0; b < B; ++b) s = fmaf(row[b], uB[b], s);
-                gy1[warp * A + r] = s;
-                rpart = fmaf(s, uA[r], rpart);
-            }
-            for (int b = lane; b < B; b += 32) {
-                float s = 0.f;
-                for (int r = 0; r < A; ++r) s = fmaf(my[r * Bp + b], uA[r], s);
-                gy2[warp * B + b] = s;
-            }
-            rpart = warp_sum(rpart);
-            if (lane == 0) gr[warp] = rpart;
-            if (lane < D) {
-                float p = 1.f;
-#pragma unroll
-                for (int k = 0; k < kMaxOrder; ++k)
-                    if (k < D && k != lane) p *= v[k];
-                gpi[warp * kMaxOrder + lane] = p;
-                int rr = dig - first[lane];
-                if (rr < 0) rr += a.dims[lane];
-                grow[warp * kMaxOrder + lane] = rr;
-            }
-            for (int p = lane; p < a.npairs; p += 32) {
-                const int m = a.pm[p], n = a.pn[p];
-                float q = 1.f;
-#pragma unroll
-                for (int k = 0; k < kMaxOrder; ++k)
-                    if (k < D && k != m && k != n) q *= v[k];
-                gpi2[warp * kMaxBlocks + p] = q;
-            }
-        }
-        __syncthreads();
-        // fold the group's faces into the patch, in warp order
-        const int nw = (o_hi - og < kSmallWarps) ? (int)(o_hi - og) : kSmallWarps;
-        for (int idx = tid; idx < D * A; idx += blockDim.x) {
-            const int m = idx / A, col = idx - (idx / A) * A;
-            float* X = patch + a.x1off[m] + col;
-            for (int w = 0; w < nw; ++w) {
-                const int rr = grow[w * kMaxOrder + m];
-                X[rr * A] = fmaf(gpi[w * kMaxOrder + m], gy1[w * A + col], X[rr * A]);
-            }
-        }
-        for (int idx = tid; idx < D * B; idx += blockDim.x) {
-            const int m = idx / B, col = idx - (idx / B) * B;
-            float* X = patch + a.x2off[m] + col;
-            for (int w = 0; w < nw; ++w) {
-                const int rr = grow[w * kMaxOrder + m];
-                X[rr * B] = fmaf(gpi[w * kMaxOrder + m], gy2[w * B + col], X[rr * B]);
-            }
-        }
-        for (int p = tid; p < a.npairs; p += blockDim.x) {
-            const int m = a.pm[p], n = a.pn[p];
-            float* X = patch + a.poff[p];
-            const int Rn = a.Rmax[n];
-            for (int w = 0; w < nw; ++w) {
-                const int rm = grow[w * kMaxOrder + m], rn = grow[w * kMaxOrder + n];
-                X[rm * Rn + rn] = fmaf(gpi2[w * kMaxBlocks + p], gr[w], X[rm * Rn + rn]);
-            }
-        }
-        __syncthreads();
-    }
-    // face partial: warp accumulators -> scratch (8 x F) -> sum in warp order
-#pragma unroll
-    for (int j = 0; j < JF; ++j) {
-        const int f = lane + 32 * j;
-        if (f < F) scratch[(size_t)warp * F + f] = hacc[j];
-    }
-    __syncthreads();
-    float* out = a.patch + c * a.patch_floats;
-    for (int f = tid; f < F; f += blockDim.x) {
-        float s = 0.f;
-        for (int w = 0; w < kSmallWarps; ++w) s += scratch[(size_t)w * F + f];
-        out[f] = s;
-    }
-    for (int64_t i = tid; i < ploc; i += blockDim.x) out[F + i] = patch[i];
-}
 
 // Reduce: for every output entry, the patches of the CTAs whose digit ranges
 // cover it, in CTA order.
@@ -288,126 +97,224 @@ __global__ void small_reduce_kernel(const float* __restrict__ patch, const int* 
 }
 
 // ---------------------------------------------------------------- host
-static int small_jf(int F) {
-    const int need = (F + 31) / 32;
-    int jf = 1;
-    while (jf < need) jf <<= 1;
-    return jf;
+static uint32_t small_magic(uint32_t d) {
+    return d <= 1 ? 0u : (uint32_t)((1ull << 32) / d + 1);
 }
+static int small_es(int dtype) { return dtype == HOSCF_F32 ? 4 : (dtype == HOSCF_BF16 ? 2 : 1); }
+static uint32_t al16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
 
-static size_t small_smem(const Shape& s, const SmallPlanInfo& sp) {
-    const int A = (int)s.A, B = (int)s.B, Bp = (int)(s.B | 1);
-    return sizeof(float) * (((A + 3) & ~3) + ((B + 3) & ~3) + (size_t)kSmallWarps * A * Bp +
-                            kSmallWarps * A + kSmallWarps * B + kSmallWarps +
-                            kSmallWarps * kMaxOrder + kSmallWarps * kMaxBlocks) +
-           sizeof(int) * (kSmallWarps * kMaxOrder + kMaxOrder) +
-           sizeof(float) * (size_t)(sp.patch_floats - s.A * s.B) + 64;
-}
-
-bool make_small_plan(const Shape& s, int nsm, SmallPlanInfo& sp) {
-    sp = SmallPlanInfo();
-    if (s.d < 3) return false;
+// Patch rows for a range of L faces, offsets and the shared-memory layout.
+static bool small_layout(const Shape& s, int es, int64_t L, int S, SmallPlanInfo& sp) {
+    const int A = (int)s.A, B = (int)s.B, D = s.D, K = sp.K;
     const int64_t F = s.A * s.B;
-    if (F > 1024) return false;
-    const int D = s.D;
-    // candidate CTA counts: a few waves of the SMs, at least one group of faces each
-    for (int64_t target = 8LL * nsm; target >= 1; target /= 2) {
-        int64_t G = std::min<int64_t>(target, (s.O + kSmallWarps - 1) / kSmallWarps);
-        G = std::max<int64_t>(G, 1);
-        int64_t L = (s.O + G - 1) / G;
-        L = (L + kSmallWarps - 1) / kSmallWarps * kSmallWarps;
-        G = (s.O + L - 1) / L;
-        int64_t off = 0;
-        for (int m = 0; m < D; ++m) {
-            const int64_t st = s.ost[m];
-            sp.Rmax[m] = (int)std::min<int64_t>(s.dims[m], (L + st - 1) / st + 1);
+    int64_t off = 0;
+    for (int m = 0; m < D; ++m)
+        sp.Rmax[m] = (int)std::min<int64_t>(s.dims[m], (L + s.ost[m] - 1) / s.ost[m] + 1);
+    // X1 / X2 blocks start on 16-byte boundaries (float4 folds when A and B
+    // are multiples of 4)
+    for (int m = 0; m < D; ++m) {
+        sp.x1off[m] = off;
+        off = (off + (int64_t)sp.Rmax[m] * A + 3) & ~3LL;
+    }
+    for (int m = 0; m < D; ++m) {
+        sp.x2off[m] = off;
+        off = (off + (int64_t)sp.Rmax[m] * B + 3) & ~3LL;
+    }
+    int np = 0;
+    for (int m = 0; m < D; ++m)
+        for (int n = m + 1; n < D; ++n) {
+            sp.pm[np] = m;
+            sp.pn[np] = n;
+            sp.poff[np] = off;
+            off += (int64_t)sp.Rmax[m] * sp.Rmax[n];
+            ++np;
         }
-        for (int m = 0; m < D; ++m) {
-            sp.x1off[m] = off;
-            off += (int64_t)sp.Rmax[m] * s.A;
-        }
-        for (int m = 0; m < D; ++m) {
-            sp.x2off[m] = off;
-            off += (int64_t)sp.Rmax[m] * s.B;
-        }
-        int np = 0;
-        for (int m = 0; m < D; ++m)
-            for (int n = m + 1; n < D; ++n) {
-                sp.pm[np] = m;
-                sp.pn[np] = n;
-                sp.poff[np] = off;
-                off += (int64_t)sp.Rmax[m] * sp.Rmax[n];
-                ++np;
+    sp.npairs = np;
+    sp.patch_floats = F + off;
+    if (sp.patch_floats > (1LL << 30)) return false;
+    const int C = (int)s.dims[D - 1];
+    sp.nsmax = std::min(K, (K + C - 1) / C + 1);
+    const int nm = D - 1, nq = nm * (nm - 1) / 2;
+    sp.nstage = S;
+    sp.stage_bytes = al16((uint64_t)K * F * es) + 16;
+    uint64_t o = 0;
+    sp.o_bars = (uint32_t)o;
+    o = al16(o + 8ull * S);
+    sp.o_ring = (uint32_t)o;
+    o = al16(o + std::max<uint64_t>((uint64_t)S * sp.stage_bytes, 4ull * sp.K1 * F));
+    sp.o_uA = (uint32_t)o;
+    o = al16(o + 4ull * ((A + 3) & ~3));
+    sp.o_uB = (uint32_t)o;
+    o = al16(o + 4ull * kSmallMaxB);
+    sp.o_y1 = (uint32_t)o;
+    o = al16(o + 8ull * K * A);
+    sp.o_y2 = (uint32_t)o;
+    o = al16(o + 8ull * K * B);
+    sp.o_r = (uint32_t)o;
+    o = al16(o + 8ull * K);
+    sp.o_S = (uint32_t)o;
+    o = al16(o + 8ull * sp.nsmax * (A + B));
+    sp.meta_words = small_meta_words(K, sp.nsmax);
+    sp.o_meta = (uint32_t)o;
+    o = al16(o + 12ull * sp.meta_words);
+    // runs of mode c a range of L faces touches
+    sp.NR = (int)((L + C - 2) / C + 1);
+    sp.o_tab = (uint32_t)o;
+    o = al16(o + 4ull * small_table_words(sp.NR, nm, nq));
+    sp.o_first = (uint32_t)o;
+    o = al16(o + 4ull * kMaxOrder);
+    sp.o_patch = (uint32_t)o;
+    o = al16(o + 4ull * (uint64_t)off);
+    int64_t nur = 0;
+    for (int m = 0; m < D; ++m) {
+        sp.uro[m] = (int)nur;
+        nur += sp.Rmax[m];
+    }
+    sp.o_ur = (uint32_t)o;
+    o = al16(o + 4ull * (uint64_t)nur);
+    sp.smem = o + 128;
+    return true;
+}
+
+bool make_small_plan(const Shape& s, int dtype, int nsm, SmallPlanInfo& sp) {
+    sp = SmallPlanInfo();
+    if (s.d < 3 || s.D < 1) return false;
+    const int64_t A = s.A, B = s.B, F = A * B;
+    if (B > kSmallMaxB || F > 1024 || A > kSmallThreads) return false;
+    // K1 faces per pass of the threads (thread per face row and per face
+    // column), two passes per group where that stays within 32 faces
+    const int K1 = (int)std::min<int64_t>(kSmallThreads / A, kSmallThreads / B);
+    if (K1 < 1) return false;
+    const int K = std::min(kSmallMaxK, 2 * K1);
+    sp.K = K;
+    sp.K1 = K1;
+    const int es = small_es(dtype);
+    const uint32_t sb = al16((uint64_t)K * F * es) + 16;
+    nsm = std::max(1, nsm);
+    // one wave of CTAs (2 per SM, else 1); more, with shorter ranges, when
+    // the patch of a long range does not fit in shared memory
+    // rows of at most 16 elements keep the kernel within 80 registers (3 CTAs
+    // per SM); wider rows within 128 (2 CTAs)
+    for (int occ = B <= 16 ? 3 : 2; occ >= 1; --occ) {
+        const size_t cap = occ == 3 ? 73 * 1024 : occ == 2 ? 110 * 1024 : 220 * 1024;
+        for (int64_t Gt = (int64_t)occ * nsm; ; Gt *= 2) {
+            int64_t G = std::min<int64_t>(Gt, (s.O + K - 1) / K);
+            G = std::max<int64_t>(G, 1);
+            int64_t L = (s.O + G - 1) / G;
+            L = (L + K - 1) / K * K;
+            G = (s.O + L - 1) / L;
+            SmallPlanInfo t = sp;
+            // ring slots: what the rest leaves, 2 .. 8 and at most 96 KB
+            bool fits = small_layout(s, es, L, 2, t) && t.smem <= cap;
+            if (fits) {
+                const int S = (int)std::max<int64_t>(
+                    2, std::min<int64_t>({8, 2 + (int64_t)(cap - t.smem) / sb, 96 * 1024 / sb}));
+                fits = small_layout(s, es, L, S, t) && t.smem <= cap;
             }
-        sp.npairs = np;
-        sp.patch_floats = F + off;
-        sp.G = (int)G;
-        sp.L = L;
-        sp.smem = small_smem(s, sp);
-        if (sp.smem <= 200 * 1024) return true;
+            if (fits) {
+                t.G = (int)G;
+                t.L = L;
+                t.occ = occ;
+                sp = t;
+                return true;
+            }
+            if (L <= K || Gt > (1LL << 24)) break;
+        }
     }
     return false;
 }
 
-template <typename E>
-static cudaError_t launch_small_t(const Shape& s, const SmallPlanInfo& sp, const SmallArgs& a,
-                                  cudaStream_t st, const KernelEvents* kev) {
-    const int jf = small_jf((int)(s.A * s.B));
-    void (*k)(const SmallArgs) = nullptr;
-    switch (jf) {
-        case 1: k = ttvc_small_kernel<E, 1>; break;
-        case 2: k = ttvc_small_kernel<E, 2>; break;
-        case 4: k = ttvc_small_kernel<E, 4>; break;
-        case 8: k = ttvc_small_kernel<E, 8>; break;
-        case 16: k = ttvc_small_kernel<E, 16>; break;
-        default: k = ttvc_small_kernel<E, 32>; break;
-    }
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
-    if (e != cudaSuccess) return e;
-    if (kev) cudaEventRecord(kev->begin, st);
-    k<<<sp.G, 256, sp.smem, st>>>(a);
-    if (kev) cudaEventRecord(kev->end, st);
-    return cudaGetLastError();
-}
-
 cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const void* data,
-                      const float* scales, const float* u, float* H, char* ws, cudaStream_t st,
-                      const KernelEvents* kev) {
+                      const float* scales, const float* u, float* H, char* ws, int* dev_err,
+                      uint64_t timeout_ns, cudaStream_t st, const KernelEvents* kev) {
+    // row / column-pair vector loads need B % 4 == 0 and 16-byte aligned
+    // faces and rows (then every slot's data starts 16-byte aligned)
+    const int es = small_es(dtype);
+    const bool vec = dtype != HOSCF_F8E4M3 && s.B % 4 == 0 &&
+                     (reinterpret_cast<uintptr_t>(data) & 15u) == 0 && (s.A * s.B * es) % 16 == 0;
+    const bool vec_cols = vec;
     SmallArgs a;
     memset(&a, 0, sizeof(a));
     a.T = data;
+    a.scales = scales;
+    a.u = u;
+    a.patch = reinterpret_cast<float*>(ws + sp.off_patch);
+    a.cover = reinterpret_cast<int*>(ws + sp.off_cover);
+    a.err = dev_err;
+    a.timeout_ns = timeout_ns ? timeout_ns : 2000000000ull;
     a.O = s.O;
+    a.L = sp.L;
     a.A = (int)s.A;
     a.B = (int)s.B;
     a.F = (int)(s.A * s.B);
-    a.Bp = (int)(s.B | 1);
     a.D = s.D;
+    a.K = sp.K;
+    a.K1 = sp.K1;
+    a.nsmax = sp.nsmax;
+    a.C = (int)s.dims[s.D - 1];
+    a.nstage = sp.nstage;
+    a.stage_bytes = sp.stage_bytes;
+    a.mag_ab = small_magic((uint32_t)(a.A + a.B));
+    a.mag_nm = small_magic((uint32_t)std::max(1, s.D - 1));
+    a.mag_c = small_magic((uint32_t)std::min<int64_t>(s.dims[s.D - 1], 1 << 15));
+    a.v4 = (a.A % 4 == 0 && a.B % 4 == 0) ? 1 : 0;
+    a.mag_ab4 = small_magic((uint32_t)std::max(1, (a.A + a.B) / 4));
+    for (int k = 0; k < s.D; ++k) {
+        a.magd[k] = small_magic((uint32_t)std::min<int64_t>(s.dims[k], 1 << 15));
+        a.uro[k] = sp.uro[k];
+    }
     for (int k = 0; k < s.D; ++k) {
         a.dims[k] = (int)s.dims[k];
         a.st[k] = s.ost[k];
         a.uoff[k] = (int)s.moff[k];
         a.Rmax[k] = sp.Rmax[k];
-        a.x1off[k] = sp.x1off[k];
-        a.x2off[k] = sp.x2off[k];
+        a.x1off[k] = (int)sp.x1off[k];
+        a.x2off[k] = (int)sp.x2off[k];
     }
-    a.npairs = sp.npairs;
-    for (int p = 0; p < sp.npairs; ++p) {
-        a.pm[p] = sp.pm[p];
-        a.pn[p] = sp.pn[p];
-        a.poff[p] = sp.poff[p];
-    }
-    a.u = u;
     a.uAoff = (int)s.moff[s.d - 2];
     a.uBoff = (int)s.moff[s.d - 1];
-    a.L = sp.L;
-    a.G = sp.G;
+    const int c = s.D - 1;
+    for (int p = 0; p < sp.npairs; ++p) {
+        if (sp.pn[p] == c) {
+            a.pcoff[sp.pm[p]] = (int)sp.poff[p];
+        } else {
+            a.qm[a.nq] = sp.pm[p];
+            a.qn[a.nq] = sp.pn[p];
+            a.qoff[a.nq] = (int)sp.poff[p];
+            ++a.nq;
+        }
+    }
     a.patch_floats = sp.patch_floats;
-    a.patch = reinterpret_cast<float*>(ws + sp.off_patch);
-    a.cover = reinterpret_cast<int*>(ws + sp.off_cover);
-    a.scales = scales;
-    cudaError_t e = dtype == HOSCF_F32    ? launch_small_t<float>(s, sp, a, st, kev)
-                    : dtype == HOSCF_BF16 ? launch_small_t<bf16_t>(s, sp, a, st, kev)
-                                          : launch_small_t<fp8_t>(s, sp, a, st, kev);
+    a.o_bars = sp.o_bars;
+    a.o_ring = sp.o_ring;
+    a.o_uA = sp.o_uA;
+    a.o_uB = sp.o_uB;
+    a.o_y1 = sp.o_y1;
+    a.o_y2 = sp.o_y2;
+    a.o_r = sp.o_r;
+    a.o_S = sp.o_S;
+    a.o_meta = sp.o_meta;
+    a.o_first = sp.o_first;
+    a.o_patch = sp.o_patch;
+    a.o_ur = sp.o_ur;
+    a.o_tab = sp.o_tab;
+    a.NR = sp.NR;
+    a.mag_bc = small_magic((uint32_t)(vec_cols ? a.B / 2 : a.B));
+    {
+        const int ncol = a.v4 ? (a.A + a.B) / 4 : a.A + a.B;
+        int P = 1;
+        while (P < ncol && P < 32) P <<= 1;
+        a.pcol = P;
+    }
+    a.meta_words = sp.meta_words;
+
+    cudaError_t e;
+    if (dtype == HOSCF_F32)
+        e = launch_small_f32(sp, a, vec, st, kev);
+    else if (dtype == HOSCF_BF16)
+        e = launch_small_bf16(sp, a, vec, st, kev);
+    else
+        e = launch_small_bm<fp8_t, false>(sp, a, st, kev);
     if (e != cudaSuccess) return e;
     SmallReduceArgs r;
     memset(&r, 0, sizeof(r));

@@ -78,7 +78,7 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
         return true;
     }
     const int es = elem_size(dtype);
-    if (make_small_plan(s, nsm, p.sp)) {
+    if (make_small_plan(s, dtype, nsm, p.sp)) {
         p.small = true;
         size_t off = 0;
         p.sp.off_patch = off;
@@ -318,17 +318,6 @@ __device__ __forceinline__ void apply_scales(const float* __restrict__ scales, i
     const float s1 = ((f0 + 3) >> 7) != g0 ? __ldg(scales + g0 + 1) : s0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) v[c] *= (((f0 + c) >> 7) == g0) ? s0 : s1;
-}
-
-// Packed FP32 (two lanes per instruction, IEEE fma / mul per lane, so the
-// results equal the scalar ones bit for bit).
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;"
-        : "=l"(d)
-        : "l"(*reinterpret_cast<const uint64_t*>(&a)), "l"(*reinterpret_cast<const uint64_t*>(&b)),
-          "l"(*reinterpret_cast<const uint64_t*>(&c)));
-    return *reinterpret_cast<const float2*>(&d);
 }
 
 // How each warp gets its tile rows.
@@ -991,7 +980,7 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         return HOSCF_OK;
     }
     if (p.small) {
-        HOSCF_CK(run_small(s, p.sp, dtype, data, scales, u, H, ws, st, kev));
+        HOSCF_CK(run_small(s, p.sp, dtype, data, scales, u, H, ws, dev_err, timeout_ns, st, kev));
         return HOSCF_OK;
     }
     const OuterInfo oi = make_outer(s);
