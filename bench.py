@@ -162,16 +162,17 @@ def whole_job_gbs(nbytes, steps, world, ms):
 
 def launches_per_step(dims):
     """Kernels the library launches for one step (pass + eigen step).
-    Pass: d = 2 copies the matrix (1); a face A*B <= 1024 takes the
-    small-face path (kernel + reduce: 2, if its plan fits shared memory);
-    otherwise the streaming kernel and its reduction (2), plus for d >= 4
-    the outer weights, the per-mode weights, two cross folds (5) and, with
-    two or more outer modes, the pair folds (2).  Eigen step: Jr build +
-    Lanczos (2)."""
+    Pass: d = 2 copies the matrix (1); a face with B <= 32, A <= 256 and
+    A*B <= 1024 takes the small-face path (kernel + patch reduce: 2);
+    otherwise the streaming kernel and its reduction (face block, y1, y2: 2),
+    plus for d >= 4 the outer weights, the per-mode weights and two cross
+    folds (4) and, with two or more outer modes, the r and pair folds (2).
+    Eigen step: Jr build + Lanczos (2)."""
     d = len(dims)
+    A, B = (dims[-2], dims[-1]) if d >= 2 else (1, 1)
     if d == 2:
         npass = 1
-    elif dims[-1] * dims[-2] <= 1024:
+    elif B <= 32 and A <= 256 and A * B <= 1024:
         npass = 2
     else:
         npass = 2 if d == 3 else 2 + 4 + (2 if d - 2 >= 2 else 0)

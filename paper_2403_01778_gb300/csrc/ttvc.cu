@@ -683,10 +683,41 @@ __device__ __forceinline__ float sum_strided(const float* __restrict__ x, size_t
     return (a0 + a1) + (a2 + a3);
 }
 
+// sum_{p < n} x[p * stride .. + 3] (16-byte aligned rows): four partial
+// sums in flight, combined in the same fixed order as sum_strided.
+__device__ __forceinline__ float4 sum_strided4(const float* __restrict__ x, size_t stride, int64_t n) {
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+    int64_t p = 0;
+    for (; p + 4 <= n; p += 4) {
+        const float4 v0 = __ldg(reinterpret_cast<const float4*>(x + (size_t)p * stride));
+        const float4 v1 = __ldg(reinterpret_cast<const float4*>(x + (size_t)(p + 1) * stride));
+        const float4 v2 = __ldg(reinterpret_cast<const float4*>(x + (size_t)(p + 2) * stride));
+        const float4 v3 = __ldg(reinterpret_cast<const float4*>(x + (size_t)(p + 3) * stride));
+        a0.x += v0.x; a0.y += v0.y; a0.z += v0.z; a0.w += v0.w;
+        a1.x += v1.x; a1.y += v1.y; a1.z += v1.z; a1.w += v1.w;
+        a2.x += v2.x; a2.y += v2.y; a2.z += v2.z; a2.w += v2.w;
+        a3.x += v3.x; a3.y += v3.y; a3.z += v3.z; a3.w += v3.w;
+    }
+    for (; p < n; ++p) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(x + (size_t)p * stride));
+        a0.x += v.x; a0.y += v.y; a0.z += v.z; a0.w += v.w;
+    }
+    return make_float4((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y),
+                       (a0.z + a1.z) + (a2.z + a3.z), (a0.w + a1.w) + (a2.w + a3.w));
+}
+
 __global__ void __launch_bounds__(256) reduce_pass_kernel(const ReduceArgs r) {
     const int col = threadIdx.x & 127;
     const int64_t nuF = r.TT * r.FA;
-    const int64_t nu1 = (r.n1 + 127) / 128, nu2 = (r.n2 + 127) / 128;
+    // y1 / y2 units: 128 threads x 4 consecutive entries (16-byte loads, four
+    // partials in flight) when n % 4 == 0 and both arrays start 16-byte
+    // aligned, else 128 x 1
+    const bool v1 = (r.n1 & 3) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(r.y1p) | reinterpret_cast<uintptr_t>(r.y1)) & 15u) == 0;
+    const bool v2 = (r.n2 & 3) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(r.y2p) | reinterpret_cast<uintptr_t>(r.y2)) & 15u) == 0;
+    const int64_t e1 = v1 ? 512 : 128, e2 = v2 ? 512 : 128;
+    const int64_t nu1 = (r.n1 + e1 - 1) / e1, nu2 = (r.n2 + e2 - 1) / e2;
     const int64_t total = nuF + nu1 + nu2;
     for (int64_t u = blockIdx.x * 2 + (threadIdx.x >> 7); u < total; u += (int64_t)gridDim.x * 2) {
         if (u < nuF) {
@@ -703,13 +734,25 @@ __global__ void __launch_bounds__(256) reduce_pass_kernel(const ReduceArgs r) {
             r.face[aa * r.B + bb] =
                 first + sum_strided(r.hp + (size_t)(c_lo + 1) * 2 * tile + inner, 2 * tile, c_hi - c_lo);
         } else if (u < nuF + nu1) {
-            const int64_t i = (u - nuF) * 128 + col;
-            if (i >= r.n1) continue;
-            r.y1[i] = sum_strided(r.y1p + i, (size_t)r.n1, r.np1);
+            if (v1) {
+                const int64_t i = (u - nuF) * 512 + 4 * col;
+                if (i >= r.n1) continue;
+                *reinterpret_cast<float4*>(r.y1 + i) = sum_strided4(r.y1p + i, (size_t)r.n1, r.np1);
+            } else {
+                const int64_t i = (u - nuF) * 128 + col;
+                if (i >= r.n1) continue;
+                r.y1[i] = sum_strided(r.y1p + i, (size_t)r.n1, r.np1);
+            }
         } else {
-            const int64_t i = (u - nuF - nu1) * 128 + col;
-            if (i >= r.n2) continue;
-            r.y2[i] = sum_strided(r.y2p + i, (size_t)r.n2, r.np2);
+            if (v2) {
+                const int64_t i = (u - nuF - nu1) * 512 + 4 * col;
+                if (i >= r.n2) continue;
+                *reinterpret_cast<float4*>(r.y2 + i) = sum_strided4(r.y2p + i, (size_t)r.n2, r.np2);
+            } else {
+                const int64_t i = (u - nuF - nu1) * 128 + col;
+                if (i >= r.n2) continue;
+                r.y2[i] = sum_strided(r.y2p + i, (size_t)r.n2, r.np2);
+            }
         }
     }
 }
