@@ -165,9 +165,10 @@ def launches_per_step(dims):
     Pass: d = 2 copies the matrix (1); a face with B <= 32, A <= 256 and
     A*B <= 1024 takes the small-face path (kernel + patch reduce: 2);
     otherwise the streaming kernel and its reduction (face block, y1, y2: 2),
-    plus for d >= 4 the outer weights, the per-mode weights and two cross
-    folds (4) and, with two or more outer modes, the r and pair folds (2).
-    Eigen step: Jr build + Lanczos (2)."""
+    plus for d >= 4 the outer weights, the per-mode weights and the cross
+    folds (one launch when A and B are multiples of 4, else two) and, with
+    two or more outer modes, the r and pair folds (2).  Eigen step: Jr build
+    + Lanczos (2)."""
     d = len(dims)
     A, B = (dims[-2], dims[-1]) if d >= 2 else (1, 1)
     if d == 2:
@@ -175,7 +176,8 @@ def launches_per_step(dims):
     elif B <= 32 and A <= 256 and A * B <= 1024:
         npass = 2
     else:
-        npass = 2 if d == 3 else 2 + 4 + (2 if d - 2 >= 2 else 0)
+        cross = 1 if A % 4 == 0 and B % 4 == 0 else 2
+        npass = 2 if d == 3 else 2 + 2 + cross + (2 if d - 2 >= 2 else 0)
     return npass + 2
 
 

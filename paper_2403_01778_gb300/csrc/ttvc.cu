@@ -845,14 +845,120 @@ __global__ void __launch_bounds__(256) fold_cross_kernel(const float* __restrict
     }
 }
 
+// The same cross folds with 16-byte loads: lane l owns columns 4l .. 4l+3 of
+// a 128-column chunk, four outer indices in flight per warp; y1 and y2 in one
+// launch (blockIdx.z).  Needs C % 4 == 0 and 16-byte aligned y rows.
+struct CrossArgs {
+    const float* y[2];
+    int64_t C[2];
+    int64_t off[2][kMaxOrder];
+};
+
+__global__ void __launch_bounds__(256) fold_cross4_kernel(const CrossArgs ca,
+                                                          const float* __restrict__ wx, OuterInfo oi,
+                                                          int64_t O, float* __restrict__ H) {
+    __shared__ float4 part[8][32];
+    const int z = blockIdx.z;
+    const float* __restrict__ y = z ? ca.y[1] : ca.y[0];
+    const int64_t C = z ? ca.C[1] : ca.C[0];
+    if ((int64_t)blockIdx.y * 128 >= C) return;
+    int m = 0;
+    int64_t row = blockIdx.x;
+    while (m < oi.D - 1 && row >= oi.dims[m]) {
+        row -= oi.dims[m];
+        ++m;
+    }
+    const int i = (int)row;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t Im = oi.dims[m];
+    const int64_t stm = oi.st[m];
+    const int64_t Q = O / Im;
+    const int64_t col = (int64_t)blockIdx.y * 128 + 4 * lane;
+    const bool colok = col < C;
+    const float* wm = wx + m * O;
+    const int64_t q0 = (Q * warp) / 8, q1 = (Q * (warp + 1)) / 8;
+    int64_t s = q0 % stm;
+    int64_t o = (q0 / stm) * Im * stm + i * stm + s;
+    const int64_t jump = (Im - 1) * stm;
+    auto step = [&]() {
+        ++o;
+        if (++s == stm) {
+            s = 0;
+            o += jump;
+        }
+    };
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 acc[4] = {z4, z4, z4, z4};
+    int64_t q = q0;
+    for (; q + 4 <= q1; q += 4) {
+        int64_t oo[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            oo[k] = o;
+            step();
+        }
+        float4 yv[4];
+        float wv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            yv[k] = colok ? __ldg(reinterpret_cast<const float4*>(y + oo[k] * C + col)) : z4;
+            wv[k] = __ldg(wm + oo[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[k].x = fmaf(wv[k], yv[k].x, acc[k].x);
+            acc[k].y = fmaf(wv[k], yv[k].y, acc[k].y);
+            acc[k].z = fmaf(wv[k], yv[k].z, acc[k].z);
+            acc[k].w = fmaf(wv[k], yv[k].w, acc[k].w);
+        }
+    }
+    for (; q < q1; ++q) {
+        const float w = __ldg(wm + o);
+        const float4 v = colok ? __ldg(reinterpret_cast<const float4*>(y + o * C + col)) : z4;
+        acc[0].x = fmaf(w, v.x, acc[0].x);
+        acc[0].y = fmaf(w, v.y, acc[0].y);
+        acc[0].z = fmaf(w, v.z, acc[0].z);
+        acc[0].w = fmaf(w, v.w, acc[0].w);
+        step();
+    }
+    part[warp][lane] = make_float4((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
+                                   (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y),
+                                   (acc[0].z + acc[1].z) + (acc[2].z + acc[3].z),
+                                   (acc[0].w + acc[1].w) + (acc[2].w + acc[3].w));
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        const int ln = threadIdx.x >> 2, e = threadIdx.x & 3;
+        const int64_t cc = (int64_t)blockIdx.y * 128 + threadIdx.x;
+        if (cc < C) {
+            float t = 0.f;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) t += reinterpret_cast<const float*>(&part[w][ln])[e];
+            H[(z ? ca.off[1][m] : ca.off[0][m]) + (int64_t)i * C + cc] = t;
+        }
+    }
+}
+
 // r[o] = sum_a y1[o][a] uA[a]   (one warp per o)
 __global__ void fold_r_kernel(const float* __restrict__ y1, const float* __restrict__ uA, int64_t O,
                               int64_t A, float* __restrict__ r) {
     const int lane = threadIdx.x & 31;
+    // 16-byte loads of y1 rows when A % 4 == 0 and y1 is 16-byte aligned
+    const bool v4 = (A & 3) == 0 && (reinterpret_cast<uintptr_t>(y1) & 15u) == 0;
     for (int64_t o = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; o < O;
          o += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         float s = 0.f;
-        for (int64_t aa = lane; aa < A; aa += 32) s = fmaf(y1[o * A + aa], uA[aa], s);
+        if (v4) {
+            const float4* row = reinterpret_cast<const float4*>(y1 + o * A);
+            for (int64_t q = lane; q < A / 4; q += 32) {
+                const float4 v = __ldg(row + q);
+                s = fmaf(v.x, __ldg(uA + 4 * q), s);
+                s = fmaf(v.y, __ldg(uA + 4 * q + 1), s);
+                s = fmaf(v.z, __ldg(uA + 4 * q + 2), s);
+                s = fmaf(v.w, __ldg(uA + 4 * q + 3), s);
+            }
+        } else {
+            for (int64_t aa = lane; aa < A; aa += 32) s = fmaf(y1[o * A + aa], uA[aa], s);
+        }
         s = warp_sum(s);
         if (lane == 0) r[o] = s;
     }
@@ -1135,10 +1241,27 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
     {
         float* wx = reinterpret_cast<float*>(ws + p.off_wx);
         outer_weights_excl_kernel<<<grid_for(s.O, 256, 4096), 256, 0, st>>>(u, oi, s.O, wx);
-        dim3 g1((unsigned)rows, (unsigned)((s.A + 31) / 32));
-        fold_cross_kernel<<<g1, 256, 0, st>>>(y1, s.A, wx, oi, s.O, H, off1);
-        dim3 g2((unsigned)rows, (unsigned)((s.B + 31) / 32));
-        fold_cross_kernel<<<g2, 256, 0, st>>>(y2, s.B, wx, oi, s.O, H, off2);
+        const bool v4 = s.A % 4 == 0 && s.B % 4 == 0 &&
+                        ((reinterpret_cast<uintptr_t>(y1) | reinterpret_cast<uintptr_t>(y2)) & 15u) == 0;
+        if (v4) {
+            CrossArgs ca;
+            memset(&ca, 0, sizeof(ca));
+            ca.y[0] = y1;
+            ca.y[1] = y2;
+            ca.C[0] = s.A;
+            ca.C[1] = s.B;
+            for (int m = 0; m < s.D; ++m) {
+                ca.off[0][m] = off1.off[m];
+                ca.off[1][m] = off2.off[m];
+            }
+            dim3 g((unsigned)rows, (unsigned)((std::max(s.A, s.B) + 127) / 128), 2);
+            fold_cross4_kernel<<<g, 256, 0, st>>>(ca, wx, oi, s.O, H);
+        } else {
+            dim3 g1((unsigned)rows, (unsigned)((s.A + 31) / 32));
+            fold_cross_kernel<<<g1, 256, 0, st>>>(y1, s.A, wx, oi, s.O, H, off1);
+            dim3 g2((unsigned)rows, (unsigned)((s.B + 31) / 32));
+            fold_cross_kernel<<<g2, 256, 0, st>>>(y2, s.B, wx, oi, s.O, H, off2);
+        }
         HOSCF_CK(cudaGetLastError());
     }
     if (s.D >= 2) {
