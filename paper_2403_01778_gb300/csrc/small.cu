@@ -59,8 +59,19 @@ __global__ void small_reduce_kernel(const float* __restrict__ patch, const int* 
         const int64_t loc = e - r.seg[sgi];
         float s = 0.f;
         int64_t dst;
+        // each lane adds the CTAs lane, lane + 32, ... in that order; four of
+        // them per round so that their loads are in flight together
+        const int2* cv2 = reinterpret_cast<const int2*>(cover);
         if (sgi == 0) {   // face block
-            for (int c = lane; c < r.G; c += 32) s += __ldg(patch + (size_t)c * r.patch_floats + loc);
+            int c = lane;
+            for (; c + 96 < r.G; c += 128) {
+                float v[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) v[t] = __ldg(patch + (size_t)(c + 32 * t) * r.patch_floats + loc);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) s += v[t];
+            }
+            for (; c < r.G; c += 32) s += __ldg(patch + (size_t)c * r.patch_floats + loc);
             dst = r.hface + loc;
         } else if (sgi <= 2 * r.D) {
             const bool x1 = sgi <= r.D;
@@ -68,11 +79,29 @@ __global__ void small_reduce_kernel(const float* __restrict__ patch, const int* 
             const int C = x1 ? r.A : r.B;
             const int i = (int)(loc / C), col = (int)(loc % C);
             const int64_t base = r.F + (x1 ? r.x1off[m] : r.x2off[m]) + col;
-            for (int c = lane; c < r.G; c += 32) {
-                const int2 cv = __ldg(reinterpret_cast<const int2*>(cover) + (c * r.D + m));
-                int rr = i - cv.x;
+            auto entry = [&](int c, int2 cvv, float& v) {
+                int rr = i - cvv.x;
                 if (rr < 0) rr += r.dims[m];
-                if (rr < cv.y) s += __ldg(patch + (size_t)c * r.patch_floats + base + (int64_t)rr * C);
+                const bool in = rr < cvv.y;
+                v = in ? __ldg(patch + (size_t)c * r.patch_floats + base + (int64_t)rr * C) : 0.f;
+                return in;
+            };
+            int c = lane;
+            for (; c + 96 < r.G; c += 128) {
+                int2 cvv[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cvv[t] = __ldg(cv2 + ((c + 32 * t) * r.D + m));
+                float v[4];
+                bool in[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) in[t] = entry(c + 32 * t, cvv[t], v[t]);
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (in[t]) s += v[t];
+            }
+            for (; c < r.G; c += 32) {
+                float v;
+                if (entry(c, __ldg(cv2 + (c * r.D + m)), v)) s += v;
             }
             dst = (x1 ? r.hx1[m] : r.hx2[m]) + loc;
         } else {
@@ -80,14 +109,34 @@ __global__ void small_reduce_kernel(const float* __restrict__ patch, const int* 
             const int m = r.pm[p], n = r.pn[p];
             const int i = (int)(loc / r.dims[n]), j = (int)(loc % r.dims[n]);
             const int Rn = r.Rmax[n];
-            for (int c = lane; c < r.G; c += 32) {
-                const int2 cm = __ldg(reinterpret_cast<const int2*>(cover) + (c * r.D + m));
-                const int2 cn = __ldg(reinterpret_cast<const int2*>(cover) + (c * r.D + n));
+            const int64_t base = r.F + r.poff[p];
+            auto entry = [&](int c, int2 cm, int2 cn, float& v) {
                 int rm = i - cm.x, rn = j - cn.x;
                 if (rm < 0) rm += r.dims[m];
                 if (rn < 0) rn += r.dims[n];
-                if (rm < cm.y && rn < cn.y)
-                    s += __ldg(patch + (size_t)c * r.patch_floats + r.F + r.poff[p] + (int64_t)rm * Rn + rn);
+                const bool in = rm < cm.y && rn < cn.y;
+                v = in ? __ldg(patch + (size_t)c * r.patch_floats + base + (int64_t)rm * Rn + rn) : 0.f;
+                return in;
+            };
+            int c = lane;
+            for (; c + 96 < r.G; c += 128) {
+                int2 cm[4], cn[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    cm[t] = __ldg(cv2 + ((c + 32 * t) * r.D + m));
+                    cn[t] = __ldg(cv2 + ((c + 32 * t) * r.D + n));
+                }
+                float v[4];
+                bool in[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) in[t] = entry(c + 32 * t, cm[t], cn[t], v[t]);
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (in[t]) s += v[t];
+            }
+            for (; c < r.G; c += 32) {
+                float v;
+                if (entry(c, __ldg(cv2 + (c * r.D + m)), __ldg(cv2 + (c * r.D + n)), v)) s += v;
             }
             dst = r.hp[p] + loc;
         }

@@ -247,3 +247,20 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(pkg.HoscfError) as e:
         pkg.hoscf_solve(T + 1, torch.zeros(15, device="cuda"))
     assert e.value.status == 1
+
+
+def test_misaligned_tensor_is_rejected():
+    """The descriptor's data must be 16-byte aligned (every load path - TMA,
+    bulk copies, vector loads - assumes it): a 4-byte offset is EINVAL, and the
+    handle stays usable."""
+    pkg = P()
+    dims = (6, 5, 24, 20)
+    buf = torch.zeros(int(np.prod(dims)) + 1, device="cuda")
+    T = buf[1:].view(dims)
+    assert T.data_ptr() % 16 != 0
+    u = torch.cat(W.unit_gaussian_vectors(dims, 1)).cuda()
+    with pytest.raises(pkg.HoscfError) as e:
+        pkg.hoscf_ttvc_blocks(T, u)
+    assert e.value.status == 1
+    H = pkg.hoscf_ttvc_blocks(torch.zeros(dims, device="cuda"), u)
+    assert float(H.abs().max()) == 0.0
