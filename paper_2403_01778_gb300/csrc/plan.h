@@ -55,6 +55,7 @@ struct SmallPlanInfo {
     int pm[kMaxBlocks] = {0}, pn[kMaxBlocks] = {0};
     int64_t patch_floats = 0;
     int nsmax = 0;             // most runs of the fastest outer mode in one group
+    int onebar = 0;            // one barrier per group (at most 4 outer modes)
     // shared-memory layout (bytes from a 128-byte aligned base)
     uint32_t o_bars = 0, o_ring = 0, o_uA = 0, o_uB = 0, o_y1 = 0, o_y2 = 0, o_r = 0, o_S = 0,
              o_meta = 0, o_first = 0, o_patch = 0, o_ur = 0, o_tab = 0;

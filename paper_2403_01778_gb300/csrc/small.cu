@@ -196,16 +196,20 @@ static bool small_layout(const Shape& s, int es, int64_t L, int S, SmallPlanInfo
     sp.o_uB = (uint32_t)o;
     o = al16(o + 4ull * kSmallMaxB);
     sp.o_y1 = (uint32_t)o;
-    o = al16(o + 8ull * K * A);
+    // y1 / y2 and metadata slots: 3 and 4 for the one-barrier schedule (at
+    // most 4 outer modes), 2 and 3 for the two-barrier one
+    const int ny = D <= 4 ? 3 : 2, nmeta = D <= 4 ? 4 : 3;
+    sp.onebar = D <= 4 ? 1 : 0;
+    o = al16(o + 4ull * ny * K * A);
     sp.o_y2 = (uint32_t)o;
-    o = al16(o + 8ull * K * B);
+    o = al16(o + 4ull * ny * K * B);
     sp.o_r = (uint32_t)o;
     o = al16(o + 8ull * K);
     sp.o_S = (uint32_t)o;
     o = al16(o + 8ull * sp.nsmax * (A + B));
     sp.meta_words = small_meta_words(K, sp.nsmax);
     sp.o_meta = (uint32_t)o;
-    o = al16(o + 12ull * sp.meta_words);
+    o = al16(o + 4ull * nmeta * sp.meta_words);
     // runs of mode c a range of L faces touches
     sp.NR = (int)((L + C - 2) / C + 1);
     sp.o_tab = (uint32_t)o;
@@ -355,6 +359,9 @@ cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const 
         while (P < ncol && P < 32) P <<= 1;
         a.pcol = P;
     }
+    // measured: one barrier per group wins up to 4 outer modes
+    // (24x20x24x20x24x20 -13 %), two barriers beyond (8^8, 16^4 8^3)
+    a.onebar = sp.onebar;
     a.meta_words = sp.meta_words;
 
     cudaError_t e;

@@ -44,6 +44,7 @@ struct SmallArgs {
     int NR;                           // runs of mode c in the run table
     uint32_t mag_bc;                  // t / (column tasks per face)
     int pcol;                         // run sums: column chunks per warp pass (power of 2)
+    int onebar;                       // one barrier per group (see the kernel's schedules)
     uint32_t meta_words;
 };
 
@@ -352,14 +353,89 @@ __device__ __forceinline__ void small_folds(const SmallArgs& a, const MetaView& 
     }
 }
 
+// Run sums over mode c (for the other outer modes) and r per face of one
+// group (D >= 2).
+__device__ __forceinline__ void small_runsums(const SmallArgs& a, const MetaView& mv,
+                                      const float* y1s, const float* y2s, float* Sb,
+                                      float* rb, const float* uB, int nf, int warp,
+                                      int lane, int tid) {
+    const int A = a.A, B = a.B, AB = A + B;
+    const int ns = mv.hdr[0];
+    const bool v4 = a.v4 != 0;
+    const int ncol = v4 ? AB >> 2 : AB;
+    float* Sg = Sb;
+    float* rs = rb;
+    // one warp per (run, block of P column chunks): lane = (face offset,
+    // chunk); faces strided by 32 / P, then a fixed butterfly over the
+    // face offsets
+    const int P = a.pcol, FP = 32 / P;
+    const int nblk = (ncol + P - 1) / P;
+    const int fo = lane / P, cl = lane - fo * P;
+    for (int wt = warp; wt < ns * nblk; wt += kSmallThreads / 32) {
+        const int sg = wt / nblk, cq = (wt - sg * nblk) * P + cl;
+        const int kb = mv.segstart[sg], ke = mv.segstart[sg + 1];
+        const bool on = cq < ncol;
+        const int col = v4 ? 4 * cq : cq;
+        const bool x1 = col < A;
+        const float* y = x1 ? y1s + col : y2s + (col - A);
+        const int ys = x1 ? A : B;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (on) {
+            for (int k = kb + fo; k < ke; k += FP) {
+                const float vk = mv.vc[k];
+                if (v4) {
+                    acc = f4fma(vk, *reinterpret_cast<const float4*>(y + k * ys), acc);
+                } else {
+                    acc.x = fmaf(vk, y[k * ys], acc.x);
+                }
+            }
+        }
+        for (int off = 16; off >= P; off >>= 1) {
+            acc.x += __shfl_xor_sync(HOSCF_FULLMASK, acc.x, off);
+            if (v4) {
+                acc.y += __shfl_xor_sync(HOSCF_FULLMASK, acc.y, off);
+                acc.z += __shfl_xor_sync(HOSCF_FULLMASK, acc.z, off);
+                acc.w += __shfl_xor_sync(HOSCF_FULLMASK, acc.w, off);
+            }
+        }
+        if (on && fo == 0) {
+            if (v4)
+                *reinterpret_cast<float4*>(Sg + sg * AB + col) = acc;
+            else
+                Sg[sg * AB + col] = acc.x;
+        }
+    }
+    // r per face (threads from the top)
+    for (int k = kSmallThreads - 1 - tid; k < nf; k += kSmallThreads) {
+        const float* y = y2s + k * B;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int b = 0;
+        for (; b + 4 <= B; b += 4) {
+            s0 = fmaf(uB[b], y[b], s0);
+            s1 = fmaf(uB[b + 1], y[b + 1], s1);
+            s2 = fmaf(uB[b + 2], y[b + 2], s2);
+            s3 = fmaf(uB[b + 3], y[b + 3], s3);
+        }
+        for (; b < B; ++b) s0 = fmaf(uB[b], y[b], s0);
+        rs[k] = (s0 + s1) + (s2 + s3);
+    }
+}
+
 // ---------------------------------------------------------------- kernel
-// Per group g (K faces), one barrier after the element work and one after
-// the run sums:
-//   folds(g-1) | metadata(g+1) (warp 7) | wait slot | element work(g)   -- bar
-//   refill slot with g+S | run sums and r per face (g)                   -- bar
-// y1/y2, run sums and r are double-buffered, metadata triple-buffered, so the
-// folds of a group overlap the next group's element work.
-template <typename E, int BM, bool VEC>
+// Two schedules of a group's three stages (element work, run sums, folds).
+// One barrier per group (up to 4 outer modes), iteration g running side by
+// side
+//   folds(g-2) | run sums and r per face (g-1) | metadata(g+1) (warp 7) |
+//   wait slot, element work(g)                                       -- bar
+//   refill the slot with group g+S
+// or, with more outer modes (where the heavier fold tasks and the run sums
+// would pile up on the same warps), two barriers per group:
+//   folds(g-1) | metadata(g+1) | wait slot, element work(g)          -- bar
+//   refill | run sums and r per face (g)                             -- bar
+// (extra iterations drain the last groups).  Run sums and r are
+// double-buffered; y1/y2 and the metadata take 3 and 4 slots in the first
+// schedule, 2 and 3 in the second.
+template <typename E, int BM, bool VEC, bool ONEBAR>
 __global__ void __launch_bounds__(kSmallThreads, BM <= 16 ? 3 : 2) ttvc_small_kernel(const SmallArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
@@ -463,30 +539,9 @@ __global__ void __launch_bounds__(kSmallThreads, BM <= 16 ? 3 : 2) ttvc_small_ke
     for (int i = 0; i < BM / 2; ++i) hacc[i] = make_float2(0.f, 0.f);
     __syncthreads();
 
-    for (int g = 0; g < ng; ++g) {
-        const int s = g % S;
-        const uint32_t par = (uint32_t)(g / S) & 1u;
-        const int64_t f0 = o_lo + (int64_t)g * K;
-        const int nf = (int)min((int64_t)K, o_hi - f0);
-        const int cur = g & 1, prv = cur ^ 1;
-        MetaView mv(meta0 + (g % 3) * a.meta_words, K, NS);
-        float* y1s = y1b + cur * K * A;
-        float* y2s = y2b + cur * K * B;
-
-        // ---- folds of group g-1 (independent of this group's data)
-        if (g > 0)
-            small_folds(a, MetaView(meta0 + ((g + 2) % 3) * a.meta_words, K, NS), tb, NR,
-                        y1b + prv * K * A, y2b + prv * K * B, Sb + prv * sbuf, rb + prv * K, uB, patch,
-                        K, warp, lane);
-        // ---- metadata of group g+1
-        if (warp == 7 && g + 1 < ng) {
-            small_meta(a, MetaView(meta0 + ((g + 1) % 3) * a.meta_words, K, NS), tb, c0, run0,
-                       first_c, ur, (int)min((int64_t)K, o_hi - f0 - K), lane);
-            advance();
-        }
-
-        // ---- element work
-        const bool ok = mbar_wait_bounded(full + s, par, a.timeout_ns);
+    auto nf_of = [&](int gi) { return (int)min((int64_t)K, o_hi - o_lo - (int64_t)gi * K); };
+    // element work of one group: rows (y1, face block) and columns (y2)
+    auto element = [&](const MetaView& mv, float* y1s, float* y2s, int64_t f0, int nf, int s) {
         const unsigned char* data = ring + (size_t)s * a.stage_bytes +
                                     (reinterpret_cast<uintptr_t>(Tp + f0 * F) & 15u);
         if (rowt) {
@@ -503,7 +558,7 @@ __global__ void __launch_bounds__(kSmallThreads, BM <= 16 ? 3 : 2) ttvc_small_ke
                     bnd = 128 - (int)(e0 & 127);
                 }
                 float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);
-#pragma unroll
+    #pragma unroll
                 for (int c = 0; c < BM / 4; ++c) {
                     float4 v = lds_row4<E, VEC>(row, c, B);
                     if constexpr (std::is_same<E, fp8_t>::value) {
@@ -572,90 +627,95 @@ __global__ void __launch_bounds__(kSmallThreads, BM <= 16 ? 3 : 2) ttvc_small_ke
                 }
             }
         }
-        if (__syncthreads_or(!ok)) {
-            // a copy never completed: record it, wait (bounded) for the
-            // copies still in flight into this CTA's slots, and leave
-            if (tid == 0) {
-                atomicCAS(a.err, 0, (int)DEV_TIMEOUT);
-                for (int gi = g; gi < g + S && gi < ng; ++gi)
-                    (void)mbar_wait_bounded(full + gi % S, (uint32_t)(gi / S) & 1u, a.timeout_ns);
-            }
-            __syncthreads();
-            return;
-        }
-        // slot s is consumed: refill it with group g + S
-        if (tid == 0 && g + S < ng) issue(g + S);
+    };
 
-        // ---- run sums over mode c (for the other outer modes) and r per face
-        if (D >= 2) {
-            const int ns = mv.hdr[0];
-            const bool v4 = a.v4 != 0;
-            const int ncol = v4 ? AB >> 2 : AB;
-            float* Sg = Sb + cur * sbuf;
-            float* rs = rb + cur * K;
-            // one warp per (run, block of P column chunks): lane = (face offset,
-            // chunk); faces strided by 32 / P, then a fixed butterfly over the
-            // face offsets
-            const int P = a.pcol, FP = 32 / P;
-            const int nblk = (ncol + P - 1) / P;
-            const int fo = lane / P, cl = lane - fo * P;
-            for (int wt = warp; wt < ns * nblk; wt += kSmallThreads / 32) {
-                const int sg = wt / nblk, cq = (wt - sg * nblk) * P + cl;
-                const int kb = mv.segstart[sg], ke = mv.segstart[sg + 1];
-                const bool on = cq < ncol;
-                const int col = v4 ? 4 * cq : cq;
-                const bool x1 = col < A;
-                const float* y = x1 ? y1s + col : y2s + (col - A);
-                const int ys = x1 ? A : B;
-                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (on) {
-                    for (int k = kb + fo; k < ke; k += FP) {
-                        const float vk = mv.vc[k];
-                        if (v4) {
-                            acc = f4fma(vk, *reinterpret_cast<const float4*>(y + k * ys), acc);
-                        } else {
-                            acc.x = fmaf(vk, y[k * ys], acc.x);
-                        }
-                    }
-                }
-                for (int off = 16; off >= P; off >>= 1) {
-                    acc.x += __shfl_xor_sync(HOSCF_FULLMASK, acc.x, off);
-                    if (v4) {
-                        acc.y += __shfl_xor_sync(HOSCF_FULLMASK, acc.y, off);
-                        acc.z += __shfl_xor_sync(HOSCF_FULLMASK, acc.z, off);
-                        acc.w += __shfl_xor_sync(HOSCF_FULLMASK, acc.w, off);
-                    }
-                }
-                if (on && fo == 0) {
-                    if (v4)
-                        *reinterpret_cast<float4*>(Sg + sg * AB + col) = acc;
-                    else
-                        Sg[sg * AB + col] = acc.x;
-                }
+    if constexpr (ONEBAR) {
+        // one barrier per group: folds(g-2) | run sums(g-1) | metadata(g+1) |
+        // element work(g); y1/y2 in 3 slots, metadata in 4
+        for (int g = 0; g < ng + 2; ++g) {
+            const int s = g % S;
+            const uint32_t par = (uint32_t)(g / S) & 1u;
+            const int64_t f0 = o_lo + (int64_t)g * K;
+            const int nf = g < ng ? nf_of(g) : 0;
+            MetaView mv(meta0 + (g & 3) * a.meta_words, K, NS);
+            float* y1s = y1b + (g % 3) * K * A;
+            float* y2s = y2b + (g % 3) * K * B;
+            if (g >= 2) {
+                const int gf = g - 2;
+                small_folds(a, MetaView(meta0 + (gf & 3) * a.meta_words, K, NS), tb, NR,
+                            y1b + (gf % 3) * K * A, y2b + (gf % 3) * K * B, Sb + (gf & 1) * sbuf,
+                            rb + (gf & 1) * K, uB, patch, nf_of(gf), warp, lane);
             }
-            // r per face (threads from the top)
-            for (int k = kSmallThreads - 1 - tid; k < nf; k += kSmallThreads) {
-                const float* y = y2s + k * B;
-                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-                int b = 0;
-                for (; b + 4 <= B; b += 4) {
-                    s0 = fmaf(uB[b], y[b], s0);
-                    s1 = fmaf(uB[b + 1], y[b + 1], s1);
-                    s2 = fmaf(uB[b + 2], y[b + 2], s2);
-                    s3 = fmaf(uB[b + 3], y[b + 3], s3);
-                }
-                for (; b < B; ++b) s0 = fmaf(uB[b], y[b], s0);
-                rs[k] = (s0 + s1) + (s2 + s3);
+            if (D >= 2 && g >= 1 && g - 1 < ng) {
+                const int gr = g - 1;
+                small_runsums(a, MetaView(meta0 + (gr & 3) * a.meta_words, K, NS),
+                              y1b + (gr % 3) * K * A, y2b + (gr % 3) * K * B, Sb + (gr & 1) * sbuf,
+                              rb + (gr & 1) * K, uB, nf_of(gr), warp, lane, tid);
             }
+            if (warp == 7 && g + 1 < ng) {
+                small_meta(a, MetaView(meta0 + ((g + 1) & 3) * a.meta_words, K, NS), tb, c0, run0,
+                           first_c, ur, nf_of(g + 1), lane);
+                advance();
+            }
+            const bool ok = g < ng ? mbar_wait_bounded(full + s, par, a.timeout_ns) : true;
+            element(mv, y1s, y2s, f0, nf, s);
+            if (__syncthreads_or(!ok)) {
+                // a copy never completed: record it, wait (bounded) for the
+                // copies still in flight into this CTA's slots, and leave
+                if (tid == 0) {
+                    atomicCAS(a.err, 0, (int)DEV_TIMEOUT);
+                    for (int gi = g; gi < g + S && gi < ng; ++gi)
+                        (void)mbar_wait_bounded(full + gi % S, (uint32_t)(gi / S) & 1u, a.timeout_ns);
+                }
+                __syncthreads();
+                return;
+            }
+            if (tid == 0 && g + S < ng) issue(g + S);
         }
-        __syncthreads();
-    }
-    // folds of the last group
-    if (ng > 0) {
-        const int gl = ng - 1, cl = gl & 1;
-        const int nfl = (int)min((int64_t)K, o_hi - o_lo - (int64_t)gl * K);
-        small_folds(a, MetaView(meta0 + (gl % 3) * a.meta_words, K, NS), tb, NR, y1b + cl * K * A,
-                    y2b + cl * K * B, Sb + cl * sbuf, rb + cl * K, uB, patch, nfl, warp, lane);
+    } else {
+        // two barriers per group: folds(g-1) | metadata(g+1) | element work(g)
+        // -- bar -- run sums(g) -- bar; y1/y2 in 2 slots, metadata in 3
+        for (int g = 0; g < ng; ++g) {
+            const int s = g % S;
+            const uint32_t par = (uint32_t)(g / S) & 1u;
+            const int64_t f0 = o_lo + (int64_t)g * K;
+            const int nf = nf_of(g);
+            const int cur = g & 1, prv = cur ^ 1;
+            MetaView mv(meta0 + (g % 3) * a.meta_words, K, NS);
+            float* y1s = y1b + cur * K * A;
+            float* y2s = y2b + cur * K * B;
+            if (g > 0)
+                small_folds(a, MetaView(meta0 + ((g + 2) % 3) * a.meta_words, K, NS), tb, NR,
+                            y1b + prv * K * A, y2b + prv * K * B, Sb + prv * sbuf, rb + prv * K, uB,
+                            patch, K, warp, lane);
+            if (warp == 7 && g + 1 < ng) {
+                small_meta(a, MetaView(meta0 + ((g + 1) % 3) * a.meta_words, K, NS), tb, c0, run0,
+                           first_c, ur, nf_of(g + 1), lane);
+                advance();
+            }
+            const bool ok = mbar_wait_bounded(full + s, par, a.timeout_ns);
+            element(mv, y1s, y2s, f0, nf, s);
+            if (__syncthreads_or(!ok)) {
+                // a copy never completed: record it, wait (bounded) for the
+                // copies still in flight into this CTA's slots, and leave
+                if (tid == 0) {
+                    atomicCAS(a.err, 0, (int)DEV_TIMEOUT);
+                    for (int gi = g; gi < g + S && gi < ng; ++gi)
+                        (void)mbar_wait_bounded(full + gi % S, (uint32_t)(gi / S) & 1u, a.timeout_ns);
+                }
+                __syncthreads();
+                return;
+            }
+            if (tid == 0 && g + S < ng) issue(g + S);
+            if (D >= 2)
+                small_runsums(a, mv, y1s, y2s, Sb + cur * sbuf, rb + cur * K, uB, nf, warp, lane, tid);
+            __syncthreads();
+        }
+        if (ng > 0) {
+            const int gl = ng - 1, cl = gl & 1;
+            small_folds(a, MetaView(meta0 + (gl % 3) * a.meta_words, K, NS), tb, NR, y1b + cl * K * A,
+                        y2b + cl * K * B, Sb + cl * sbuf, rb + cl * K, uB, patch, nf_of(gl), warp, lane);
+        }
     }
 
     // ---- face block partial: per-thread accumulators -> K1 x F scratch (the
@@ -682,7 +742,7 @@ __global__ void __launch_bounds__(kSmallThreads, BM <= 16 ? 3 : 2) ttvc_small_ke
 template <typename E, int BM, bool VEC>
 cudaError_t launch_small_k(const SmallPlanInfo& sp, const SmallArgs& a, cudaStream_t st,
                            const KernelEvents* kev) {
-    auto k = ttvc_small_kernel<E, BM, VEC>;
+    auto k = a.onebar ? ttvc_small_kernel<E, BM, VEC, true> : ttvc_small_kernel<E, BM, VEC, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
     if (e != cudaSuccess) return e;
     if (kev) cudaEventRecord(kev->begin, st);
