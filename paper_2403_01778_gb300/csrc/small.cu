@@ -19,8 +19,12 @@
 //   them.  All folds go into a shared-memory patch of the CTA (rows limited to
 //   the digits its range covers), each patch entry updated by one thread in
 //   face order, so the result is deterministic.
-// * Per-face digits and factor products are advanced incrementally by one
-//   warp a group ahead (no 64-bit divisions in the loop).
+// * Every run the CTA's range touches has its patch offsets and factor
+//   products in a table built once at the start; per group one warp derives
+//   the per-face values (u_c[j], patch row, run) a group ahead from a
+//   mode-c digit cursor (no 64-bit divisions in the loop).
+// * The stages of consecutive groups overlap: one barrier per group up to 4
+//   outer modes, two beyond (see the kernel).
 // One reduce kernel then sums, for each output entry, the patches of the CTAs
 // that cover it, in CTA order.
 #include <algorithm>
@@ -312,10 +316,7 @@ cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const 
     a.mag_c = small_magic((uint32_t)std::min<int64_t>(s.dims[s.D - 1], 1 << 15));
     a.v4 = (a.A % 4 == 0 && a.B % 4 == 0) ? 1 : 0;
     a.mag_ab4 = small_magic((uint32_t)std::max(1, (a.A + a.B) / 4));
-    for (int k = 0; k < s.D; ++k) {
-        a.magd[k] = small_magic((uint32_t)std::min<int64_t>(s.dims[k], 1 << 15));
-        a.uro[k] = sp.uro[k];
-    }
+    for (int k = 0; k < s.D; ++k) a.uro[k] = sp.uro[k];
     for (int k = 0; k < s.D; ++k) {
         a.dims[k] = (int)s.dims[k];
         a.st[k] = s.ost[k];

@@ -28,7 +28,6 @@ struct SmallArgs {
     uint32_t mag_ab, mag_nm, mag_c;   // t / (A+B), t / (D-1), t / C by multiply-high
     uint32_t mag_ab4;                 // t / ((A+B)/4)
     int v4;                           // A, B multiples of 4: folds by float4
-    uint32_t magd[kMaxOrder];         // t / dims[m] (dims < 2^15)
     int uro[kMaxOrder];               // staged factor rows of outer mode m
     int dims[kMaxOrder];
     int64_t st[kMaxOrder];
