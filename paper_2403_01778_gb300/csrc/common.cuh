@@ -194,15 +194,20 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned nblocks, 
     __shared__ int s_ok;
     ++epoch;
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(count, 1u);   // result unused: a reduction, no round trip
+        // release: the CTA's writes (ordered before this thread by the CTA
+        // barrier above) become visible before the arrival; no reply awaited
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
         const unsigned target = epoch * nblocks;
-        volatile unsigned* vc = count;
+        auto seen = [count]() {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            return v;
+        };
         int ok = 1;
-        if ((int)(*vc - target) < 0) {
+        if ((int)(seen() - target) < 0) {
             const uint64_t t0 = global_timer_ns();
             unsigned spins = 0;
-            while ((int)(*vc - target) < 0) {
+            while ((int)(seen() - target) < 0) {
                 __nanosleep(20);
                 if ((++spins & 255u) == 0) {
                     if (*(volatile int*)err) { ok = 0; break; }
@@ -214,8 +219,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned nblocks, 
                 }
             }
         }
-        __threadfence();
-        s_ok = ok;
+        s_ok = ok;   // the acquire load that saw the target orders the reads after the barrier
     }
     __syncthreads();
     return s_ok != 0;

@@ -245,24 +245,38 @@ __device__ void matvec_rows_cached(const EigArgs& a, const float* __restrict__ v
 }
 
 // out[i] = sum_{c < G} pb[c * ps + i] for i < cnt, every CTA computing the
-// same values in the same order: TPI threads per index (a power of two within
-// a warp) each sum a strided subset of CTAs, then a butterfly combines them.
-// All loads are independent, so one L2 round trip dominates.
+// same values in the same order.  Lanes take 32 consecutive indices (one
+// contiguous segment of a CTA's row per warp load), warps take every
+// kEigWarps-th CTA with up to 16 loads per lane issued before any add, and
+// the kEigWarps warp sums are added in warp order by warp 0.  scratch holds
+// 2 * kEigWarps * 32 values (two buffers, so chunks of 32 indices need one
+// CTA barrier each).
 template <typename T>
-__device__ void reduce_partials(const T* pb, int ps, int G, int cnt, T* out) {
-    int tpi = 32;
-    while (tpi > 1 && tpi * cnt > kEigThreads) tpi >>= 1;
-    const int per_round = kEigThreads / tpi;
-    const int sub = threadIdx.x % tpi;
-    for (int base = 0; base < cnt; base += per_round) {
-        const int i = base + (int)threadIdx.x / tpi;
+__device__ void reduce_partials(const T* pb, int ps, int G, int cnt, T* out, T* scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i0 = 0, h = 0; i0 < cnt; i0 += 32, h ^= 1) {
+        const int i = i0 + lane;
         T s = 0;
         if (i < cnt) {
-#pragma unroll 8
-            for (int c = sub; c < G; c += tpi) s += __ldcg(pb + (size_t)c * ps + i);
+            for (int c0 = warp; c0 < G; c0 += 16 * kEigWarps) {
+                T v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int c = c0 + u * kEigWarps;
+                    v[u] = c < G ? __ldcg(pb + (size_t)c * ps + i) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) s += v[u];
+            }
         }
-        for (int o = tpi / 2; o > 0; o >>= 1) s += __shfl_xor_sync(HOSCF_FULLMASK, s, o);
-        if (sub == 0 && i < cnt) out[i] = s;
+        T* sc = scratch + h * (kEigWarps * 32);
+        sc[warp * 32 + lane] = s;
+        __syncthreads();
+        if (warp == 0 && i < cnt) {
+            T t = sc[lane];
+            for (int w = 1; w < kEigWarps; ++w) t += sc[w * 32 + lane];
+            out[i] = t;
+        }
     }
     __syncthreads();
 }
@@ -334,6 +348,9 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     float* cache = (hd[15] != 0.0) ? jcache : nullptr;
     if (cache) fill_cache_rows(a, r0, r1, cache, crow, &hd[0]);
     __shared__ double s_znorm;   // |z| of the last tridiagonal solve (solve modes)
+    __shared__ double s_rp[2 * kEigWarps * 32];   // cross-warp sums of reduce_partials
+    double* const rp_d = s_rp;
+    float* const rp_f = reinterpret_cast<float*>(s_rp);
 
     const int ps = a.pstride;
     int phase = 0;
@@ -386,7 +403,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                     if (lane == 0) pdd[(size_t)24 * G + (size_t)c * kMaxOrder + m] = t;
                 }
                 if (!eig_sync(a, G, bar_epoch)) return;
-                reduce_partials<double>(pdd + (size_t)24 * G, kMaxOrder, G, a.d, mu_s);
+                reduce_partials<double>(pdd + (size_t)24 * G, kMaxOrder, G, a.d, mu_s, rp_d);
                 for (int q = tid; q < nr; q += kEigThreads) {
                     const int m = mode_of(a, q + r0);
                     Yl[q] = (float)((double)Yl[q] - mu_s[m] * (double)a.proj_u[q + r0]);
@@ -417,7 +434,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             }
             if (tid == 3) pdd[(size_t)c * 4 + 3] = hd[0];
             if (!eig_sync(a, G, bar_epoch)) return;
-            reduce_partials<double>(pdd, 4, G, 4, hd + 1);   // hd[1..4]
+            reduce_partials<double>(pdd, 4, G, 4, hd + 1, rp_d);   // hd[1..4]
             const double xy = hd[1], xx = hd[2], yy = hd[3];
             if (!(xx > 0.0) || !isfinite(xx) || !isfinite(yy)) {
                 if (tid == 0) atomicCAS(a.err, 0, (int)DEV_NONFINITE);
@@ -441,7 +458,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 pdd[(size_t)(G + c) * 4] = t;
             }
             if (!eig_sync(a, G, bar_epoch)) return;
-            reduce_partials<double>(pdd + (size_t)G * 4, 4, G, 1, hd + 5);
+            reduce_partials<double>(pdd + (size_t)G * 4, 4, G, 1, hd + 5, rp_d);
             const double b0 = sqrt(fmax(hd[5], 0.0));
             const double jfro = sqrt(hd[4]) * (double)a.scale;
             const double r = (rho != 0.0) ? sqrt_d * b0 / fabs(rho) : INFINITY;
@@ -509,7 +526,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 if (lane == 0) pbuf()[(size_t)c * ps + i] = s;
             }
             if (!eig_sync(a, G, bar_epoch)) return;
-            reduce_partials<float>(pbuf(), ps, G, cnt, hsum);
+            reduce_partials<float>(pbuf(), ps, G, cnt, hsum, rp_f);
             ++phase;
             if (nproj) {
                 float mu2 = 0.f;
@@ -546,7 +563,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                     if (lane == 0) pbuf()[(size_t)c * ps + i] = s;
                 }
                 if (!eig_sync(a, G, bar_epoch)) return;
-                reduce_partials<float>(pbuf(), ps, G, j + 2, hsum);
+                reduce_partials<float>(pbuf(), ps, G, j + 2, hsum, rp_f);
                 ++phase;
                 float ssq2 = 0.f;
                 for (int i = 0; i <= j; ++i) ssq2 = fmaf(hsum[i], hsum[i], ssq2);
@@ -658,7 +675,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         if (lane == 0) pdd[(size_t)8 * G + (size_t)c * (kMaxOrder + 1) + i] = s;
     }
     if (!eig_sync(a, G, bar_epoch)) return;
-    reduce_partials<double>(pdd + (size_t)8 * G, kMaxOrder + 1, G, d + 1, hd + 6);
+    reduce_partials<double>(pdd + (size_t)8 * G, kMaxOrder + 1, G, d + 1, hd + 6, rp_d);
     const double* bn = hd + 6;
     double tot = 0.0;
     for (int m = 0; m < d; ++m) tot += bn[m];
