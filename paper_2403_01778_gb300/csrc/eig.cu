@@ -157,31 +157,26 @@ __device__ void fill_cache_rows(const EigArgs& a, int r0, int r1, float* cache,
         }
         const float4* __restrict__ src4 = reinterpret_cast<const float4*>(src + head);
         float* d4 = dst + head;
-        int64_t v = threadIdx.x;
-        for (; v + 3 * T < nv; v += 4 * T) {
-            float4 h[4];
+        // batches of kFillBatch loads per thread, all issued before the stores
+        // (the fill is bound by L2 latency, not bandwidth)
+        constexpr int kFillBatch = 16;
+        for (int64_t v0 = threadIdx.x; v0 < nv; v0 += kFillBatch * T) {
+            float4 h[kFillBatch];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) h[t] = __ldcg(src4 + v + t * T);
+            for (int t = 0; t < kFillBatch; ++t)
+                if (v0 + t * T < nv) h[t] = __ldcg(src4 + v0 + t * T);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                float* o = d4 + 4 * (v + t * T);
-                o[0] = h[t].x;
-                o[1] = h[t].y;
-                o[2] = h[t].z;
-                o[3] = h[t].w;
-                s2a = fmaf(h[t].x, h[t].x, fmaf(h[t].y, h[t].y, s2a));
-                s2b = fmaf(h[t].z, h[t].z, fmaf(h[t].w, h[t].w, s2b));
+            for (int t = 0; t < kFillBatch; ++t) {
+                if (v0 + t * T < nv) {
+                    float* o = d4 + 4 * (v0 + t * T);
+                    o[0] = h[t].x;
+                    o[1] = h[t].y;
+                    o[2] = h[t].z;
+                    o[3] = h[t].w;
+                    s2a = fmaf(h[t].x, h[t].x, fmaf(h[t].y, h[t].y, s2a));
+                    s2b = fmaf(h[t].z, h[t].z, fmaf(h[t].w, h[t].w, s2b));
+                }
             }
-        }
-        for (; v < nv; v += T) {
-            const float4 h = __ldcg(src4 + v);
-            float* o = d4 + 4 * v;
-            o[0] = h.x;
-            o[1] = h.y;
-            o[2] = h.z;
-            o[3] = h.w;
-            s2a = fmaf(h.x, h.x, fmaf(h.y, h.y, s2a));
-            s2b = fmaf(h.z, h.z, fmaf(h.w, h.w, s2b));
         }
         for (int64_t i = head + 4 * nv + threadIdx.x; i < cnt; i += T) {
             const float h = __ldcg(src + i);
@@ -333,19 +328,21 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     float* rscratch = vf + ((n + 3) & ~3);                                // 9 * kMaxLanczos
     float* jcache = rscratch + 9 * kMaxLanczos;                           // cache_floats
 
-    // shared-memory row cache for this CTA's rows of Jr, if it fits
-    if (tid == 0) {
+    // shared-memory row cache for this CTA's rows of Jr, if it fits: row
+    // q - r0 starts at crow[q - r0] = sum over the rows r0..q-1 of their
+    // lengths (n - I_m for a row of mode m)
+    auto rows_before = [&](int q) {
         int64_t off = 0;
-        for (int q = r0; q < r1; ++q) {
-            crow[q - r0] = off;
-            off += row_len(a, mode_of(a, q));
+        for (int m = 0; m < a.d; ++m) {
+            const int lo = max(r0, (int)a.moff[m]), hi = min(q, (int)a.moff[m + 1]);
+            if (hi > lo) off += (int64_t)(hi - lo) * row_len(a, m);
         }
-        crow[nr] = off;
-        hd[0] = 0.0;
-        hd[15] = (off <= a.cache_floats) ? 1.0 : 0.0;
-    }
+        return off;
+    };
+    for (int t = tid; t <= nr; t += kEigThreads) crow[t] = rows_before(r0 + t);
+    if (tid == 0) hd[0] = 0.0;
     __syncthreads();
-    float* cache = (hd[15] != 0.0) ? jcache : nullptr;
+    float* cache = (rows_before(r1) <= a.cache_floats) ? jcache : nullptr;
     if (cache) fill_cache_rows(a, r0, r1, cache, crow, &hd[0]);
     __shared__ double s_znorm;   // |z| of the last tridiagonal solve (solve modes)
     __shared__ double s_rp[2 * kEigWarps * 32];   // cross-warp sums of reduce_partials
