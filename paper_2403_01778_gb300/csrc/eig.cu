@@ -195,9 +195,11 @@ __device__ void fill_cache_rows(const EigArgs& a, int r0, int r1, float* cache,
 // of one mode (same column pattern), so each vector element read from
 // shared memory feeds four independent FMA chains; a reduce-scatter then
 // sums the four rows over the lanes with six shuffles.
+// With vec4 (every mode offset a multiple of 4, so every row, its column
+// runs and the vector are 16-byte aligned) the loads are 16 bytes wide.
 __device__ void matvec_rows_cached(const EigArgs& a, const float* __restrict__ vf, int r0, int r1,
                                    const float* __restrict__ cache, const int64_t* crow,
-                                   float* yrow) {
+                                   float* yrow, bool vec4) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int RW = (r1 - r0 + kEigWarps - 1) / kEigWarps;
     const int qb = r0 + warp * RW, qe = min(r1, qb + RW);
@@ -212,15 +214,36 @@ __device__ void matvec_rows_cached(const EigArgs& a, const float* __restrict__ v
 #pragma unroll
         for (int i = 0; i < 4; ++i) rp[i] = cache + crow[q + min(i, cnt - 1) - r0];
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int j = lane; j < lo; j += 32) {
-            const float v = vf[j];
+        if (vec4) {
+            auto fma4 = [](float4 r, float4 v, float acc) {
+                return fmaf(r.w, v.w, fmaf(r.z, v.z, fmaf(r.y, v.y, fmaf(r.x, v.x, acc))));
+            };
+            const float4* v4 = reinterpret_cast<const float4*>(vf);
+            const float4* vh4 = reinterpret_cast<const float4*>(vhi);
+            const int lo4 = lo >> 2, len4 = len >> 2;
+            for (int j = lane; j < lo4; j += 32) {
+                const float4 v = v4[j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fmaf(rp[i][j], v, acc[i]);
-        }
-        for (int j = lo + lane; j < len; j += 32) {
-            const float v = vhi[j];
+                for (int i = 0; i < 4; ++i)
+                    acc[i] = fma4(reinterpret_cast<const float4*>(rp[i])[j], v, acc[i]);
+            }
+            for (int j = lo4 + lane; j < len4; j += 32) {
+                const float4 v = vh4[j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fmaf(rp[i][j], v, acc[i]);
+                for (int i = 0; i < 4; ++i)
+                    acc[i] = fma4(reinterpret_cast<const float4*>(rp[i])[j], v, acc[i]);
+            }
+        } else {
+            for (int j = lane; j < lo; j += 32) {
+                const float v = vf[j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] = fmaf(rp[i][j], v, acc[i]);
+            }
+            for (int j = lo + lane; j < len; j += 32) {
+                const float v = vhi[j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] = fmaf(rp[i][j], v, acc[i]);
+            }
         }
         // reduce-scatter: lanes with bit 4 set keep rows 2,3, bit 3 picks the odd row
         const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
@@ -323,7 +346,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     int64_t* crow = reinterpret_cast<int64_t*>(xrow + R);                 // R + 2
     float* hsum = reinterpret_cast<float*>(crow + R + 2);                 // kMaxLanczos + 16
     float* Vl = hsum + kMaxLanczos + 16;                                  // M1 x R
-    float* Yl = Vl + (size_t)M1 * R;                                      // R
+    float* Yl = Vl + (((size_t)M1 * R + 3) & ~size_t(3));                 // R
     float* vf = Yl + ((R + 3) & ~3);                                      // n (padded)
     float* rscratch = vf + ((n + 3) & ~3);                                // 9 * kMaxLanczos
     float* jcache = rscratch + 9 * kMaxLanczos;                           // cache_floats
@@ -343,6 +366,16 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     if (tid == 0) hd[0] = 0.0;
     __syncthreads();
     float* cache = (rows_before(r1) <= a.cache_floats) ? jcache : nullptr;
+    // 16-byte vector exchange and mat-vec loads: every mode offset (hence n,
+    // every row length and every cached row start) a multiple of 4 floats
+    bool vec4 = ((reinterpret_cast<uintptr_t>(a.V) | reinterpret_cast<uintptr_t>(vf) |
+                  reinterpret_cast<uintptr_t>(jcache)) & 15) == 0;
+    int64_t min_len = a.n;
+    for (int m = 0; m <= a.d; ++m) vec4 = vec4 && (a.moff[m] & 3) == 0;
+    for (int m = 0; m < a.d; ++m) min_len = min(min_len, row_len(a, m));
+    // 16-byte mat-vec loads pay off on long rows only (>= 8 per lane); on
+    // short ones the ragged lane split costs more than they save
+    const bool vec4_mv = vec4 && min_len >= 1024;
     if (cache) fill_cache_rows(a, r0, r1, cache, crow, &hd[0]);
     __shared__ double s_znorm;   // |z| of the last tridiagonal solve (solve modes)
     __shared__ double s_rp[2 * kEigWarps * 32];   // cross-warp sums of reduce_partials
@@ -379,10 +412,33 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     for (int j = 0; j < a.mmax && !done; ++j) {
         // every CTA gets the whole current vector
         const float* src = vslot(j);
-        for (int q = tid; q < n; q += kEigThreads) vf[q] = __ldcg(src + q);
+        if (vec4) {
+            const float4* s4 = reinterpret_cast<const float4*>(src);
+            float4* d4 = reinterpret_cast<float4*>(vf);
+            const int n4 = n >> 2;
+            for (int q0 = tid; q0 < n4; q0 += 4 * kEigThreads) {
+                float4 t[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (q0 + u * kEigThreads < n4) t[u] = __ldcg(s4 + q0 + u * kEigThreads);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (q0 + u * kEigThreads < n4) d4[q0 + u * kEigThreads] = t[u];
+            }
+        } else {
+            for (int q0 = tid; q0 < n; q0 += 8 * kEigThreads) {
+                float t[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (q0 + u * kEigThreads < n) t[u] = __ldcg(src + q0 + u * kEigThreads);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (q0 + u * kEigThreads < n) vf[q0 + u * kEigThreads] = t[u];
+            }
+        }
         __syncthreads();
         if (cache)
-            matvec_rows_cached(a, vf, r0, r1, cache, crow, Yl);
+            matvec_rows_cached(a, vf, r0, r1, cache, crow, Yl, vec4_mv);
         else
             matvec_rows(a, vf, r0, r1, nullptr, crow, false, j == 0 ? &hd[0] : nullptr, Yl);
         __syncthreads();
@@ -837,7 +893,7 @@ __global__ void final_fix_kernel(float* __restrict__ u, int d, ModeInfoArr mi, d
 static size_t lanczos_smem_base(int64_t n, int R, int mmax) {
     return sizeof(double) * (size_t)(16 + 3 * kMaxLanczos) + sizeof(double) * (size_t)R +
            sizeof(int64_t) * (size_t)(R + 2) +
-           sizeof(float) * (size_t)(kMaxLanczos + 16) + sizeof(float) * (size_t)(mmax + 1) * R +
+           sizeof(float) * (size_t)(kMaxLanczos + 16) + sizeof(float) * (((size_t)(mmax + 1) * R + 3) & ~size_t(3)) +
            sizeof(float) * (size_t)((R + 3) & ~3) + sizeof(float) * (size_t)((n + 3) & ~3) +
            sizeof(float) * 9 * kMaxLanczos + 256;
 }

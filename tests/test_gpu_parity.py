@@ -148,6 +148,29 @@ def test_eig_step_matches_dense_eigh():
         assert abs(abs(float(ug.double().cpu().numpy()[o:o + dims[n]] @ un)) - 1) <= 1e-5
 
 
+@pytest.mark.parametrize("dims", [(512, 512, 1024), (200, 200, 200, 200)])
+def test_eig_step_many_ctas_matches_dense_eigh(dims):
+    """Eigen step (Alg. 1 line 5) with J spread over many CTAs: cached row
+    blocks, grid barriers, cross-CTA sums, and on the first shape (rows of
+    1024+ floats) the 16-byte mat-vec loads.  Blocks sigma u_m u_n^T plus
+    noise, a random start, against LAPACK's dense eigh of the same J."""
+    rng = np.random.default_rng(91)
+    d = len(dims)
+    u = [v.numpy().astype(np.float64) for v in W.unit_gaussian_vectors(dims, 92)]
+    Hr = np.concatenate([(5.0 * np.outer(u[m], u[n]) +
+                          0.01 * rng.standard_normal((dims[m], dims[n]))).ravel()
+                         for m, n in oracle.block_pairs(d)]).astype(np.float32)
+    J = oracle.nepv_matrix(Hr.astype(np.float64), list(dims))
+    x_prev = np.concatenate([v.numpy().astype(np.float64)
+                             for v in W.unit_gaussian_vectors(dims, 93)]) / math.sqrt(d)
+    lam, x = oracle.largest_magnitude_eigpair(J, x_prev)
+    xg, ug, lg = P().hoscf_eig_step(dims, to_gpu(Hr), to_gpu(x_prev), eig_adapt=0.0)
+    torch.cuda.synchronize()
+    assert abs(lg.item() - lam) <= 1e-5 * abs(lam)
+    assert abs(float(xg.cpu().numpy() @ x) - 1) <= 1e-5
+    assert float(xg.cpu().numpy() @ x_prev) >= 0
+
+
 def compare_solution(res, ref, tol=1e-5):
     assert abs(res.sigma - ref.sigma) <= tol * abs(ref.sigma)
     for un, ur in zip(res.factors(), ref.u):
