@@ -68,7 +68,7 @@ struct LanczosLaunch {
     uint64_t timeout_ns;
     int64_t cache_floats;
     size_t smem;
-    double adapt;   // > 0: eig_tol = max(eig_tol, min(1e-5, adapt * r)) after the certificate
+    double adapt;   // > 0: eig_tol = max(eig_tol, min(1e-3, adapt * r)) after the certificate
     int rqi = 0;    // 1: Rayleigh-quotient solve instead of the eigenpair; 2: plain solve
     float shift_add = 0.f;        // operator: scale * Jr v + shift_add * v
     const float* proj_u = nullptr;   // project the operator onto the factors' tangent space
