@@ -688,15 +688,35 @@ __device__ __forceinline__ float sum_strided(const float* __restrict__ x, size_t
 __device__ __forceinline__ float4 sum_strided4(const float* __restrict__ x, size_t stride, int64_t n) {
     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
     int64_t p = 0;
+    auto add = [](float4& a, const float4 v) {
+        a.x += v.x;
+        a.y += v.y;
+        a.z += v.z;
+        a.w += v.w;
+    };
+    // eight loads in flight, added in the order of two rounds of four
+    for (; p + 8 <= n; p += 8) {
+        float4 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __ldg(reinterpret_cast<const float4*>(x + (size_t)(p + i) * stride));
+        add(a0, v[0]);
+        add(a1, v[1]);
+        add(a2, v[2]);
+        add(a3, v[3]);
+        add(a0, v[4]);
+        add(a1, v[5]);
+        add(a2, v[6]);
+        add(a3, v[7]);
+    }
     for (; p + 4 <= n; p += 4) {
         const float4 v0 = __ldg(reinterpret_cast<const float4*>(x + (size_t)p * stride));
         const float4 v1 = __ldg(reinterpret_cast<const float4*>(x + (size_t)(p + 1) * stride));
         const float4 v2 = __ldg(reinterpret_cast<const float4*>(x + (size_t)(p + 2) * stride));
         const float4 v3 = __ldg(reinterpret_cast<const float4*>(x + (size_t)(p + 3) * stride));
-        a0.x += v0.x; a0.y += v0.y; a0.z += v0.z; a0.w += v0.w;
-        a1.x += v1.x; a1.y += v1.y; a1.z += v1.z; a1.w += v1.w;
-        a2.x += v2.x; a2.y += v2.y; a2.z += v2.z; a2.w += v2.w;
-        a3.x += v3.x; a3.y += v3.y; a3.z += v3.z; a3.w += v3.w;
+        add(a0, v0);
+        add(a1, v1);
+        add(a2, v2);
+        add(a3, v3);
     }
     for (; p < n; ++p) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(x + (size_t)p * stride));
@@ -718,8 +738,34 @@ __global__ void __launch_bounds__(256) reduce_pass_kernel(const ReduceArgs r) {
                     ((reinterpret_cast<uintptr_t>(r.y2p) | reinterpret_cast<uintptr_t>(r.y2)) & 15u) == 0;
     const int64_t e1 = v1 ? 512 : 128, e2 = v2 ? 512 : 128;
     const int64_t nu1 = (r.n1 + e1 - 1) / e1, nu2 = (r.n2 + e2 - 1) / e2;
-    const int64_t total = nuF + nu1 + nu2;
-    for (int64_t u = blockIdx.x * 2 + (threadIdx.x >> 7); u < total; u += (int64_t)gridDim.x * 2) {
+    // face units: 4 rows x 128 columns, 4 consecutive columns per thread
+    // (16-byte loads) when the tile is 128 wide and rows and partials are
+    // 16-byte aligned; else one row of 128 columns
+    const bool vF = r.FB == 128 && (r.B & 3) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(r.hp) | reinterpret_cast<uintptr_t>(r.face)) & 15u) == 0;
+    const int64_t FA4 = (r.FA + 3) / 4;
+    const int64_t nuFv = vF ? r.TT * FA4 : nuF;
+    const int64_t total = nuFv + nu1 + nu2;
+    for (int64_t u0 = blockIdx.x * 2 + (threadIdx.x >> 7); u0 < total; u0 += (int64_t)gridDim.x * 2) {
+        if (vF && u0 < nuFv) {
+            const int64_t t = u0 / FA4;
+            const int rr = (int)(u0 - t * FA4) * 4 + (col >> 5);
+            const int cb = (col & 31) * 4;
+            const int64_t ta = t / r.TB, tb = t - (t / r.TB) * r.TB;
+            const int64_t aa = ta * r.FA + rr, bb = tb * r.FB + cb;
+            if (rr >= r.FA || aa >= r.A || bb >= r.B) continue;
+            const int64_t c_lo = r.P > 0 ? t * r.P : (t * r.O) / r.W;
+            const int64_t c_hi = r.P > 0 ? t * r.P + r.P - 1 : ((t + 1) * r.O - 1) / r.W;
+            const size_t inner = (size_t)rr * r.FB + cb, tile = (size_t)r.FA * r.FB;
+            const float4 first = __ldg(reinterpret_cast<const float4*>(
+                r.hp + ((size_t)c_lo * 2 + (r.P == 0 && c_lo * r.W < t * r.O ? 1 : 0)) * tile + inner));
+            const float4 rest =
+                sum_strided4(r.hp + (size_t)(c_lo + 1) * 2 * tile + inner, 2 * tile, c_hi - c_lo);
+            *reinterpret_cast<float4*>(r.face + aa * r.B + bb) =
+                make_float4(first.x + rest.x, first.y + rest.y, first.z + rest.z, first.w + rest.w);
+            continue;
+        }
+        const int64_t u = vF ? u0 - nuFv + nuF : u0;   // index in the unvectorised numbering
         if (u < nuF) {
             const int64_t t = u / r.FA;
             const int rr = (int)(u - t * r.FA);
