@@ -683,8 +683,9 @@ __device__ __forceinline__ float sum_strided(const float* __restrict__ x, size_t
     return (a0 + a1) + (a2 + a3);
 }
 
-// sum_{p < n} x[p * stride .. + 3] (16-byte aligned rows): four partial
-// sums in flight, combined in the same fixed order as sum_strided.
+// sum_{p < n} x[p * stride .. + 3] (16-byte aligned rows): up to eight
+// loads in flight, four running sums (p mod 4) combined in the same fixed
+// order as sum_strided.
 __device__ __forceinline__ float4 sum_strided4(const float* __restrict__ x, size_t stride, int64_t n) {
     float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
     int64_t p = 0;
@@ -729,9 +730,9 @@ __device__ __forceinline__ float4 sum_strided4(const float* __restrict__ x, size
 __global__ void __launch_bounds__(256) reduce_pass_kernel(const ReduceArgs r) {
     const int col = threadIdx.x & 127;
     const int64_t nuF = r.TT * r.FA;
-    // y1 / y2 units: 128 threads x 4 consecutive entries (16-byte loads, four
-    // partials in flight) when n % 4 == 0 and both arrays start 16-byte
-    // aligned, else 128 x 1
+    // y1 / y2 units: 128 threads x 4 consecutive entries (16-byte loads, up
+    // to eight partials in flight) when n % 4 == 0 and both arrays start
+    // 16-byte aligned, else 128 x 1
     const bool v1 = (r.n1 & 3) == 0 &&
                     ((reinterpret_cast<uintptr_t>(r.y1p) | reinterpret_cast<uintptr_t>(r.y1)) & 15u) == 0;
     const bool v2 = (r.n2 & 3) == 0 &&
