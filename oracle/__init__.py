@@ -18,10 +18,13 @@ What each function follows
 ``kkt_from_blocks``       eq. (2.4) with g_n = (1/(d-1)) sum_{m!=n} A_{n,m} u^(m),
                           i.e. g = sqrt(d) J(x) x for the balanced x = [u]/sqrt(d).
 ``hoscf``                 Algorithm 1 (lines 1-15) with the readings below.
-``rqi_step``              Sec. 4.4 (iHOSCF), reading below.  PARITY UNPINNED for
-                          the per-iteration RQI path: only its result (a KKT point
-                          with the HOSCF sigma) and Table 3's soft iteration ratio
-                          pin it.
+``rqi_step``              Sec. 4.4 (iHOSCF), reading below.  The step is pinned
+                          (the spectral form in a known eigenbasis, the order-2
+                          block case, cubic convergence).  PARITY UNPINNED for
+                          the acceptance rule of the iHOSCF loop (keep y when its
+                          pass certifies or |sigma(y)| >= |sigma(x_k)|): only the
+                          result (a KKT point with the HOSCF sigma) and Table 3's
+                          soft iteration ratio pin it.
 ``hopm``                  the HOPM (ALS) baseline named in Sec. 1 / Sec. 6.1,
                           used as an independent cross-check only.
 ``greedy``                the greedy rank-one update of Sec. 1 / Example 3:

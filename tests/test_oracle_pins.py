@@ -404,6 +404,78 @@ def test_e4m3_scaled_roundtrip_error_bound():
     assert np.all(err <= np.maximum(np.abs(x) * 2.0 ** -4, 2.0 ** -10 * amax / 448.0 * 1.0001))
 
 
+# ------------------------------------------------------------- RQI step (Sec. 4.4)
+def _rqi_spectral(Q, lam, x):
+    """One Rayleigh-quotient step written in the eigenbasis of J = Q diag(lam) Q^T:
+    rho = sum_j lam_j c_j^2 / sum_j c_j^2 and y ~ sum_j c_j / (lam_j - rho) q_j,
+    c = Q^T x; unit length, <y, x> >= 0."""
+    c = Q.T @ x
+    rho = float(np.sum(lam * c * c) / np.sum(c * c))
+    y = Q @ (c / (lam - rho))
+    y /= np.linalg.norm(y)
+    return (y if y @ x >= 0 else -y), rho
+
+
+def test_rqi_step_matches_the_spectral_form():
+    """oracle.rqi_step on one block (d = 1: x~ = u, plain RQI) against the step
+    written in a known eigenbasis."""
+    rng = np.random.default_rng(5)
+    n = 7
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.array([4.0, 2.5, 1.0, -0.5, -1.5, -3.0, 0.25])
+    J = (Q * lam) @ Q.T
+    u = rng.standard_normal(n)
+    u /= np.linalg.norm(u)
+    y_ref, rho_ref = _rqi_spectral(Q, lam, u)
+    assert np.min(np.abs(lam - rho_ref)) > 0.05       # a well-posed shift
+    (y,), rho = oracle.rqi_step(J, [u], [n])
+    assert abs(rho - rho_ref) <= 1e-13
+    assert np.max(np.abs(y - y_ref)) <= 1e-11
+
+
+def test_rqi_step_order2_block_form():
+    """d = 2, A = diag(s1, s2): J = [[0, A], [A, 0]] has eigenpairs +-s_i,
+    (e_i, +-e_i)/sqrt(2); the step from x~ = [u1; u2]/sqrt(2) is the spectral
+    form, then each block is normalised (Alg. 1 lines 6-9)."""
+    s1, s2 = 3.0, 1.0
+    A = np.diag([s1, s2])
+    Hp = A.ravel()
+    J = oracle.nepv_matrix(Hp, [2, 2])
+    a, b = 0.3, -0.8
+    u1, u2 = np.array([np.cos(a), np.sin(a)]), np.array([np.cos(b), np.sin(b)])
+    r2 = 1 / np.sqrt(2)
+    Q = np.array([[r2, 0, r2, 0], [0, r2, 0, r2], [r2, 0, -r2, 0], [0, r2, 0, -r2]])
+    lam = np.array([s1, s2, -s1, -s2])
+    xt = np.concatenate([u1, u2]) * r2
+    y_ref, rho_ref = _rqi_spectral(Q, lam, xt)
+    assert abs(rho_ref - (s1 * u1[0] * u2[0] + s2 * u1[1] * u2[1])) <= 1e-14
+    (v1, v2), rho = oracle.rqi_step(J, [u1, u2], [2, 2])
+    assert abs(rho - rho_ref) <= 1e-14
+    assert np.max(np.abs(v1 - y_ref[:2] / np.linalg.norm(y_ref[:2]))) <= 1e-12
+    assert np.max(np.abs(v2 - y_ref[2:] / np.linalg.norm(y_ref[2:]))) <= 1e-12
+
+
+def test_rqi_step_converges_cubically():
+    """Near an eigenvector at angle eps, one RQI step leaves an angle O(eps^3)
+    (symmetric J): a tenfold smaller eps gives a ~1000-fold smaller angle."""
+    rng = np.random.default_rng(6)
+    n = 9
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.linspace(-2.0, 5.0, n)
+    J = (Q * lam) @ Q.T
+    w = rng.standard_normal(n)
+    w -= (w @ Q[:, -1]) * Q[:, -1]
+    w /= np.linalg.norm(w)
+    ang = []
+    q = Q[:, -1]
+    for eps in (3e-2, 3e-3):
+        u = q + eps * w
+        u /= np.linalg.norm(u)
+        (y,), _ = oracle.rqi_step(J, [u], [n])
+        ang.append(np.linalg.norm(y - (y @ q) * q))   # sine of the angle to q
+    assert ang[0] <= 3e-4 and 3e-4 <= ang[1] / ang[0] <= 3e-3
+
+
 # ------------------------------------------------------------- planted mistakes
 def test_planted_mistakes_are_caught(monkeypatch):
     """A dropped 1/(d-1), a transposed block and a wrong gauge sign each break
