@@ -149,6 +149,31 @@ hoscf_status hoscf_eig_step(hoscf_handle* h, int order, const int64_t* dims, con
                             double* lambda_out, const hoscf_opts* opts, void* stream);
 
 /*
+ * hoscf_rqi_step - one Rayleigh-quotient step of iHOSCF (Sec. 4.4) from the
+ * factors u: x~ = [u^(1); ...; u^(d)] / sqrt(d), rho = x~^T J x~ / x~^T x~,
+ * y = (J - rho I)^{-1} x~, then the block normalisation of Alg. 1 lines 6-9.
+ * The step iHOSCF's solve takes after each eigen step (the acceptance rule
+ * stays in hoscf_solve).
+ *   order, dims   host.
+ *   H             device, P floats (packed blocks; J = blocks / (d-1)).
+ *   u             device, n_tot floats: the factors (each block unit length,
+ *                 as hoscf_eig_step returns them; not renormalised).
+ *   x_out         device, n_tot doubles, or NULL: y / ||y|| with
+ *                 <x_out, x~> >= 0.
+ *   u_out         device, n_tot floats: x_out's blocks each scaled to unit
+ *                 length (a zero block stays zero).
+ *   rho_out       device, 1 double, or NULL: the shift rho.
+ * The solve is Lanczos on the Krylov space of x~ with a shifted tridiagonal
+ * solve (stop: relative Galerkin residual <= eig_tol; at most eig_max_steps
+ * steps); FP32 vectors, FP64 tridiagonal and normalisation.  Asynchronous on
+ * `stream`.  Errors: EINVAL (order, dims, a null H / u / u_out), NONFINITE
+ * (a zero x~), ECUDA.
+ */
+hoscf_status hoscf_rqi_step(hoscf_handle* h, int order, const int64_t* dims, const float* H,
+                            const float* u, double* x_out, float* u_out, double* rho_out,
+                            const hoscf_opts* opts, void* stream);
+
+/*
  * hoscf_solve - HOSCF / iHOSCF (Algorithm 1 and Sec. 4.4).
  *   T       tensor (device data; F32, BF16 or F8E4M3).
  *   u0      device, n_tot floats: initial guess; each block is normalised

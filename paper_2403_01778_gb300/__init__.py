@@ -7,7 +7,8 @@ functions works everywhere, calling them needs the built library and a GPU.
 """
 from .api import (HoscfError, SolveResult, balanced, handle, hoscf_backward, hoscf_eig_step,  # noqa: F401
                   hoscf_opts_default, hoscf_profile_enable, hoscf_profile_read, hoscf_quantize,
-                  hoscf_selftest_timeout, hoscf_solve, hoscf_solve_batched, hoscf_solve_greedy,
+                  hoscf_rqi_step, hoscf_selftest_timeout, hoscf_solve, hoscf_solve_batched,
+                  hoscf_solve_greedy,
                   hoscf_ttvc_blocks, hoscf_ttvc_blocks_static, hoscf_workspace_size, n_blocks,
                   n_tot)
 from .autograd import HOSCFFunction, hoscf  # noqa: F401

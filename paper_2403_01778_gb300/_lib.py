@@ -23,7 +23,7 @@ MAX_ORDER = 8
 
 # Every entry point the header declares (checked by the ABI test).
 EXPORTS = ("hoscf_create", "hoscf_destroy", "hoscf_last_error", "hoscf_opts_default",
-           "hoscf_workspace_size", "hoscf_ttvc_blocks", "hoscf_eig_step", "hoscf_solve",
+           "hoscf_workspace_size", "hoscf_ttvc_blocks", "hoscf_eig_step", "hoscf_rqi_step", "hoscf_solve",
            "hoscf_solve_batched", "hoscf_backward", "hoscf_quantize",
            "hoscf_ttvc_blocks_static", "hoscf_profile_enable", "hoscf_profile_read",
            "hoscf_selftest_timeout", "hoscf_solve_greedy")
@@ -73,6 +73,8 @@ def load():
     lib.hoscf_workspace_size.argtypes = [c_int, P(c_int64), c_int, P(c_size_t)]
     lib.hoscf_ttvc_blocks.argtypes = [c_void_p, P(TensorDesc), c_void_p, c_void_p, c_void_p]
     lib.hoscf_eig_step.argtypes = [c_void_p, c_int, P(c_int64), c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, P(Opts), c_void_p]
+    lib.hoscf_rqi_step.argtypes = [c_void_p, c_int, P(c_int64), c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, P(Opts), c_void_p]
     lib.hoscf_solve.argtypes = [c_void_p, P(TensorDesc), c_void_p, P(Opts), c_void_p,
                                 P(c_double), P(Info), c_void_p]

@@ -211,6 +211,30 @@ def hoscf_eig_step(dims, H: torch.Tensor, x_prev: torch.Tensor, eig_tol=None, ei
     return x, u, lam
 
 
+def hoscf_rqi_step(dims, H: torch.Tensor, u: torch.Tensor, eig_tol=None, eig_max_steps=None,
+                   stream=None):
+    """One Rayleigh-quotient step of iHOSCF (Sec. 4.4) from the factors u:
+    y = (J - rho I)^-1 x~ with x~ = [u] / sqrt(d), rho its Rayleigh quotient,
+    then the block normalisation (Alg. 1 lines 6-9).  Returns (x float64 unit
+    y, u float32 normalised blocks, rho float64 tensor)."""
+    dims = [int(v) for v in dims]
+    n = n_tot(dims)
+    u = u.contiguous()
+    if u.dtype != torch.float32 or u.numel() != n:
+        raise ValueError("u must be float32 with sum(dims) entries")
+    x = torch.empty(n, device=H.device, dtype=torch.float64)
+    uo = torch.empty(n, device=H.device, dtype=torch.float32)
+    rho = torch.empty(1, device=H.device, dtype=torch.float64)
+    arr = (ctypes.c_int64 * len(dims))(*dims)
+    o = _opts(eig_tol=eig_tol, eig_max_steps=eig_max_steps)
+    h = handle(H.device.index)
+    _check(_lib.load().hoscf_rqi_step(h, len(dims), arr, ctypes.c_void_p(H.data_ptr()),
+                                      ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.c_void_p(uo.data_ptr()), ctypes.c_void_p(rho.data_ptr()),
+                                      ctypes.byref(o), _stream_ptr(stream)), h)
+    return x, uo, rho
+
+
 @dataclass
 class SolveResult:
     sigma: float

@@ -413,6 +413,28 @@ hoscf_status hoscf_eig_step(hoscf_handle* h, int order, const int64_t* dims, con
                       o.eig_adapt);
 }
 
+hoscf_status hoscf_rqi_step(hoscf_handle* h, int order, const int64_t* dims, const float* H,
+                            const float* u, double* x_out, float* u_out, double* rho_out,
+                            const hoscf_opts* opts, void* stream) {
+    if (!h) return HOSCF_EINVAL;
+    if (!dims_valid(order, dims)) return fail(h, HOSCF_EINVAL, "order must be 2..%d and dims >= 1", HOSCF_MAX_ORDER);
+    if (!H || !u || !u_out) return fail(h, HOSCF_EINVAL, "NULL pointer argument");
+    DeviceGuard g(h->device);
+    hoscf_opts o;
+    hoscf_opts_default(&o);
+    if (opts) o = *opts;
+    Layout L;
+    hoscf_status st = plan_all(h, order, dims, HOSCF_F32, false, true,
+                               std::min(std::max(o.eig_max_steps, 2), 128), L);
+    if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    st = reset_dev_state(h, s);
+    if (st) return st;
+    // start x~ = u / sqrt(d) (the kernel's balanced start from factors), shift
+    // = the Rayleigh quotient alpha_0, no certificate shortcut
+    return eig_launch(h, L, H, nullptr, u, x_out, u_out, rho_out, &o, 0, 0.0, s, 0.0, 1);
+}
+
 hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u0,
                          const hoscf_opts* opts, float* u_out, double* sigma_out,
                          hoscf_info* info, void* stream) {

@@ -171,6 +171,55 @@ def test_eig_step_many_ctas_matches_dense_eigh(dims):
     assert float(xg.cpu().numpy() @ x_prev) >= 0
 
 
+def test_rqi_step_matches_oracle_near_a_maximum():
+    """iHOSCF's RQI step (Sec. 4.4) from a point near the maximum: the shift
+    rho and the normalised blocks of y = (J - rho I)^-1 x~ against the
+    oracle's dense solve on the same FP32 blocks and factors."""
+    dims = (20, 30, 25)
+    T, _ = W.planted_cp(dims, [3.0], seed=17, noise_abs=0.5)
+    T = T.numpy().astype(np.float64)
+    u0 = [v.numpy().astype(np.float64) for v in W.unit_gaussian_vectors(dims, 18)]
+    near = oracle.hoscf(T, u0, tol=1e-2, max_iter=50)
+    uk = [v.astype(np.float32).astype(np.float64) for v in near.u]
+    Hr = oracle.blocks(T, uk).astype(np.float32)
+    J = oracle.nepv_matrix(Hr.astype(np.float64), list(dims))
+    v_ref, rho_ref = oracle.rqi_step(J, uk, list(dims))
+    xg, ug, rg = P().hoscf_rqi_step(dims, to_gpu(Hr), to_gpu(np.concatenate(uk).astype(np.float32)))
+    torch.cuda.synchronize()
+    assert abs(rg.item() - rho_ref) <= 1e-6 * abs(rho_ref)
+    ugn = ug.double().cpu().numpy()
+    o = 0
+    for n, vr in zip(dims, v_ref):
+        assert float(ugn[o:o + n] @ vr) >= 1 - 1e-5
+        o += n
+
+
+def test_rqi_step_many_ctas_matches_oracle():
+    """The RQI step with J spread over many CTAs (512x512x1024 blocks
+    sigma a_m a_n^T plus noise, a start near the top eigenvector)."""
+    dims = (512, 512, 1024)
+    rng = np.random.default_rng(95)
+    d = len(dims)
+    a = [v.numpy().astype(np.float64) for v in W.unit_gaussian_vectors(dims, 96)]
+    Hr = np.concatenate([(5.0 * np.outer(a[m], a[n]) +
+                          0.01 * rng.standard_normal((dims[m], dims[n]))).ravel()
+                         for m, n in oracle.block_pairs(d)]).astype(np.float32)
+    J = oracle.nepv_matrix(Hr.astype(np.float64), list(dims))
+    uk = []
+    for v in a:
+        w = v + 0.05 * rng.standard_normal(v.shape) / np.sqrt(v.size)
+        uk.append((w / np.linalg.norm(w)).astype(np.float32).astype(np.float64))
+    v_ref, rho_ref = oracle.rqi_step(J, uk, list(dims))
+    xg, ug, rg = P().hoscf_rqi_step(dims, to_gpu(Hr), to_gpu(np.concatenate(uk).astype(np.float32)))
+    torch.cuda.synchronize()
+    assert abs(rg.item() - rho_ref) <= 1e-6 * abs(rho_ref)
+    ugn = ug.double().cpu().numpy()
+    o = 0
+    for n, vr in zip(dims, v_ref):
+        assert float(ugn[o:o + n] @ vr) >= 1 - 1e-5
+        o += n
+
+
 def compare_solution(res, ref, tol=1e-5):
     assert abs(res.sigma - ref.sigma) <= tol * abs(ref.sigma)
     for un, ur in zip(res.factors(), ref.u):
