@@ -68,6 +68,9 @@ def test_null_and_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.hoscf_last_error(None) == b"null handle"
     assert lib.hoscf_ttvc_blocks(None, None, None, None, None) == EINVAL
     assert lib.hoscf_solve(None, None, None, None, None, None, None, None) == EINVAL
+    arr3 = (ctypes.c_int64 * 3)(4, 5, 6)
+    assert lib.hoscf_eig_step(None, 3, arr3, None, None, None, None, None, None, None) == EINVAL
+    assert lib.hoscf_rqi_step(None, 3, arr3, None, None, None, None, None, None, None) == EINVAL
     assert lib.hoscf_backward(None, None, None, 0.0, 0.0, None, None, None) == EINVAL
     assert lib.hoscf_profile_enable(None, 1) == EINVAL
     n, ms = ctypes.c_int(), ctypes.c_double()
