@@ -183,11 +183,12 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // Software barrier across the co-resident CTAs of a cooperative launch.
 // `*count` is zero when the launch starts (the launcher's preceding kernel
 // on the same stream clears it) and only grows: every CTA adds one per
-// barrier with a fire-and-forget reduction, then polls until the count
-// reaches epoch x nblocks, `epoch` being the number of barriers this CTA has
-// passed (uniform over the CTA).  One round trip per barrier, no release
-// flag.  Every wait is bounded by `limit_ns`; on timeout *err is set and
-// false is returned (the caller then leaves the kernel).
+// barrier with a fire-and-forget release reduction (it publishes the CTA's
+// earlier writes), then polls with acquire loads until the count reaches
+// epoch x nblocks, `epoch` being the number of barriers this CTA has passed
+// (uniform over the CTA).  One round trip per barrier, no release flag, no
+// full fences.  Every wait is bounded by `limit_ns`; on timeout *err is set
+// and false is returned (the caller then leaves the kernel).
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned nblocks, unsigned& epoch,
                                              int* err, uint64_t limit_ns) {
     __syncthreads();
