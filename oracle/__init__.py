@@ -20,11 +20,12 @@ What each function follows
 ``hoscf``                 Algorithm 1 (lines 1-15) with the readings below.
 ``rqi_step``              Sec. 4.4 (iHOSCF), reading below.  The step is pinned
                           (the spectral form in a known eigenbasis, the order-2
-                          block case, cubic convergence).  PARITY UNPINNED for
-                          the acceptance rule of the iHOSCF loop (keep y when its
-                          pass certifies or |sigma(y)| >= |sigma(x_k)|): only the
-                          result (a KKT point with the HOSCF sigma) and Table 3's
-                          soft iteration ratio pin it.
+                          block case, cubic convergence); the acceptance rule of
+                          the iHOSCF loop (keep y when its pass certifies or
+                          |sigma(y)| >= |sigma(x_k)|) by steps made to return a
+                          certified point, an uncertified point of larger
+                          |sigma|, and a point of smaller |sigma| (then the loop
+                          must reproduce plain HOSCF's iterates).
 ``hopm``                  the HOPM (ALS) baseline named in Sec. 1 / Sec. 6.1,
                           used as an independent cross-check only.
 ``greedy``                the greedy rank-one update of Sec. 1 / Example 3:

@@ -476,6 +476,57 @@ def test_rqi_step_converges_cubically():
     assert ang[0] <= 3e-4 and 3e-4 <= ang[1] / ang[0] <= 3e-3
 
 
+def test_ihoscf_rejects_an_rqi_step_that_lowers_sigma(monkeypatch):
+    """Acceptance rule of iHOSCF (Sec. 4.4 reading): a y with a smaller
+    |sigma| that its pass does not certify is rejected, so the loop keeps the
+    eigen-step iterates x_k - exactly plain HOSCF's sequence - with one extra
+    pass per iteration and no acceptances."""
+    dims = (6, 5, 4)
+    T, _ = W.planted_cp(dims, [3.0], seed=41, noise_abs=0.3)
+    T = T.numpy().astype(np.float64)
+    u0 = rand_unit(dims, 42)
+    bad = rand_unit(dims, 43)
+    monkeypatch.setattr(oracle, "rqi_step", lambda J, u, d: ([v.copy() for v in bad], 0.0))
+    assert abs(oracle.kkt_vectors(T, bad)[1]) < 0.5 * 3.0     # bad lowers sigma
+    ref = oracle.hoscf(T, u0, tol=1e-10, max_iter=100, variant="hoscf")
+    r = oracle.hoscf(T, u0, tol=1e-10, max_iter=100, variant="ihoscf")
+    assert r.rqi_accepts == 0
+    assert r.iters == ref.iters and abs(r.sigma - ref.sigma) <= 1e-14 * abs(ref.sigma)
+    for a, b in zip(r.u, ref.u):
+        assert np.max(np.abs(a - b)) <= 1e-12
+    # per iteration: the pass of x_k, then the rejected pass of y (the last
+    # iteration's x_k certifies and takes no RQI step)
+    assert r.passes == 1 + 2 * r.iters - 1
+
+
+def test_ihoscf_accepts_an_rqi_step_its_pass_certifies(monkeypatch):
+    """Acceptance rule, other branch: a y whose pass certifies convergence is
+    kept at once.  The step is made to return the maximiser found beforehand
+    by plain HOSCF to 1e-13, from a start where plain HOSCF needs several
+    iterations to reach 1e-8."""
+    dims = (6, 5, 4)
+    T, _ = W.planted_cp(dims, [3.0], seed=41, noise_abs=0.3)
+    T = T.numpy().astype(np.float64)
+    u0 = rand_unit(dims, 42)
+    best = oracle.hoscf(T, u0, tol=1e-13, max_iter=500, variant="hoscf")
+    plain = oracle.hoscf(T, u0, tol=1e-8, max_iter=500, variant="hoscf")
+    assert best.converged and plain.iters >= 3
+    monkeypatch.setattr(oracle, "rqi_step", lambda J, u, d: ([v.copy() for v in best.u], 0.0))
+    r = oracle.hoscf(T, u0, tol=1e-8, max_iter=500, variant="ihoscf")
+    assert r.converged and r.rqi_accepts == 1 and r.iters == 1
+    assert abs(r.sigma - best.sigma) <= 1e-12 * abs(best.sigma)
+    # the |sigma| branch: an uncertified y with a larger |sigma| than x_1 is
+    # kept too (passes: x_0, x_1, then y)
+    rng = np.random.default_rng(46)
+    near = [v + 1e-3 * rng.standard_normal(v.size) for v in best.u]
+    near = [v / np.linalg.norm(v) for v in near]
+    monkeypatch.setattr(oracle, "rqi_step", lambda J, u, d: ([v.copy() for v in near], 0.0))
+    r = oracle.hoscf(T, u0, tol=1e-8, max_iter=500, variant="ihoscf")
+    (s1, r1), (sy, ry) = r.history[1], r.history[2]
+    assert ry > 1e-8 and abs(sy) >= abs(s1) and r1 > 1e-8
+    assert r.rqi_accepts >= 1 and r.converged
+
+
 # ------------------------------------------------------------- planted mistakes
 def test_planted_mistakes_are_caught(monkeypatch):
     """A dropped 1/(d-1), a transposed block and a wrong gauge sign each break
