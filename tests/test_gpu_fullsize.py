@@ -96,3 +96,30 @@ def test_blocks_sampled_at_full_size(name, fmt, per_block):
             assert abs(got - ref) <= tol, ((m, n), i, j, got, ref, tol)
     del T32, Tg, sg, H
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("name,fmt", [("cfg2a_1024cube_rank5", "fp32"), ("cfg3_200p4", "fp8")])
+def test_solve_at_full_size_is_a_kkt_point_for_the_oracle(name, fmt):
+    """Whole solves at full size (the 200^4 one on FP8 storage with FP32
+    refinement): the oracle's FP64 pass over the FP32 tensor at the returned
+    factors gives the same sigma and a KKT residual (eq. 2.4) within the
+    tolerance."""
+    dims = tuple(W.CONFIGS[name]["dims"])
+    T32 = W.config_tensor(name, 0, device="cuda")
+    u0 = torch.cat(W.unit_gaussian_vectors(dims, 9)).cuda()
+    if fmt == "fp32":
+        r = P().hoscf_solve(T32, u0, tol=1e-6)
+    else:
+        q, s = P().hoscf_quantize(T32, fmt)
+        r = P().hoscf_solve(q, u0, tol=1e-6, scales=s, refine=T32)
+        del q, s
+    torch.cuda.synchronize()
+    assert r.converged
+    Th = T32.cpu().numpy()
+    del T32
+    torch.cuda.empty_cache()
+    u = [f.double().cpu().numpy() for f in r.factors()]
+    g, full = oracle.kkt_vectors(Th, u)
+    rr = np.linalg.norm(np.concatenate(g) - full * np.concatenate(u)) / abs(full)
+    assert abs(full - r.sigma) <= 1e-5 * abs(full), (full, r.sigma)
+    assert rr <= 1e-5, rr
