@@ -631,14 +631,16 @@ __global__ void __launch_bounds__(256, TiledOcc<E>::value)
         }
     }
     flush(cc_t);
-    if (RING && !ok) {
-        // A wait gave up (results are void; the host reports the timeout).
-        // Every copy already issued must still land before the CTA's shared
-        // memory is released: wait for each, with a bound of at least 1 s
-        // whatever the caller's limit.
-        const uint64_t drain_ns = a.timeout_ns > 1000000000ull ? a.timeout_ns : 1000000000ull;
-        for (int k = kfail; k < nis; ++k)
-            mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1), drain_ns);
+    if constexpr (RING) {
+        if (!ok) {
+            // A wait gave up (results are void; the host reports the timeout).
+            // Every copy already issued must still land before the CTA's shared
+            // memory is released: wait for each, with a bound of at least 1 s
+            // whatever the caller's limit.
+            const uint64_t drain_ns = a.timeout_ns > 1000000000ull ? a.timeout_ns : 1000000000ull;
+            for (int k = kfail; k < nis; ++k)
+                mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1), drain_ns);
+        }
     }
     if (CPA) cp_async_wait_all();
 }
