@@ -174,3 +174,23 @@ def test_reference_arm_runs_on_rank_zero_only():
     args = argparse.Namespace(workload="cfg1_64cube", steps=1, warmup=0, gpus=2)
     assert bench.run_reference(args, rank=1, world=2) == 0
     assert bench.max_over_ranks(7.5) == 7.5
+
+
+def test_binding_rejects_bad_tensors_before_any_device_call():
+    """The Python binding checks dtypes, sizes and placement on the host and
+    raises ValueError before it touches the library or a device."""
+    import paper_2403_01778_gb300 as P
+    dims = (4, 5, 6)
+    H = torch.zeros(P.n_blocks(dims))
+    with pytest.raises(ValueError):
+        P.hoscf_eig_step(dims, H, torch.zeros(15, dtype=torch.float32))     # x_prev must be FP64
+    with pytest.raises(ValueError):
+        P.hoscf_eig_step(dims, H, torch.zeros(14, dtype=torch.float64))     # wrong length
+    with pytest.raises(ValueError):
+        P.hoscf_rqi_step(dims, H, torch.zeros(15, dtype=torch.float64))     # u must be FP32
+    with pytest.raises(ValueError):
+        P.hoscf_rqi_step(dims, H, torch.zeros(16, dtype=torch.float32))     # wrong length
+    with pytest.raises(ValueError):
+        P.hoscf_quantize(torch.zeros(8), "bf16")                            # host tensor
+    with pytest.raises(ValueError):
+        P.hoscf_ttvc_blocks(torch.zeros(dims), torch.zeros(15))             # host tensor
