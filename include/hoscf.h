@@ -57,8 +57,13 @@ typedef enum {
     HOSCF_VARIANT_HOSCF = 0,   /* Algorithm 1 */
     HOSCF_VARIANT_IHOSCF = 1,  /* Sec. 4.4: RQI with J built at the new point x_k (one more pass) */
     HOSCF_VARIANT_IHOSCF_PREV = 2, /* Sec. 4.4 read with J_{k-1} (tracks plain HOSCF) */
-    HOSCF_VARIANT_JACOBI_HOPM = 3  /* Sec. 1 / 6.1 comparison method: every factor at once,
+    HOSCF_VARIANT_JACOBI_HOPM = 3, /* Sec. 1 / 6.1 comparison method: every factor at once,
                                       u^(n) <- A x_{k!=n} u^(k) / ||.||, from the same blocks */
+    HOSCF_VARIANT_ASVD = 4         /* Sec. 1 comparison method (orders 2 and 3): with u^(f)
+                                      fixed, (u^(m), u^(n)) <- the largest singular pair of
+                                      the block A_{m,n} = A x_f u^(f), f = 1, 2, 3, 1, ...
+                                      (Gauss-Seidel); the pair negated together when
+                                      <a, u^(m)> + <b, u^(n)> < 0; one eigen step per pair */
 } hoscf_variant;
 
 typedef struct hoscf_handle hoscf_handle;
@@ -118,10 +123,25 @@ hoscf_status hoscf_workspace_size(int order, const int64_t* dims, int dtype, siz
  *      paper's blocks use unit vectors, eq. 3.4; no normalisation is done).
  *   H  device, P floats, packed as described above (overwritten).
  * Asynchronous on `stream`; FP32 accumulation.  Errors: EINVAL (order < 2
- * or > 8, a dim < 1, null pointer, F8 without scales), ENOMEM, ECUDA.
+ * or > 8, a dim < 1, null pointer, F8 without scales), ENOMEM, ECUDA.  A
+ * device-side wait that gives up (TIMEOUT) cannot be known when the call
+ * returns: it is recorded in the handle's device status word, H is then
+ * invalid, and hoscf_device_status reports it.
  */
 hoscf_status hoscf_ttvc_blocks(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u,
                                float* H, void* stream);
+
+/*
+ * hoscf_device_status - failures the asynchronous calls (hoscf_ttvc_blocks,
+ * hoscf_eig_step, hoscf_rqi_step) recorded on the device (no counterpart in
+ * the paper).  Synchronises `stream`, reads the handle's device status word
+ * and clears it.  Returns OK, TIMEOUT (a bounded device wait gave up; the
+ * outputs of the call that hit it, and of later calls on the handle until
+ * this one, are invalid) or NONFINITE.  The synchronous calls hoscf_solve,
+ * hoscf_solve_greedy and hoscf_backward report their own device failures and
+ * start from a clear word, discarding an unread one.
+ */
+hoscf_status hoscf_device_status(hoscf_handle* h, void* stream);
 
 /*
  * hoscf_eig_step - the largest-magnitude eigenpair of J (Alg. 1 line 5),
@@ -142,7 +162,8 @@ hoscf_status hoscf_ttvc_blocks(hoscf_handle* h, const hoscf_tensor_desc* T, cons
  * tol = eig_tol when eig_adapt = 0; at most eig_max_steps; opts may be NULL
  * for defaults).  The start-point certificate, the tridiagonal matrix, the
  * Ritz value and the final normalisation are FP64; the Lanczos vectors are
- * FP32 like the blocks.  Asynchronous on `stream`.
+ * FP32 like the blocks.  Asynchronous on `stream`; device-side failures go to
+ * the handle's status word (hoscf_device_status).
  */
 hoscf_status hoscf_eig_step(hoscf_handle* h, int order, const int64_t* dims, const float* H,
                             const double* x_prev, double* x_out, float* u_out,
@@ -192,7 +213,7 @@ hoscf_status hoscf_rqi_step(hoscf_handle* h, int order, const int64_t* dims, con
  * iterate is predicted to reach it), and on `refine` (FP32) afterwards.
  * Synchronous: returns when the outputs are final.  NOT_CONVERGED after
  * max_iter (outputs = last certified iterate), NONFINITE, TIMEOUT, EINVAL,
- * ENOMEM, ECUDA.
+ * ENOMEM, ECUDA; EUNSUPPORTED for the ASVD variant on orders above 3.
  */
 hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u0,
                          const hoscf_opts* opts, float* u_out, double* sigma_out,
@@ -301,14 +322,17 @@ hoscf_status hoscf_profile_read(hoscf_handle* h, int* count, double* total_ms);
  *   kind 0   an mbarrier phase that no thread or copy completes (the wait
  *            the streaming kernel uses for its TMA copies);
  *   kind 1   the software grid barrier of the eigen step with one arrival
- *            missing (2 CTAs).
+ *            missing (2 CTAs);
+ *   kind 2   kind 0 launched asynchronously on `stream` like the pass, its
+ *            timeout left in the status word for hoscf_device_status.
  *   timeout_ns   the bound, 1 .. 10^10.
- * Synchronous; nothing else is in flight in these kernels, so the context
- * stays usable.  Returns HOSCF_TIMEOUT when the failure was detected and
- * reported (the expected outcome), EINVAL for bad arguments, ECUDA
- * otherwise.
+ *   stream   kind 2 only (cudaStream_t as void*).
+ * Kinds 0 and 1 are synchronous; nothing else is in flight in these
+ * kernels, so the context stays usable.  Returns HOSCF_TIMEOUT when the
+ * failure was detected and reported (the expected outcome of kinds 0 and 1),
+ * OK for a launched kind 2, EINVAL for bad arguments, ECUDA otherwise.
  */
-hoscf_status hoscf_selftest_timeout(hoscf_handle* h, int kind, int64_t timeout_ns);
+hoscf_status hoscf_selftest_timeout(hoscf_handle* h, int kind, int64_t timeout_ns, void* stream);
 
 /*
  * hoscf_ttvc_blocks_static - hoscf_ttvc_blocks without any allocation.
@@ -319,21 +343,28 @@ hoscf_status hoscf_selftest_timeout(hoscf_handle* h, int kind, int64_t timeout_n
  * workspace with cudaMalloc).
  *   T, u, H  as for hoscf_ttvc_blocks (the caller still owns and passes the
  *            inputs and the output); F32 and BF16 tensors.
+ *   status   device, 1 int, or NULL: written in stream order after the pass
+ *            with 0 (H is valid) or HOSCF_TIMEOUT's device code (a bounded
+ *            wait of the pass gave up; H is invalid).  With NULL such a
+ *            failure goes unreported.
  *   stream   cudaStream_t as void* (NULL = legacy default stream); the
  *            buffers must belong to the calling thread's current device.
  * Scratch comes from one file-scope device array of
  * HOSCF_STATIC_SCRATCH_BYTES (64 MiB) that every GPU loading this library
  * holds until the process exits.  Problems whose scratch would exceed it are
- * rejected with HOSCF_EINVAL (e.g. 512^3 FP32 fits, 1024^3 does not).  The
- * first call on each device looks up the array's device address (with that
- * device current), so make that first call before any stream capture.
- * All calls share the array and every call overwrites it: calls that overlap
- * on the GPU (other streams, other threads) race and must be serialised by
- * the caller.  Asynchronous on `stream`; status codes only (no message).
+ * rejected with HOSCF_EINVAL (e.g. 512^3 FP32 fits, 1024^3 does not).  Each
+ * call whose stream is not capturing looks up the array's device address
+ * (with the device current; so a device reset between calls is harmless);
+ * a call made while the stream captures uses the address an earlier call on
+ * that device found, so make one call before any stream capture (EINVAL
+ * otherwise).  All calls share the array and every call overwrites it:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  Asynchronous on `stream`; status codes only
+ * (no message).
  */
 #define HOSCF_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 hoscf_status hoscf_ttvc_blocks_static(const hoscf_tensor_desc* T, const float* u, float* H,
-                                      void* stream);
+                                      int* status, void* stream);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,10 @@ What each function follows
                           must reproduce plain HOSCF's iterates).
 ``hopm``                  the HOPM (ALS) baseline named in Sec. 1 / Sec. 6.1,
                           used as an independent cross-check only.
+``asvd``                  the ASVD comparison method of Sec. 1 (d = 2, 3): two
+                          factors at a time from the largest singular pair of
+                          the coupling block of the two free modes, Gauss-Seidel
+                          over the fixed mode.
 ``greedy``                the greedy rank-one update of Sec. 1 / Example 3:
                           B^(r) = best rank-one approximation of A^(r),
                           A^(r+1) = A^(r) - B^(r), A^(1) = A; the deflated tensor
@@ -238,13 +242,15 @@ def nepv_matrix(Hp, dims) -> np.ndarray:
     return full_block_matrix(Hp, dims) / (len(dims) - 1)
 
 
-def largest_magnitude_eigpair(J, x_prev=None):
+def largest_magnitude_eigpair(J, x_prev=None, dense_max: int = 4096):
     """Largest-magnitude eigenpair of a symmetric matrix (Alg. 1 line 5).
 
     Ties between +l and -l go to the positive one.  The eigenvector is unit
-    length with <x, x_prev> >= 0 when x_prev is given."""
+    length with <x, x_prev> >= 0 when x_prev is given.  Matrices of order up
+    to `dense_max` use LAPACK's dense eigh; larger ones ARPACK (both ends of
+    the spectrum)."""
     n = J.shape[0]
-    if n <= 4096:
+    if n <= dense_max:
         w, V = np.linalg.eigh(J)
         lo, hi = 0, n - 1
         k = hi if w[hi] >= -w[lo] else lo
@@ -437,6 +443,57 @@ def hoscf(T, u0_list, tol: float = 1e-8, max_iter: int = 200, variant: str = "ho
     r41 = residual_4_1(Hp, dims, u)
     sigma_f, u_f = gauge(*final_fix(sigma, u))            # lines 12-15 + gauge
     return Result(sigma_f, u_f, iters, passes, r, r <= tol, hist, accepts, r41)
+
+
+def asvd(T, u0_list, tol: float = 1e-8, max_iter: int = 500, nthreads: int = 0,
+         keep_history: bool = True) -> Result:
+    """ASVD, the alternating-SVD comparison method of Sec. 1, for d = 3 (and
+    the degenerate d = 2, where it is one SVD).
+
+    A Gauss-Seidel sweep over the fixed mode f = 1, 2, 3, 1, ...: with u^(f)
+    fixed, the other two factors (m, n) become the largest singular pair of
+    the intermediate matrix A x_f u^(f), which is the coupling block A_{m,n}
+    of eq. (3.3).  Reading for the sign: (a, b) with a^T A_{m,n} b = +s_1, the
+    pair negated together when <a, u^(m)> + <b, u^(n)> < 0.  One sub-step is
+    one eigen step (iters); the blocks at every new point are one pass, and
+    the certificate and stopping rule are HOSCF's (KKT residual at the point
+    the blocks were built for)."""
+    dims = list(T.shape)
+    d = len(dims)
+    if d not in (2, 3):
+        raise ValueError("ASVD is defined here for orders 2 and 3")
+    u = _unit_blocks(u0_list)
+    hist = []
+    iters = passes = 0
+
+    def build(uu):
+        nonlocal passes
+        Hq = blocks(T, uu, nthreads)
+        passes += 1
+        _, sg, rr = kkt_from_blocks(Hq, dims, uu)
+        if keep_history:
+            hist.append((sg, rr))
+        return Hq, sg, rr
+
+    Hp, sigma, r = build(u)
+    while not (r <= tol or iters >= max_iter):
+        if d == 2:
+            m, n = 0, 1
+        else:
+            f = iters % 3
+            m, n = [k for k in range(3) if k != f]
+        B = unpack_blocks(Hp, dims)[(m, n)]
+        U, S, Vt = np.linalg.svd(B)
+        a, b = U[:, 0].copy(), Vt[0].copy()
+        if float(a @ u[m]) + float(b @ u[n]) < 0:
+            a, b = -a, -b
+        u = list(u)
+        u[m], u[n] = a, b
+        iters += 1
+        Hp, sigma, r = build(u)
+    r41 = residual_4_1(Hp, dims, u)
+    sigma_f, u_f = gauge(*final_fix(sigma, u))
+    return Result(sigma_f, u_f, iters, passes, r, r <= tol, hist, 0, r41)
 
 
 def hopm(T, u0_list, tol: float = 1e-10, max_iter: int = 2000):

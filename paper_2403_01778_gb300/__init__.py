@@ -5,8 +5,8 @@ The compute path is libhoscf.so (hand-written CUDA); this package only
 marshals torch tensors into it.  There is no CPU fallback: importing the
 functions works everywhere, calling them needs the built library and a GPU.
 """
-from .api import (HoscfError, SolveResult, balanced, handle, hoscf_backward, hoscf_eig_step,  # noqa: F401
-                  hoscf_opts_default, hoscf_profile_enable, hoscf_profile_read, hoscf_quantize,
+from .api import (HoscfError, SolveResult, handle, hoscf_backward, hoscf_device_status,  # noqa: F401
+                  hoscf_eig_step, hoscf_opts_default, hoscf_profile_enable, hoscf_profile_read, hoscf_quantize,
                   hoscf_rqi_step, hoscf_selftest_timeout, hoscf_solve, hoscf_solve_batched,
                   hoscf_solve_greedy,
                   hoscf_ttvc_blocks, hoscf_ttvc_blocks_static, hoscf_workspace_size, n_blocks,

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "NOT_CONVERGED
                 5: "NONFINITE", 6: "TIMEOUT", 7: "EUNSUPPORTED"}
 
 HOSCF_F32, HOSCF_BF16, HOSCF_F8E4M3 = 0, 1, 2
-VARIANTS = {"hoscf": 0, "ihoscf": 1, "ihoscf_prev": 2, "jacobi_hopm": 3}
+VARIANTS = {"hoscf": 0, "ihoscf": 1, "ihoscf_prev": 2, "jacobi_hopm": 3, "asvd": 4}
 MAX_ORDER = 8
 
 # Every entry point the header declares (checked by the ABI test).
@@ -26,7 +26,7 @@ EXPORTS = ("hoscf_create", "hoscf_destroy", "hoscf_last_error", "hoscf_opts_defa
            "hoscf_workspace_size", "hoscf_ttvc_blocks", "hoscf_eig_step", "hoscf_rqi_step", "hoscf_solve",
            "hoscf_solve_batched", "hoscf_backward", "hoscf_quantize",
            "hoscf_ttvc_blocks_static", "hoscf_profile_enable", "hoscf_profile_read",
-           "hoscf_selftest_timeout", "hoscf_solve_greedy")
+           "hoscf_selftest_timeout", "hoscf_solve_greedy", "hoscf_device_status")
 
 
 class TensorDesc(ctypes.Structure):
@@ -84,10 +84,11 @@ def load():
                                    c_void_p, c_void_p, c_void_p]
     lib.hoscf_quantize.argtypes = [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_void_p,
                                    c_void_p]
-    lib.hoscf_ttvc_blocks_static.argtypes = [P(TensorDesc), c_void_p, c_void_p, c_void_p]
+    lib.hoscf_ttvc_blocks_static.argtypes = [P(TensorDesc), c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.hoscf_device_status.argtypes = [c_void_p, c_void_p]
     lib.hoscf_profile_enable.argtypes = [c_void_p, c_int]
     lib.hoscf_profile_read.argtypes = [c_void_p, P(c_int), P(c_double)]
-    lib.hoscf_selftest_timeout.argtypes = [c_void_p, c_int, c_int64]
+    lib.hoscf_selftest_timeout.argtypes = [c_void_p, c_int, c_int64, c_void_p]
     lib.hoscf_solve_greedy.argtypes = [c_void_p, P(TensorDesc), c_int, c_void_p, P(Opts),
                                        c_void_p, P(c_double), P(Info), P(c_double), c_void_p]
     for name in EXPORTS:

@@ -137,28 +137,45 @@ def hoscf_profile_read(device: int = 0) -> tuple[int, float]:
     return n.value, ms.value
 
 
-def hoscf_selftest_timeout(kind: int, timeout_ns: int = 1_000_000, device: int = 0) -> int:
+def hoscf_selftest_timeout(kind: int, timeout_ns: int = 1_000_000, device: int = 0,
+                           stream=None) -> int:
     """Run a bounded device wait that can never be satisfied (kind 0: an
-    mbarrier phase, 1: the grid barrier with an arrival missing) and return
-    the library's status for it (HOSCF_TIMEOUT = 6 when the failure path
-    works)."""
+    mbarrier phase, 1: the grid barrier with an arrival missing, 2: kind 0
+    launched asynchronously, reported later by hoscf_device_status) and
+    return the library's status for it (HOSCF_TIMEOUT = 6 when the failure
+    path works; OK for a launched kind 2)."""
     h = handle(device)
-    return int(_lib.load().hoscf_selftest_timeout(h, int(kind), int(timeout_ns)))
+    return int(_lib.load().hoscf_selftest_timeout(h, int(kind), int(timeout_ns),
+                                                  _stream_ptr(stream)))
+
+
+def hoscf_device_status(device: int = 0, stream=None) -> int:
+    """Failures the asynchronous calls recorded on the device: synchronises
+    the stream, returns the status (0 = OK, 6 = TIMEOUT, 5 = NONFINITE) and
+    clears it."""
+    h = handle(device)
+    return int(_lib.load().hoscf_device_status(h, _stream_ptr(stream)))
 
 
 def hoscf_ttvc_blocks_static(T: torch.Tensor, u: torch.Tensor, H: torch.Tensor | None = None,
-                             stream=None) -> torch.Tensor:
+                             status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """hoscf_ttvc_blocks without allocation inside the library: scratch comes
     from the library's fixed 64 MiB device array (calls must not overlap).
-    The output tensor is allocated here by torch unless H is given."""
+    The output tensor is allocated here by torch unless H is given; `status`
+    (a 1-element int32 CUDA tensor, optional) receives the pass's device
+    status (0 = H valid)."""
     d = _Desc(T)
     u = u.contiguous()
     if u.dtype != torch.float32 or u.numel() != n_tot(d.shape):
         raise ValueError("u must be float32 with sum(dims) entries")
     if H is None:
         H = torch.empty(n_blocks(d.shape), device=T.device, dtype=torch.float32)
+    if status is not None and (status.dtype != torch.int32 or not status.is_cuda):
+        raise ValueError("status must be an int32 CUDA tensor")
     st = _lib.load().hoscf_ttvc_blocks_static(ctypes.byref(d.desc), ctypes.c_void_p(u.data_ptr()),
-                                              ctypes.c_void_p(H.data_ptr()), _stream_ptr(stream))
+                                              ctypes.c_void_p(H.data_ptr()),
+                                              ctypes.c_void_p(status.data_ptr() if status is not None else 0),
+                                              _stream_ptr(stream))
     if st != 0:
         raise HoscfError(st, "hoscf_ttvc_blocks_static failed")
     return H
@@ -390,8 +407,3 @@ def hoscf_solve_batched(tensors, u0s, tol=1e-6, max_iter=200, eig_tol=None, time
                                          _stream_ptr(stream))
     _check(st, h, allow=(0, _lib.HOSCF_NOT_CONVERGED))
     return [float(s) for s in sig], uo, [infos[i] for i in range(cnt)], st
-
-
-def balanced(u: torch.Tensor, dims) -> torch.Tensor:
-    """x = [u^(1); ...; u^(d)] / sqrt(d) in float64 (marshalling helper)."""
-    return u.double() / math.sqrt(len(dims))

@@ -33,6 +33,7 @@ struct hoscf_handle {
     bool prof_on = false;
     size_t prof_n = 0;
     std::vector<KernelEvents> prof;
+    BatchGraphCache graphs;       // batched solve: instantiated graphs of recent batches
     char msg[512] = {0};
 };
 
@@ -97,7 +98,12 @@ struct Layout {
 
 hoscf_status ensure_ws(hoscf_handle* h, size_t bytes) {
     if (bytes <= h->ws_bytes) return HOSCF_OK;
+    int pending = 0;   // a failure recorded by earlier asynchronous calls survives the move
     if (h->ws) {
+        // nothing may still run on the old workspace when it is freed
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(&pending, h->ws + kOffErr, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "workspace move");
         cudaFree(h->ws);
         h->ws = nullptr;
         h->ws_bytes = 0;
@@ -110,6 +116,12 @@ hoscf_status ensure_ws(hoscf_handle* h, size_t bytes) {
                     cudaGetErrorString(e));
     }
     h->ws_bytes = want;
+    // the head (status word, barrier counter, scalars) starts at zero
+    e = cudaMemset(h->ws, 0, kHeadBytes);
+    if (e == cudaSuccess && pending)
+        e = cudaMemcpy(h->ws + kOffErr, &pending, sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(h, e, "workspace set-up");
     return HOSCF_OK;
 }
 
@@ -180,6 +192,14 @@ int* dev_err(hoscf_handle* h) { return reinterpret_cast<int*>(h->ws + kOffErr); 
 
 hoscf_status reset_dev_state(hoscf_handle* h, cudaStream_t st) {
     CK(cudaMemsetAsync(h->ws, 0, 256, st));
+    return HOSCF_OK;
+}
+
+// The asynchronous entry points clear only the grid-barrier state: a failure
+// an earlier asynchronous call recorded in the device status word stays there
+// until hoscf_device_status reads it.
+hoscf_status reset_barrier_state(hoscf_handle* h, cudaStream_t st) {
+    CK(cudaMemsetAsync(h->ws + kOffBar, 0, 256 - kOffBar, st));
     return HOSCF_OK;
 }
 
@@ -294,6 +314,7 @@ hoscf_status hoscf_destroy(hoscf_handle* h) {
         if (h->ws) cudaFree(h->ws);
         if (h->h_pinned) cudaFreeHost(h->h_pinned);
         if (h->pinned_big) cudaFreeHost(h->pinned_big);
+        h->graphs.release();
         if (h->own) cudaStreamDestroy(h->own);
         for (KernelEvents& e : h->prof) {
             cudaEventDestroy(e.begin);
@@ -370,6 +391,21 @@ hoscf_status hoscf_ttvc_blocks(hoscf_handle* h, const hoscf_tensor_desc* T, cons
     return HOSCF_OK;
 }
 
+hoscf_status hoscf_device_status(hoscf_handle* h, void* stream) {
+    if (!h) return HOSCF_EINVAL;
+    DeviceGuard g(h->device);
+    if (!h->ws) return HOSCF_OK;                  // nothing has run on this handle
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CK(cudaMemcpyAsync(h->h_pinned + 32, h->ws + kOffErr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int code;
+    memcpy(&code, h->h_pinned + 32, sizeof(int));
+    if (code == 0) return HOSCF_OK;
+    CK(cudaMemsetAsync(h->ws + kOffErr, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    return dev_status(h, code);
+}
+
 hoscf_status hoscf_profile_enable(hoscf_handle* h, int enable) {
     if (!h) return HOSCF_EINVAL;
     h->prof_on = enable != 0;
@@ -407,7 +443,7 @@ hoscf_status hoscf_eig_step(hoscf_handle* h, int order, const int64_t* dims, con
                                std::min(std::max(o.eig_max_steps, 2), 128), L);
     if (st) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    st = reset_dev_state(h, s);
+    st = reset_barrier_state(h, s);
     if (st) return st;
     return eig_launch(h, L, H, x_prev, nullptr, x_out, u_out, lambda_out, &o, 0, 0.0, s,
                       o.eig_adapt);
@@ -428,7 +464,7 @@ hoscf_status hoscf_rqi_step(hoscf_handle* h, int order, const int64_t* dims, con
                                std::min(std::max(o.eig_max_steps, 2), 128), L);
     if (st) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    st = reset_dev_state(h, s);
+    st = reset_barrier_state(h, s);
     if (st) return st;
     // start x~ = u / sqrt(d) (the kernel's balanced start from factors), shift
     // = the Rayleigh quotient alpha_0, no certificate shortcut
@@ -447,8 +483,11 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
     if (opts) o = *opts;
     if (o.max_iter < 0 || !(o.tol >= 0)) return fail(h, HOSCF_EINVAL, "bad tol / max_iter");
     if (o.variant != HOSCF_VARIANT_HOSCF && o.variant != HOSCF_VARIANT_IHOSCF &&
-        o.variant != HOSCF_VARIANT_IHOSCF_PREV && o.variant != HOSCF_VARIANT_JACOBI_HOPM)
+        o.variant != HOSCF_VARIANT_IHOSCF_PREV && o.variant != HOSCF_VARIANT_JACOBI_HOPM &&
+        o.variant != HOSCF_VARIANT_ASVD)
         return fail(h, HOSCF_EINVAL, "unknown variant %d", o.variant);
+    if (o.variant == HOSCF_VARIANT_ASVD && T->order > 3)
+        return fail(h, HOSCF_EUNSUPPORTED, "ASVD is built for orders 2 and 3");
     const hoscf_tensor_desc* Tr = o.refine;
     if (Tr) {
         st = check_desc(h, Tr);
@@ -462,10 +501,36 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Layout L;
     const int mmax = std::min(std::max(o.eig_max_steps, 2), 128);
+    // ASVD: the eigen step of each two-mode sub-problem (one block, J2 =
+    // [[0, A_mn], [A_mn^T, 0]]) runs in the extra region, after its input and
+    // output pair buffers and its eigenvalue
+    const bool asvd = o.variant == HOSCF_VARIANT_ASVD;
+    Layout Lpair[3];
+    size_t extra = 0, off_pin = 0, off_pout = 0, off_lam = 0, off_peig = 0;
+    if (asvd) {
+        int64_t ntot = 0;
+        for (int k = 0; k < T->order; ++k) ntot += T->dims[k];
+        off_pin = 0;
+        off_pout = align_up(sizeof(float) * (size_t)ntot, 256);
+        off_lam = off_pout + align_up(sizeof(float) * (size_t)ntot, 256);
+        off_peig = off_lam + 256;
+        size_t peig = 0;
+        int b = 0;
+        for (int m = 0; m < T->order; ++m)
+            for (int n = m + 1; n < T->order; ++n, ++b) {
+                const int64_t dd[2] = {T->dims[m], T->dims[n]};
+                if (!make_shape(2, dd, Lpair[b].s) ||
+                    !make_eig_plan(Lpair[b].s, h->nsm, 1, mmax, Lpair[b].ep))
+                    return fail(h, HOSCF_EINVAL, "ASVD eigen plan failed");
+                peig = std::max(peig, Lpair[b].ep.bytes);
+            }
+        extra = off_peig + peig;
+    }
     // the pass region must fit both the low-precision and the FP32 pass
     st = plan_all(h, T->order, T->dims, Tr ? HOSCF_F32 : T->dtype, true, true, mmax, L,
-                  Tr ? T->dtype : -1);
+                  Tr ? T->dtype : -1, extra);
     if (st) return st;
+    for (Layout& lp : Lpair) lp.off_eig = L.off_extra + off_peig;
     PassPlan pp_lo = L.pp;
     if (Tr) make_pass_plan(L.s, T->dtype, h->nsm, true, pp_lo);
     const Shape& S = L.s;
@@ -521,9 +586,11 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
     // is certified); scalars are read back synchronously
     auto do_step = [&](const float* Hsrc, const float* u, float* u_res, int rqi, double* out,
                        int check = 1) -> hoscf_status {
+        // Jacobi-HOPM takes its update from the certificate's mat-vec; ASVD
+        // needs only the certificate here (its step is the pair's eigen step)
+        const int hopm_mode = (o.variant == HOSCF_VARIANT_JACOBI_HOPM || asvd) && rqi == 0 ? 1 : 0;
         hoscf_status q = eig_launch(h, L, Hsrc, nullptr, u, nullptr, u_res, nullptr, &o, check,
-                                    o.tol, s, o.eig_adapt, rqi, 0.f, nullptr, 0.f, 0.0,
-                                    o.variant == HOSCF_VARIANT_JACOBI_HOPM && rqi == 0 ? 1 : 0);
+                                    o.tol, s, o.eig_adapt, rqi, 0.f, nullptr, 0.f, 0.0, hopm_mode);
         if (q) return q;
         cudaError_t e = cudaMemcpyAsync(h->h_pinned, scal, sizeof(double) * SC_COUNT,
                                         cudaMemcpyDeviceToHost, s);
@@ -566,7 +633,9 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
             // precision form: the low-precision tensor has done its part; the
             // remaining passes and the certificate use the FP32 tensor
             use_ref = true;
-            if (sc[SC_CONVERGED] == 0.0 && iters < o.max_iter) {
+            // (ASVD's step is not the certificate's by-product: it re-certifies
+            // the current point on the FP32 tensor and steps from there)
+            if (!asvd && sc[SC_CONVERGED] == 0.0 && iters < o.max_iter) {
                 ++iters;
                 std::swap(ucur, unext);
             }
@@ -580,6 +649,30 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
         }
         if (iters >= o.max_iter) break;
         ++iters;
+        if (asvd) {
+            // fixed mode f = 1, 2, 3, 1, ... (d = 3); the free pair (m, n)
+            int m = 0, n = 1;
+            if (S.d == 3) {
+                const int f = (iters - 1) % 3;
+                m = f == 0 ? 1 : 0;
+                n = f == 2 ? 1 : 2;
+            }
+            const int b = m == 0 ? n - 1 : 2;      // lexicographic pair index (d <= 3)
+            float* pin = reinterpret_cast<float*>(h->ws + L.off_extra + off_pin);
+            float* pout = reinterpret_cast<float*>(h->ws + L.off_extra + off_pout);
+            double* lam = reinterpret_cast<double*>(h->ws + L.off_extra + off_lam);
+            const int64_t im = S.dims[m], in = S.dims[n];
+            CK(cudaMemcpyAsync(pin, ucur + S.moff[m], sizeof(float) * im, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(pin + im, ucur + S.moff[n], sizeof(float) * in, cudaMemcpyDeviceToDevice, s));
+            st = eig_launch(h, Lpair[b], Hcur + S.boff[b], nullptr, pin, nullptr, pout, lam, &o, 0,
+                            0.0, s, o.eig_adapt);
+            if (st) return st;
+            CK(launch_asvd_pair_fix(ucur, S.n_tot, S.moff[m], im, S.moff[n], in, pout, lam, unext, s));
+            std::swap(ucur, unext);
+            st = do_pass(ucur, Hcur);
+            if (st) return st;
+            continue;
+        }
         if (o.variant == HOSCF_VARIANT_HOSCF || o.variant == HOSCF_VARIANT_JACOBI_HOPM) {
             std::swap(ucur, unext);
             st = do_pass(ucur, Hcur);
@@ -587,7 +680,8 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
             continue;
         }
         if (o.variant == HOSCF_VARIANT_IHOSCF) {
-            // RQI with J built at the new point x_k (Sec. 4.4, reading in the design doc)
+            // RQI with J built at the new point x_k (Sec. 4.4, read with the
+            // matrix of the point the eigen step just returned)
             st = do_pass(unext, Hoth);                 // J(x_k)
             if (st) return st;
             st = do_step(Hoth, unext, uy, 1, sk);      // certify x_k, then solve for y
@@ -686,11 +780,15 @@ hoscf_status hoscf_solve_batched(hoscf_handle* h, int count, const hoscf_tensor_
     if (threads != 256 && threads != 512 && threads != 1024)
         return fail(h, HOSCF_EINVAL, "batch_threads must be 256, 512 or 1024");
     DeviceGuard g(h->device);
-    // descriptors + results: ~100 bytes per tensor, staged through pinned memory
+    // descriptors + results: ~100 bytes per tensor, staged through pinned
+    // memory; the workspace head (status word, barrier state) is left alone
     const size_t need = 4096 + (size_t)count * 128;
-    hoscf_status st = ensure_ws(h, need);
+    hoscf_status st = ensure_ws(h, kHeadBytes + need);
     if (st) return st;
     if (h->pinned_big_bytes < need) {
+        // captured graphs copy through the old staging buffer: drop them first
+        CK(cudaDeviceSynchronize());
+        h->graphs.release();
         if (h->pinned_big) cudaFreeHost(h->pinned_big);
         h->pinned_big = nullptr;
         h->pinned_big_bytes = 0;
@@ -703,8 +801,9 @@ hoscf_status hoscf_solve_batched(hoscf_handle* h, int count, const hoscf_tensor_
     if (!h->own) CK(cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking));
     CK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
     Err err;
-    st = run_batched(count, T, u0, u_out, o, threads, h->ws, h->ws_bytes, h->nsm, h->own,
-                     sigma_out, infos, h->pinned_big, h->pinned_big_bytes, err);
+    st = run_batched(count, T, u0, u_out, o, threads, h->ws + kHeadBytes, h->ws_bytes - kHeadBytes,
+                     h->nsm, h->own, sigma_out, infos, h->pinned_big, h->pinned_big_bytes,
+                     h->graphs, err);
     if (st) return fail(h, st, "%s", err.msg);
     return HOSCF_OK;
 }
@@ -839,8 +938,8 @@ hoscf_status hoscf_solve_greedy(hoscf_handle* h, const hoscf_tensor_desc* T, int
     return result;
 }
 
-hoscf_status hoscf_selftest_timeout(hoscf_handle* h, int kind, int64_t timeout_ns) {
-    if (!h || (kind != 0 && kind != 1) || timeout_ns <= 0 || timeout_ns > 10000000000ll)
+hoscf_status hoscf_selftest_timeout(hoscf_handle* h, int kind, int64_t timeout_ns, void* stream) {
+    if (!h || kind < 0 || kind > 2 || timeout_ns <= 0 || timeout_ns > 10000000000ll)
         return HOSCF_EINVAL;
     DeviceGuard g(h->device);
     const size_t need = kHeadBytes;
@@ -850,6 +949,14 @@ hoscf_status hoscf_selftest_timeout(hoscf_handle* h, int kind, int64_t timeout_n
     cudaStream_t s = h->own;
     st = reset_dev_state(h, s);
     if (st) return st;
+    if (kind == 2) {
+        // asynchronous form: the wait runs on the caller's stream and its
+        // timeout is left in the status word for hoscf_device_status
+        selftest_mbar_kernel<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+            dev_err(h), (uint64_t)timeout_ns);
+        CK(cudaGetLastError());
+        return HOSCF_OK;
+    }
     if (kind == 0) {
         selftest_mbar_kernel<<<1, 32, 0, s>>>(dev_err(h), (uint64_t)timeout_ns);
     } else {

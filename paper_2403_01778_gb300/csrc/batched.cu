@@ -469,7 +469,8 @@ struct BatchDev {
 hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* const* u0,
                          float* const* u_out, const hoscf_opts& o, int threads, char* ws,
                          size_t ws_bytes, int nsm, cudaStream_t st, double* sigma_out,
-                         hoscf_info* infos, void* pinned, size_t pinned_bytes, Err& err) {
+                         hoscf_info* infos, void* pinned, size_t pinned_bytes,
+                         BatchGraphCache& cache, Err& err) {
     // validate and describe the batch
     std::vector<BatchItem> items((size_t)count);
     std::vector<int64_t> sizes((size_t)count);
@@ -574,11 +575,22 @@ hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* con
     mix(&threads, sizeof(threads));
     mix(&smem, sizeof(smem));
     mix(&st, sizeof(st));
-    static std::mutex mu;
-    static cudaGraphExec_t cached = nullptr;
-    static uint64_t cached_key = 0;
-    std::lock_guard<std::mutex> lock(mu);
-    if (e == cudaSuccess && !(cached && cached_key == key)) {
+    const void* hpp = hp;
+    const void* wsp = ws;
+    mix(&hpp, sizeof(hpp));
+    mix(&wsp, sizeof(wsp));
+    if (key == 0) key = 1;
+    int slot = -1;
+    for (int i = 0; i < BatchGraphCache::kSlots; ++i)
+        if (cache.exec[i] && cache.key[i] == key) slot = i;
+    if (e == cudaSuccess && slot < 0) {
+        // capture this batch; it replaces the least recently used entry
+        slot = 0;
+        for (int i = 1; i < BatchGraphCache::kSlots; ++i)
+            if (!cache.exec[i] || (cache.exec[slot] && cache.used[i] < cache.used[slot])) slot = i;
+        if (cache.exec[slot]) cudaGraphExecDestroy(cache.exec[slot]);
+        cache.exec[slot] = nullptr;
+        cache.key[slot] = 0;
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
@@ -590,14 +602,20 @@ hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* con
             e = cudaStreamEndCapture(st, &graph);
         }
         if (e == cudaSuccess) {
-            if (cached) cudaGraphExecDestroy(cached);
-            cached = nullptr;
-            e = cudaGraphInstantiate(&cached, graph, 0);
-            cached_key = (e == cudaSuccess) ? key : 0;
+            e = cudaGraphInstantiate(&cache.exec[slot], graph, 0);
+            if (e == cudaSuccess) {
+                cache.key[slot] = key;
+                ++cache.captures;
+            } else {
+                cache.exec[slot] = nullptr;
+            }
         }
         if (graph) cudaGraphDestroy(graph);
     }
-    if (e == cudaSuccess) e = cudaGraphLaunch(cached, st);
+    if (e == cudaSuccess) {
+        cache.used[slot] = ++cache.clock;
+        e = cudaGraphLaunch(cache.exec[slot], st);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaGetLastError();

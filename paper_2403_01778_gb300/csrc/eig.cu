@@ -889,6 +889,44 @@ __global__ void final_fix_kernel(float* __restrict__ u, int d, ModeInfoArr mi, d
     if (threadIdx.x == 0) *sigma = fabs(*sigma);
 }
 
+// ASVD sub-step epilogue (Sec. 1): the eigen step of the two-mode problem
+// J2 = [[0, B], [B^T, 0]] returned the normalised blocks (a, b') of an
+// eigenvector for lambda = +-s_1.  For lambda < 0 the vector is (a, -b), so b'
+// is negated to give a^T B b = +s_1; the pair is then negated together when
+// <a, u_m> + <b, u_n> < 0 (u the current point).  The next iterate is the
+// current one with modes m and n replaced.  One CTA; the dot product is an
+// FP64 sum in a fixed order.
+__global__ void asvd_pair_fix_kernel(const float* __restrict__ ucur, int64_t n_tot, int64_t om,
+                                     int64_t im, int64_t on, int64_t in,
+                                     const float* __restrict__ pair, const double* __restrict__ lambda,
+                                     float* __restrict__ unext) {
+    __shared__ double red[32];
+    __shared__ int s_flip;
+    const float sb = (*lambda < 0.0) ? -1.f : 1.f;
+    double acc = 0.0;
+    for (int64_t q = threadIdx.x; q < im + in; q += blockDim.x) {
+        const float v = q < im ? pair[q] : sb * pair[q];
+        const float w = q < im ? ucur[om + q] : ucur[on + (q - im)];
+        acc += (double)v * (double)w;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(HOSCF_FULLMASK, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        s_flip = t < 0.0 ? 1 : 0;
+    }
+    __syncthreads();
+    const float fa = s_flip ? -1.f : 1.f;
+    for (int64_t q = threadIdx.x; q < n_tot; q += blockDim.x) {
+        float v = ucur[q];
+        if (q >= om && q < om + im) v = fa * pair[q - om];
+        if (q >= on && q < on + in) v = fa * sb * pair[im + (q - on)];
+        unext[q] = v;
+    }
+}
+
 // ---------------------------------------------------------------- host
 static size_t lanczos_smem_base(int64_t n, int R, int mmax) {
     return sizeof(double) * (size_t)(16 + 3 * kMaxLanczos) + sizeof(double) * (size_t)R +
@@ -1063,6 +1101,13 @@ cudaError_t launch_scale_modes(const Shape& s, const float* u, const double* nrm
     const int64_t n = s.n_tot;
     scale_modes_kernel<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, st>>>(
         u, s.d, mode_info(s), nrm2, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_asvd_pair_fix(const float* ucur, int64_t n_tot, int64_t om, int64_t im,
+                                 int64_t on, int64_t in, const float* pair, const double* lambda,
+                                 float* unext, cudaStream_t st) {
+    asvd_pair_fix_kernel<<<1, 256, 0, st>>>(ucur, n_tot, om, im, on, in, pair, lambda, unext);
     return cudaGetLastError();
 }
 

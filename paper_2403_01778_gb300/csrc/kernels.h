@@ -20,10 +20,30 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
                       const KernelEvents* kev = nullptr);
 
 // batched.cu
+// Instantiated graphs of the batched solve, one small cache per handle: a
+// batch signature (descriptors, launch shape, buffers, stream) maps to the
+// graph captured for it; the least recently used entry is replaced.
+struct BatchGraphCache {
+    static constexpr int kSlots = 4;
+    uint64_t key[kSlots] = {};
+    cudaGraphExec_t exec[kSlots] = {};
+    uint64_t used[kSlots] = {};
+    uint64_t clock = 0;
+    int captures = 0;          // graphs captured over the handle's life (measurement)
+    void release() {
+        for (int i = 0; i < kSlots; ++i) {
+            if (exec[i]) cudaGraphExecDestroy(exec[i]);
+            exec[i] = nullptr;
+            key[i] = 0;
+        }
+    }
+};
+
 hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* const* u0,
                          float* const* u_out, const hoscf_opts& o, int threads, char* ws,
                          size_t ws_bytes, int nsm, cudaStream_t st, double* sigma_out,
-                         hoscf_info* infos, void* pinned, size_t pinned_bytes, Err& err);
+                         hoscf_info* infos, void* pinned, size_t pinned_bytes,
+                         BatchGraphCache& cache, Err& err);
 
 // backward.cu
 cudaError_t launch_tangent_project(const Shape& s, const float* u, const float* w, double* b,
@@ -98,5 +118,10 @@ cudaError_t launch_mode_norms(const Shape& s, const float* u, double* out, cudaS
 cudaError_t launch_scale_modes(const Shape& s, const float* u, const double* nrm2, float* out,
                                cudaStream_t st);
 cudaError_t launch_final_fix(const Shape& s, float* u, double* sigma, cudaStream_t st);
+// ASVD: sign rule for the top singular pair of block (m, n) and the next
+// iterate (the current one with modes m and n replaced).
+cudaError_t launch_asvd_pair_fix(const float* ucur, int64_t n_tot, int64_t om, int64_t im,
+                                 int64_t on, int64_t in, const float* pair, const double* lambda,
+                                 float* unext, cudaStream_t st);
 
 }  // namespace hoscf

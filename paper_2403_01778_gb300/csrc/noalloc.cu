@@ -22,16 +22,26 @@ std::mutex g_mu;
 char* g_scratch_dev[kMaxDevices] = {nullptr};
 
 // Host code cannot use g_scratch's name as a device address (it is a host
-// stand-in); the real address is looked up once per device, with that device
-// current.
-hoscf_status scratch_for_current_device(char** out) {
+// stand-in); the real address is looked up with the device current.  The
+// lookup is repeated on every call whose stream is not capturing, so a
+// context that was destroyed and created again (cudaDeviceReset, a primary
+// context released and retained by the host application) never leaves a
+// stale address behind; while a stream captures, the address found by an
+// earlier call on that device is used.
+hoscf_status scratch_for_current_device(cudaStream_t st, char** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return HOSCF_ECUDA;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return HOSCF_ECUDA;
+    }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_dev[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_dev[dev]) {
+        if (cap != cudaStreamCaptureStatusNone) return HOSCF_EINVAL;   // no set-up during capture
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
@@ -46,7 +56,7 @@ hoscf_status scratch_for_current_device(char** out) {
 }  // namespace
 
 extern "C" hoscf_status hoscf_ttvc_blocks_static(const hoscf_tensor_desc* T, const float* u,
-                                                 float* H, void* stream) {
+                                                 float* H, int* status, void* stream) {
     using namespace hoscf;
     if (!T || !u || !H || !T->data || !T->dims) return HOSCF_EINVAL;
     if (T->order < 2 || T->order > HOSCF_MAX_ORDER) return HOSCF_EINVAL;
@@ -63,16 +73,24 @@ extern "C" hoscf_status hoscf_ttvc_blocks_static(const hoscf_tensor_desc* T, con
     PassPlan pp;
     make_pass_plan(s, T->dtype, nsm, true, pp);
     if (kHead + pp.bytes > (size_t)HOSCF_STATIC_SCRATCH_BYTES) return HOSCF_EINVAL;  // too large
-    char* base = nullptr;
-    hoscf_status st = scratch_for_current_device(&base);
-    if (st) return st;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    char* base = nullptr;
+    hoscf_status st = scratch_for_current_device(cs, &base);
+    if (st) return st;
     int* dev_err = reinterpret_cast<int*>(base);
     if (cudaMemsetAsync(dev_err, 0, sizeof(int), cs) != cudaSuccess) {
         cudaGetLastError();
         return HOSCF_ECUDA;
     }
     Err err;
-    return run_ttvc(s, pp, T->dtype, T->data, T->scales, u, H, base + kHead, dev_err,
-                    2000000000ull, cs, err);
+    st = run_ttvc(s, pp, T->dtype, T->data, T->scales, u, H, base + kHead, dev_err,
+                  2000000000ull, cs, err);
+    if (st) return st;
+    // the pass's device status word (0, or the code of a wait that gave up)
+    // goes to the caller's word, in stream order after the pass
+    if (status && cudaMemcpyAsync(status, dev_err, sizeof(int), cudaMemcpyDeviceToDevice, cs) != cudaSuccess) {
+        cudaGetLastError();
+        return HOSCF_ECUDA;
+    }
+    return HOSCF_OK;
 }

@@ -633,7 +633,10 @@ __global__ void __launch_bounds__(256, TiledOcc<E>::value)
     flush(cc_t);
     if constexpr (RING) {
         if (!ok) {
-            // A wait gave up (results are void; the host reports the timeout).
+            // A wait gave up: the blocks are void and the code is in the device
+            // status word, which the caller reads (hoscf_solve after each step,
+            // hoscf_device_status for the asynchronous calls, the status output
+            // of hoscf_ttvc_blocks_static).
             // Every copy already issued must still land before the CTA's shared
             // memory is released: wait for each, with a bound of at least 1 s
             // whatever the caller's limit.

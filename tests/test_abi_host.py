@@ -75,12 +75,14 @@ def test_null_and_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.hoscf_profile_enable(None, 1) == EINVAL
     n, ms = ctypes.c_int(), ctypes.c_double()
     assert lib.hoscf_profile_read(None, ctypes.byref(n), ctypes.byref(ms)) == EINVAL
-    assert lib.hoscf_ttvc_blocks_static(None, None, None, None) == EINVAL
+    assert lib.hoscf_ttvc_blocks_static(None, None, None, None, None) == EINVAL
+    assert lib.hoscf_device_status(None, None) == EINVAL
+    assert lib.hoscf_selftest_timeout(None, 0, 1000, None) == EINVAL
     # a descriptor of order 9 is rejected before any device call
     dims = (ctypes.c_int64 * 9)(*([2] * 9))
     desc = _lib.TensorDesc(9, dims, 0, ctypes.c_void_p(16), None)
     buf = ctypes.c_void_p(16)
-    assert lib.hoscf_ttvc_blocks_static(ctypes.byref(desc), buf, buf, None) == EINVAL
+    assert lib.hoscf_ttvc_blocks_static(ctypes.byref(desc), buf, buf, None, None) == EINVAL
     size = ctypes.c_size_t()
     for order, dd in [(3, (4, 0, 5)), (1, (4,)), (9, (2,) * 9)]:
         arr = (ctypes.c_int64 * len(dd))(*dd)

@@ -48,8 +48,30 @@ def test_wait_that_runs_out_reports_timeout_and_context_survives(kind):
 
 def test_selftest_rejects_bad_arguments():
     pkg = P()
-    assert pkg.hoscf_selftest_timeout(2, 1000) == 1
+    assert pkg.hoscf_selftest_timeout(3, 1000) == 1
     assert pkg.hoscf_selftest_timeout(0, 0) == 1
+
+
+def test_asynchronous_timeout_is_reported_by_device_status():
+    """A bounded wait that gives up inside an asynchronous call (kind 2: the
+    pass's mbarrier wait, launched on the caller's stream) is not known when
+    the call returns; hoscf_device_status reports it once and clears it, and
+    the handle then gives exact blocks and a working eigen step again."""
+    pkg = P()
+    assert pkg.hoscf_device_status() == 0
+    assert pkg.hoscf_selftest_timeout(2, 2_000_000) == 0       # launched, not read back
+    assert pkg.hoscf_device_status() == 6                      # HOSCF_TIMEOUT
+    assert pkg.hoscf_device_status() == 0                      # cleared
+    dims = (40, 50, 136)
+    rng = np.random.default_rng(9)
+    Ti = rng.integers(-3, 4, size=dims).astype(np.float32)
+    ui = [rng.integers(-2, 3, size=n).astype(np.float64) for n in dims]
+    H = pkg.hoscf_ttvc_blocks(torch.from_numpy(Ti).cuda(),
+                              torch.from_numpy(np.concatenate(ui).astype(np.float32)).cuda())
+    assert np.array_equal(H.double().cpu().numpy(), oracle.blocks(Ti, ui))
+    x0 = torch.from_numpy(np.concatenate(ui) / np.linalg.norm(np.concatenate(ui))).cuda()
+    pkg.hoscf_eig_step(dims, H, x0)
+    assert pkg.hoscf_device_status() == 0
 
 
 def test_kernel_timing_aid_counts_each_pass():

@@ -10,6 +10,7 @@ import torch
 
 import oracle
 import workloads as W
+from helpers import assert_same_solution, check_gauge
 
 pytestmark = pytest.mark.gpu
 
@@ -141,11 +142,12 @@ def test_eig_step_matches_dense_eigh():
     xg, ug, lg = P().hoscf_eig_step(dims, Hg, to_gpu(x_prev), eig_adapt=0.0)
     torch.cuda.synchronize()
     assert abs(lg.item() - lam) <= 1e-5 * abs(lam)
-    assert abs(abs(float(xg.cpu().numpy() @ x)) - 1) <= 1e-6
+    # both sides align the eigenvector with x_prev, so x is compared with its sign
+    assert abs(float(xg.cpu().numpy() @ x) - 1) <= 1e-6
     assert float(xg.cpu().numpy() @ x_prev) >= 0
     for n, un in enumerate(oracle.normalise_blocks(x, list(dims))):
         o = int(sum(dims[:n]))
-        assert abs(abs(float(ug.double().cpu().numpy()[o:o + dims[n]] @ un)) - 1) <= 1e-5
+        assert abs(float(ug.double().cpu().numpy()[o:o + dims[n]] @ un) - 1) <= 1e-5
 
 
 @pytest.mark.parametrize("dims", [(512, 512, 1024), (200, 200, 200, 200)])
@@ -221,10 +223,8 @@ def test_rqi_step_many_ctas_matches_oracle():
 
 
 def compare_solution(res, ref, tol=1e-5):
-    assert abs(res.sigma - ref.sigma) <= tol * abs(ref.sigma)
-    for un, ur in zip(res.factors(), ref.u):
-        c = abs(float(un.double().cpu().numpy() @ ur))
-        assert abs(1 - c) <= tol
+    """sigma and the factors with their signs (final fix + gauge on both sides)."""
+    assert_same_solution(res.sigma, res.factors(), ref.sigma, ref.u, tol)
 
 
 def test_solve_order2_is_svd():
@@ -233,10 +233,11 @@ def test_solve_order2_is_svd():
     u0 = torch.cat(W.unit_gaussian_vectors((40, 30), 12)).cuda()
     r = P().hoscf_solve(to_gpu(A), u0, tol=1e-6, max_iter=20)
     assert r.converged
-    assert abs(r.sigma - S[0]) <= 1e-5 * S[0]
-    f = r.factors()
-    assert abs(abs(float(f[0].double().cpu().numpy() @ U[:, 0])) - 1) <= 1e-5
-    assert abs(abs(float(f[1].double().cpu().numpy() @ Vt[0])) - 1) <= 1e-5
+    # the top singular pair with the gauge applied: u2's largest-|.| entry positive
+    a, b = U[:, 0].copy(), Vt[0].copy()
+    if b[int(np.argmax(np.abs(b)))] < 0:
+        a, b = -a, -b
+    assert_same_solution(r.sigma, r.factors(), S[0], [a, b])
 
 
 def test_solve_64cube_matches_oracle():
@@ -336,3 +337,58 @@ def test_misaligned_tensor_is_rejected():
     assert e.value.status == 1
     H = pkg.hoscf_ttvc_blocks(torch.zeros(dims, device="cuda"), u)
     assert float(H.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("max_iter", [0, 1, 3, 300])
+def test_reported_residuals_match_the_oracle_at_the_returned_point(max_iter):
+    """hoscf_info's KKT residual, eq. (4.1) residual and raw sigma against the
+    oracle's values (blocks by eq. 3.3 in FP64) at the factors the library
+    returns, both at unconverged points (max_iter 0, 1, 3) and at the
+    converged one.  Both residuals are invariant under the sign flips of the
+    final fix and the gauge.  Tolerance: relative 1e-4 plus an absolute 2e-6
+    for the FP32 blocks' rounding in J x - rho x."""
+    dims = (30, 40, 50)
+    T, _ = W.planted_cp(dims, [2.0, 1.0], seed=31, noise_abs=0.3)
+    u0 = torch.cat(W.unit_gaussian_vectors(dims, 33)).cuda()
+    r = P().hoscf_solve(T.cuda(), u0, tol=1e-6, max_iter=max_iter)
+    assert r.converged == (max_iter == 300)
+    uf = [v.double().cpu().numpy() for v in r.factors()]
+    Hr = oracle.blocks(T.numpy(), uf)
+    r41 = oracle.residual_4_1(Hr, list(dims), uf)
+    _, sig, rk = oracle.kkt_from_blocks(Hr, list(dims), uf)
+    assert abs(r.resid_4_1 - r41) <= 1e-4 * r41 + 2e-6, (r.resid_4_1, r41)
+    assert abs(r.resid - rk) <= 1e-4 * rk + 2e-6, (r.resid, rk)
+    assert abs(abs(r.sigma_raw) - abs(sig)) <= 1e-5 * abs(sig)
+    assert abs(r.sigma - abs(sig)) <= 1e-5 * abs(sig)
+    if max_iter == 0:
+        assert r.iters == 0 and r.passes == 1
+
+
+@pytest.mark.parametrize("dims,seed", [((20, 30, 25), 51), ((40, 7, 33), 52), ((130, 70, 260), 53),
+                                        ((30, 20), 54)])
+def test_asvd_matches_oracle(dims, seed):
+    """The ASVD comparison method (Sec. 1): two factors at a time from the
+    largest singular pair of the block of the free modes, Gauss-Seidel over
+    the fixed mode.  The solve reaches the oracle's ASVD point (sigma and the
+    signed factors), and the first sub-steps agree iterate by iterate: after
+    each one sigma = a^T A_mn b = s_1 > 0 on both sides."""
+    T, _ = W.planted_cp(dims, [4.0, 1.0], seed=seed, noise_abs=0.3)
+    u0 = W.unit_gaussian_vectors(dims, seed + 1)
+    ref = oracle.asvd(T.numpy(), [v.numpy() for v in u0], tol=1e-10, max_iter=2000)
+    assert ref.converged
+    u0g = torch.cat(u0).cuda()
+    r = P().hoscf_solve(T.cuda(), u0g, tol=1e-6, max_iter=2000, variant="asvd")
+    assert r.converged and r.passes == r.iters + 1
+    compare_solution(r, ref)
+    for k in range(1, min(4, ref.iters) + 1):
+        rk = P().hoscf_solve(T.cuda(), u0g, tol=0.0, max_iter=k, variant="asvd", eig_adapt=0.0)
+        sr = ref.history[k][0]
+        assert sr > 0 and abs(rk.sigma_raw - sr) <= 1e-5 * sr, (k, rk.sigma_raw, sr)
+
+
+def test_asvd_rejects_order_4():
+    pkg = P()
+    T = torch.randn(4, 5, 6, 3, device="cuda")
+    with pytest.raises(pkg.HoscfError) as e:
+        pkg.hoscf_solve(T, torch.cat(W.unit_gaussian_vectors(T.shape, 1)).cuda(), variant="asvd")
+    assert e.value.status == 7

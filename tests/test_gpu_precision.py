@@ -10,6 +10,7 @@ import torch
 
 import oracle
 import workloads as W
+from helpers import assert_same_solution
 
 pytestmark = pytest.mark.gpu
 EPS32 = 2.0 ** -24
@@ -88,6 +89,4 @@ def test_low_precision_solve_with_fp32_refinement(fmt):
     q, s = P().hoscf_quantize(Tg, fmt)
     r = P().hoscf_solve(q, torch.cat(u0).cuda(), scales=s, refine=Tg, tol=1e-6, switch_tol=1e-2)
     assert r.converged and r.passes_refine >= 1 and r.passes > r.passes_refine
-    assert abs(r.sigma - ref.sigma) <= 1e-5 * ref.sigma
-    for un, ur in zip(r.factors(), ref.u):
-        assert abs(1 - abs(float(un.double().cpu().numpy() @ ur))) <= 1e-5
+    assert_same_solution(r.sigma, r.factors(), ref.sigma, ref.u)

@@ -553,3 +553,149 @@ def test_planted_mistakes_are_caught(monkeypatch):
 
     s, uf = oracle.final_fix(-1.0, rand_unit(dims, 95))
     assert s > 0 and abs(uf[0][0]) > 0
+
+
+# ------------------------------------------------------------- eq. (4.1)
+@pytest.mark.parametrize("t", [0.0, 0.3, 1.1, np.pi / 2, 2.5])
+def test_residual_4_1_order2_closed_form(t):
+    """Eq. (4.1) worked by hand for d = 2, A = diag(3, 1), u = e1,
+    v = (cos t, sin t): x = [u; v]/sqrt(2), J = [[0, A], [A^T, 0]],
+    rho = x^T J x = 3 cos t, ||J x - rho x|| = sqrt(5) |sin t| and
+    ||J||_F = 2 sqrt(5), so the residual is
+    sqrt(5) |sin t| / (2 sqrt(5) + 3 |cos t|)."""
+    Hp = np.array([3.0, 0.0, 0.0, 1.0])
+    u = [np.array([1.0, 0.0]), np.array([np.cos(t), np.sin(t)])]
+    want = np.sqrt(5.0) * abs(np.sin(t)) / (2.0 * np.sqrt(5.0) + 3.0 * abs(np.cos(t)))
+    assert abs(oracle.residual_4_1(Hp, [2, 2], u) - want) <= 1e-15
+
+
+@pytest.mark.parametrize("dims", [(5, 6, 7), (4, 3, 5, 2), (3, 2, 4, 2, 3)])
+def test_residual_4_1_against_the_kkt_vectors(dims):
+    """For the balanced x = [u]/sqrt(d), (J x)_n = g_n / sqrt(d) with
+    g_n = A x_{k!=n} u^(k) and rho = A(u^(1), ..., u^(d)) (eq. 3.2-3.3), so
+    eq. (4.1) equals ||g - rho u|| / (sqrt(d) (||J||_F + |rho|)) with
+    ||J||_F^2 = 2 sum_{m<n} ||A_{m,n}||_F^2 / (d-1)^2.  g and rho come from
+    the direct contraction of the tensor (not from the blocks)."""
+    d = len(dims)
+    T = W.gaussian_tensor(dims, 71).numpy().astype(np.float64)
+    u = rand_unit(dims, 72)
+    g, rho = oracle.kkt_vectors(T, u)
+    Hp = oracle.blocks(T, u)
+    jf = np.sqrt(2.0 * sum(float(np.sum(B * B)) for B in oracle.unpack_blocks(Hp, list(dims)).values())) / (d - 1)
+    num = np.linalg.norm(np.concatenate(g) - rho * np.concatenate(u)) / np.sqrt(d)
+    want = num / (jf + abs(rho))
+    got = oracle.residual_4_1(Hp, list(dims), u)
+    assert abs(got - want) <= 1e-12 * want
+    # invariant under scaling of the tensor and under sign flips of factor pairs
+    assert abs(oracle.residual_4_1(oracle.blocks(7.0 * T, u), list(dims), u) - got) <= 1e-12 * got
+    uf = [-u[0]] + [-u[1]] + u[2:]
+    assert abs(oracle.residual_4_1(oracle.blocks(T, uf), list(dims), uf) - got) <= 1e-12 * got
+
+
+def test_residual_4_1_vanishes_at_a_singular_pair():
+    """At the factors of an exact rank-one tensor x is an eigenvector of
+    J(x) (Thm 2), so eq. (4.1) is zero to rounding."""
+    dims = (6, 5, 4, 3)
+    f = [v / np.linalg.norm(v) for v in rand_unit(dims, 73)]
+    T = 2.5 * W.outer([torch.from_numpy(v) for v in f]).numpy()
+    assert oracle.residual_4_1(oracle.blocks(T, f), list(dims), f) <= 1e-15
+    r = oracle.hoscf(T, rand_unit(dims, 74), tol=1e-13, max_iter=50)
+    assert r.resid_4_1 <= 1e-14
+
+
+# ------------------------------------------------------------- Alg. 1 line 5, ARPACK branch
+@pytest.mark.parametrize("lo,hi", [(-5.0, 4.0), (-4.0, 5.0), (-3.0, 3.0)])
+def test_largest_magnitude_arpack_branch_matches_eigh(lo, hi):
+    """The branch for large matrices (ARPACK on both spectrum ends) against a
+    matrix of known spectrum Q diag(w) Q^T: the largest-|w| end is chosen
+    and the eigenvector is the matching column of Q, sign-aligned with
+    x_prev.  On a tie (w = -3 and 3) the computed ends differ only by
+    rounding and either may win (both give the same rank-one term after
+    Alg. 1 lines 12-15); the vector must belong to the end chosen."""
+    n = 300
+    rng = np.random.default_rng(75)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    w = np.concatenate([[lo, hi], rng.uniform(-0.9 * min(-lo, hi), 0.9 * min(-lo, hi), n - 2)])
+    J = (Q * w) @ Q.T
+    J = 0.5 * (J + J.T)
+    x_prev = rng.standard_normal(n)
+    lam, x = oracle.largest_magnitude_eigpair(J, x_prev, dense_max=0)
+    k = 1 if hi > -lo else 0 if hi < -lo else (1 if lam > 0 else 0)
+    assert abs(lam - w[k]) <= 1e-10 * abs(w[k])
+    q = Q[:, k] if Q[:, k] @ x_prev >= 0 else -Q[:, k]
+    assert np.linalg.norm(x - q) <= 1e-8
+    if hi != -lo:
+        lam_d, x_d = oracle.largest_magnitude_eigpair(J, x_prev)
+        assert abs(lam - lam_d) <= 1e-10 * abs(lam_d) and np.linalg.norm(x - x_d) <= 1e-8
+
+
+# ------------------------------------------------------------- ASVD (Sec. 1)
+def test_asvd_order2_is_one_svd():
+    """d = 2: the intermediate matrix is A itself, so one sub-step gives the
+    top singular triplet and the next pass certifies it."""
+    A = W.gaussian_tensor((9, 6), 81).numpy()
+    U, S, Vt = np.linalg.svd(A.astype(np.float64))
+    r = oracle.asvd(A, rand_unit((9, 6), 82), tol=1e-12, max_iter=10)
+    assert r.converged and r.iters == 1 and r.passes == 2
+    assert abs(r.sigma - S[0]) <= 1e-12 * S[0]
+    assert abs(abs(r.u[0] @ U[:, 0]) - 1) <= 1e-12 and abs(abs(r.u[1] @ Vt[0]) - 1) <= 1e-12
+
+
+def test_asvd_noiseless_rank_one_in_two_sub_steps():
+    """T = s a1 o a2 o a3: the first block A x_1 u1 = s <a1,u1> a2 a3^T gives
+    (a2, a3) exactly; the second, A x_2 a2 = s a1 a3^T, gives a1: the third
+    pass certifies the exact solution."""
+    dims = (7, 5, 6)
+    f = [v / np.linalg.norm(v) for v in rand_unit(dims, 83)]
+    T = 2.0 * W.outer([torch.from_numpy(v) for v in f]).numpy()
+    r = oracle.asvd(T, rand_unit(dims, 84), tol=1e-13, max_iter=20)
+    assert r.converged and r.iters == 2 and r.passes == 3
+    assert abs(r.sigma - 2.0) <= 1e-13 * 2.0
+    for n in range(3):
+        assert abs(abs(r.u[n] @ f[n]) - 1) <= 1e-13
+
+
+@pytest.mark.parametrize("seed", [85, 86, 87])
+def test_asvd_is_monotone_and_reaches_the_hopm_point(seed):
+    """Each sub-step maximises |A(u1, u2, u3)| over the two free factors, so
+    |sigma| never decreases along the iterates (a wrong pair, block or
+    transpose breaks this); on a planted case ASVD, HOPM and HOSCF reach the
+    same maximum."""
+    dims = (8, 9, 7)
+    T, _ = W.planted_cp(dims, [4.0, 1.5], seed=seed, noise_abs=0.8)
+    T = T.numpy().astype(np.float64)
+    u0 = rand_unit(dims, seed + 10)
+    r = oracle.asvd(T, u0, tol=1e-12, max_iter=500)
+    assert r.converged
+    s = [abs(h[0]) for h in r.history]
+    assert all(b >= a - 1e-12 * b for a, b in zip(s, s[1:]))
+    s_hopm, _ = oracle.hopm(T, u0, tol=1e-12)
+    s_hoscf = oracle.hoscf(T, u0, tol=1e-12, max_iter=500).sigma
+    assert abs(r.sigma - s_hopm) <= 1e-10 * s_hopm
+    assert abs(r.sigma - s_hoscf) <= 1e-10 * s_hoscf
+
+
+def test_asvd_brute_force_2x2x2():
+    """On 2x2x2 tensors the best of several ASVD starts equals the maximum of
+    |T(u1,u2,u3)| over unit vectors (grid + local refinement)."""
+    from scipy.optimize import minimize
+    th = np.linspace(0, np.pi, 181, endpoint=False)
+    C = np.stack([np.cos(th), np.sin(th)], 1)
+    for seed in range(3):
+        T = W.gaussian_tensor((2, 2, 2), 60 + seed).numpy().astype(np.float64)
+        F = np.abs(np.einsum("abc,ia,jb,kc->ijk", T, C, C, C))
+        i, j, k = np.unravel_index(np.argmax(F), F.shape)
+
+        def f(t):
+            v = [np.array([np.cos(x), np.sin(x)]) for x in t]
+            return -abs(np.einsum("abc,a,b,c->", T, *v))
+        best = -minimize(f, [th[i], th[j], th[k]], method="Nelder-Mead",
+                         options=dict(xatol=1e-12, fatol=1e-14, maxiter=4000)).fun
+        sig = max(oracle.asvd(T, rand_unit((2, 2, 2), s), tol=1e-13, max_iter=500).sigma
+                  for s in range(8))
+        assert abs(sig - best) < 1e-9 * best
+
+
+def test_asvd_rejects_other_orders():
+    with pytest.raises(ValueError):
+        oracle.asvd(np.ones((2, 2, 2, 2)), rand_unit((2, 2, 2, 2), 1))
