@@ -220,6 +220,55 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
                          hoscf_info* info, void* stream);
 
 /*
+ * Sharded form (tensor split over ranks, one GPU each; no paper counterpart
+ * beyond its multi-node scaling runs of Sec. 6.2).  A rank holds the slab of
+ * rows [row0, row0 + rows) of mode 1, itself a dense row-major tensor of
+ * dims (rows, I_2, ..., I_d) because mode 1 is the slowest index.
+ *
+ * hoscf_ttvc_blocks_slab - this slab's contribution to every coupling block
+ * of the whole tensor (eq. 3.3), in the whole tensor's packed layout:
+ *   T     the slab (device data; F32, BF16 or F8E4M3 with its own scales).
+ *   row0  first mode-1 row of the slab; dim0 = I_1 of the whole tensor
+ *         (row0 >= 0, row0 + rows <= dim0).
+ *   u     device, n_tot = dim0 + I_2 + ... + I_d floats (whole factors).
+ *   H     device, P floats of the whole tensor (overwritten): A_{1,n} holds
+ *         the slab's rows at rows row0.. and zeros elsewhere; A_{m,n} with
+ *         m >= 2 holds the slab's partial sum over its mode-1 rows.
+ * The elementwise sum of H over all slabs of a partition of mode 1 is the
+ * whole tensor's blocks.  Asynchronous on `stream`.  Errors as for
+ * hoscf_ttvc_blocks, plus EINVAL for rows outside mode 1.
+ */
+hoscf_status hoscf_ttvc_blocks_slab(hoscf_handle* h, const hoscf_tensor_desc* T, int64_t row0,
+                                    int64_t dim0, const float* u, float* H, void* stream);
+
+/* The caller's collective: sum `count` floats at device pointer H over all
+ * ranks, in place, ordered on `stream` (e.g. an NCCL all-reduce); return 0 on
+ * success. */
+typedef int (*hoscf_reduce_fn)(float* H, int64_t count, void* stream, void* user);
+
+typedef struct {
+    int64_t row0;              /* first mode-1 row this rank's slab holds */
+    int64_t dim0;              /* I_1 of the whole tensor */
+    hoscf_reduce_fn reduce;    /* SUM over ranks, in place (required) */
+    void* user;                /* passed to reduce */
+} hoscf_shard;
+
+/*
+ * hoscf_solve_sharded - hoscf_solve on a tensor sharded by slabs of mode 1.
+ * Every rank calls it with its slab T, the same u0 (whole factors, n_tot
+ * floats) and the same opts; each pass is hoscf_ttvc_blocks_slab followed by
+ * shard->reduce on the whole blocks, and everything after the pass (the
+ * certificate, the eigen step, the final fix) runs on the whole blocks on
+ * every rank, so all ranks return the same u_out and sigma.  opts->refine,
+ * when set, is the FP32 slab of the same rows.  A reduce callback that
+ * returns nonzero ends the call with ECUDA.  Other statuses as hoscf_solve.
+ */
+hoscf_status hoscf_solve_sharded(hoscf_handle* h, const hoscf_tensor_desc* T,
+                                 const hoscf_shard* shard, const float* u0,
+                                 const hoscf_opts* opts, float* u_out, double* sigma_out,
+                                 hoscf_info* info, void* stream);
+
+/*
  * hoscf_solve_batched - `count` independent F32 tensors of orders 3..4 and
  * small dims, solved in one persistent launch (no paper counterpart; the
  * per-tensor algorithm is hoscf_solve's HOSCF variant).

@@ -10,5 +10,6 @@ from .api import (HoscfError, SolveResult, handle, hoscf_backward, hoscf_device_
                   hoscf_rqi_step, hoscf_selftest_timeout, hoscf_solve, hoscf_solve_batched,
                   hoscf_solve_greedy,
                   hoscf_ttvc_blocks, hoscf_ttvc_blocks_static, hoscf_workspace_size, n_blocks,
-                  n_tot)
+                  n_tot, hoscf_create_handle, hoscf_destroy_handle, shard_rows, allreduce_blocks,
+                  hoscf_ttvc_blocks_slab, hoscf_solve_sharded)
 from .autograd import HOSCFFunction, hoscf  # noqa: F401

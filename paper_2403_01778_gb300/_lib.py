@@ -26,7 +26,8 @@ EXPORTS = ("hoscf_create", "hoscf_destroy", "hoscf_last_error", "hoscf_opts_defa
            "hoscf_workspace_size", "hoscf_ttvc_blocks", "hoscf_eig_step", "hoscf_rqi_step", "hoscf_solve",
            "hoscf_solve_batched", "hoscf_backward", "hoscf_quantize",
            "hoscf_ttvc_blocks_static", "hoscf_profile_enable", "hoscf_profile_read",
-           "hoscf_selftest_timeout", "hoscf_solve_greedy", "hoscf_device_status")
+           "hoscf_selftest_timeout", "hoscf_solve_greedy", "hoscf_device_status",
+           "hoscf_ttvc_blocks_slab", "hoscf_solve_sharded")
 
 
 class TensorDesc(ctypes.Structure):
@@ -39,6 +40,14 @@ class Opts(ctypes.Structure):
                 ("eig_tol", c_double), ("eig_max_steps", c_int), ("eig_adapt", c_double),
                 ("refine", ctypes.POINTER(TensorDesc)), ("switch_tol", c_double),
                 ("timeout_ns", c_int64), ("batch_threads", c_int)]
+
+
+# int reduce(float* H, int64_t count, void* stream, void* user)
+REDUCE_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int64, c_void_p, c_void_p)
+
+
+class Shard(ctypes.Structure):
+    _fields_ = [("row0", c_int64), ("dim0", c_int64), ("reduce", REDUCE_FN), ("user", c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -86,6 +95,10 @@ def load():
                                    c_void_p]
     lib.hoscf_ttvc_blocks_static.argtypes = [P(TensorDesc), c_void_p, c_void_p, c_void_p, c_void_p]
     lib.hoscf_device_status.argtypes = [c_void_p, c_void_p]
+    lib.hoscf_ttvc_blocks_slab.argtypes = [c_void_p, P(TensorDesc), c_int64, c_int64, c_void_p,
+                                           c_void_p, c_void_p]
+    lib.hoscf_solve_sharded.argtypes = [c_void_p, P(TensorDesc), P(Shard), c_void_p, P(Opts),
+                                        c_void_p, P(c_double), P(Info), c_void_p]
     lib.hoscf_profile_enable.argtypes = [c_void_p, c_int]
     lib.hoscf_profile_read.argtypes = [c_void_p, P(c_int), P(c_double)]
     lib.hoscf_selftest_timeout.argtypes = [c_void_p, c_int, c_int64, c_void_p]

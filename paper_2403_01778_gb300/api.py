@@ -407,3 +407,117 @@ def hoscf_solve_batched(tensors, u0s, tol=1e-6, max_iter=200, eig_tol=None, time
                                          _stream_ptr(stream))
     _check(st, h, allow=(0, _lib.HOSCF_NOT_CONVERGED))
     return [float(s) for s in sig], uo, [infos[i] for i in range(cnt)], st
+
+
+# ------------------------------------------------------------------ sharded form
+def hoscf_create_handle(device: int = 0) -> ctypes.c_void_p:
+    """A library handle of one's own (a handle serves one host thread and one
+    stream at a time; the functions above share one handle per device).
+    Release it with hoscf_destroy_handle."""
+    h = ctypes.c_void_p()
+    st = _lib.load().hoscf_create(ctypes.byref(h), int(device))
+    if st != 0:
+        raise HoscfError(st, f"hoscf_create(device={device}) failed")
+    return h
+
+
+def hoscf_destroy_handle(h: ctypes.c_void_p) -> None:
+    _lib.load().hoscf_destroy(h)
+
+
+def shard_rows(dim0: int, rank: int, world: int) -> tuple[int, int]:
+    """(row0, rows): the contiguous slab of mode 1 that `rank` of `world`
+    holds; the first dim0 % world ranks hold one row more.  Every rank holds
+    at least one row."""
+    dim0, rank, world = int(dim0), int(rank), int(world)
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    if dim0 < world:
+        raise ValueError(f"mode 1 has {dim0} rows for {world} ranks (at least one row each)")
+    base, more = divmod(dim0, world)
+    return rank * base + min(rank, more), base + (1 if rank < more else 0)
+
+
+def allreduce_blocks(t: torch.Tensor, group=None) -> None:
+    """The sharded form's collective: SUM of the whole blocks over the ranks
+    of `group`, in place (torch.distributed; NCCL for CUDA tensors)."""
+    import torch.distributed as dist
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+
+
+class _DeviceView:
+    """__cuda_array_interface__ of `count` float32 at a library device
+    pointer, so torch can name the buffer without copying it."""
+
+    def __init__(self, ptr: int, count: int):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": "<f4",
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None, "stream": None}
+
+
+def hoscf_ttvc_blocks_slab(T: torch.Tensor, row0: int, dim0: int, u: torch.Tensor,
+                           H: torch.Tensor | None = None, scales=None, handle_=None,
+                           stream=None) -> torch.Tensor:
+    """This slab's contribution to the whole tensor's blocks (T = rows
+    [row0, row0 + T.shape[0]) of mode 1 of a tensor with dim0 rows)."""
+    d = _Desc(T, scales)
+    full = (int(dim0),) + d.shape[1:]
+    u = u.contiguous()
+    if u.dtype != torch.float32 or u.numel() != n_tot(full):
+        raise ValueError("u must be float32 with the whole tensor's sum(dims) entries")
+    if H is None:
+        H = torch.empty(n_blocks(full), device=T.device, dtype=torch.float32)
+    h = handle_ if handle_ is not None else handle(T.device.index)
+    _check(_lib.load().hoscf_ttvc_blocks_slab(h, ctypes.byref(d.desc), int(row0), int(dim0),
+                                              ctypes.c_void_p(u.data_ptr()),
+                                              ctypes.c_void_p(H.data_ptr()), _stream_ptr(stream)), h)
+    return H
+
+
+def hoscf_solve_sharded(T: torch.Tensor, row0: int, dim0: int, u0: torch.Tensor, reduce=None,
+                        group=None, tol=1e-6, max_iter=200, variant="hoscf", eig_tol=None,
+                        eig_max_steps=None, eig_adapt=None, scales=None,
+                        refine: torch.Tensor | None = None, switch_tol=None, timeout_ns=None,
+                        handle_=None, stream=None) -> SolveResult:
+    """HOSCF on a tensor sharded by slabs of mode 1: T is this rank's slab
+    (rows [row0, row0 + T.shape[0]) of dim0), u0 the whole initial guess.
+    `reduce(t)` sums the whole blocks t over the ranks in place; by default
+    allreduce_blocks over `group`.  Every rank gets the same result."""
+    d = _Desc(T, scales)
+    full = (int(dim0),) + d.shape[1:]
+    n = n_tot(full)
+    u0 = u0.contiguous()
+    if u0.dtype != torch.float32 or u0.numel() != n:
+        raise ValueError("u0 must be float32 with the whole tensor's sum(dims) entries")
+    rd = _Desc(refine) if refine is not None else None
+    o = _opts(tol, max_iter, variant, eig_tol, eig_max_steps,
+              rd.desc if rd is not None else None, switch_tol, timeout_ns, eig_adapt)
+    fn = reduce if reduce is not None else (lambda t: allreduce_blocks(t, group))
+    dev = T.device
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    errors = []
+
+    def _cb(hptr, count, stream_ptr, user):
+        try:
+            with torch.cuda.stream(s):
+                fn(torch.as_tensor(_DeviceView(hptr, count), device=dev))
+            return 0
+        except BaseException as exc:   # reported after the call returns
+            errors.append(exc)
+            return 1
+
+    cb = _lib.REDUCE_FN(_cb)
+    sh = _lib.Shard(int(row0), int(dim0), cb, None)
+    u_out = torch.empty(n, device=dev, dtype=torch.float32)
+    sigma = ctypes.c_double()
+    info = Info()
+    h = handle_ if handle_ is not None else handle(dev.index)
+    st = _lib.load().hoscf_solve_sharded(h, ctypes.byref(d.desc), ctypes.byref(sh),
+                                         ctypes.c_void_p(u0.data_ptr()), ctypes.byref(o),
+                                         ctypes.c_void_p(u_out.data_ptr()), ctypes.byref(sigma),
+                                         ctypes.byref(info), ctypes.c_void_p(s.cuda_stream))
+    if errors:
+        raise errors[0]
+    _check(st, h, allow=(0, _lib.HOSCF_NOT_CONVERGED))
+    return SolveResult(sigma.value, u_out, full, info.iters, info.passes, info.passes_refine,
+                       info.rqi_accepts, info.resid, info.resid_4_1, info.sigma_raw, st == 0)

@@ -471,9 +471,15 @@ hoscf_status hoscf_rqi_step(hoscf_handle* h, int order, const int64_t* dims, con
     return eig_launch(h, L, H, nullptr, u, x_out, u_out, rho_out, &o, 0, 0.0, s, 0.0, 1);
 }
 
-hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u0,
-                         const hoscf_opts* opts, float* u_out, double* sigma_out,
-                         hoscf_info* info, void* stream) {
+// HOSCF / iHOSCF / comparison variants (hoscf_solve), optionally with the
+// tensor sharded over ranks by slabs of mode 1 (hoscf_solve_sharded): then T
+// is this rank's slab, every pass is the slab pass scattered into the whole
+// tensor's block layout followed by the caller's SUM reduction over ranks,
+// and everything after the pass (certificate, eigen step, final fix) runs
+// on the whole blocks, identically on every rank.
+static hoscf_status solve_core(hoscf_handle* h, const hoscf_tensor_desc* T, const hoscf_shard* sh,
+                               const float* u0, const hoscf_opts* opts, float* u_out,
+                               double* sigma_out, hoscf_info* info, void* stream) {
     if (!h) return HOSCF_EINVAL;
     hoscf_status st = check_desc(h, T);
     if (st) return st;
@@ -497,6 +503,15 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
         for (int k = 0; k < T->order; ++k)
             if (Tr->dims[k] != T->dims[k]) return fail(h, HOSCF_EINVAL, "refine tensor shape differs");
     }
+    // the whole tensor's dims (a shard holds rows [row0, row0 + I_1') of mode 1)
+    int64_t fdims[HOSCF_MAX_ORDER];
+    for (int k = 0; k < T->order; ++k) fdims[k] = T->dims[k];
+    if (sh) {
+        if (sh->row0 < 0 || sh->dim0 < 1 || sh->row0 + T->dims[0] > sh->dim0)
+            return fail(h, HOSCF_EINVAL, "slab rows [%lld, %lld) outside mode 1 of size %lld",
+                        (long long)sh->row0, (long long)(sh->row0 + T->dims[0]), (long long)sh->dim0);
+        fdims[0] = sh->dim0;
+    }
     DeviceGuard g(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Layout L;
@@ -509,7 +524,7 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
     size_t extra = 0, off_pin = 0, off_pout = 0, off_lam = 0, off_peig = 0;
     if (asvd) {
         int64_t ntot = 0;
-        for (int k = 0; k < T->order; ++k) ntot += T->dims[k];
+        for (int k = 0; k < T->order; ++k) ntot += fdims[k];
         off_pin = 0;
         off_pout = align_up(sizeof(float) * (size_t)ntot, 256);
         off_lam = off_pout + align_up(sizeof(float) * (size_t)ntot, 256);
@@ -518,7 +533,7 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
         int b = 0;
         for (int m = 0; m < T->order; ++m)
             for (int n = m + 1; n < T->order; ++n, ++b) {
-                const int64_t dd[2] = {T->dims[m], T->dims[n]};
+                const int64_t dd[2] = {fdims[m], fdims[n]};
                 if (!make_shape(2, dd, Lpair[b].s) ||
                     !make_eig_plan(Lpair[b].s, h->nsm, 1, mmax, Lpair[b].ep))
                     return fail(h, HOSCF_EINVAL, "ASVD eigen plan failed");
@@ -526,13 +541,28 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
             }
         extra = off_peig + peig;
     }
+    // shard: the slab pass (its scratch, its packed blocks, its factors) in
+    // the extra region after the ASVD buffers
+    Shape Ss;
+    PassPlan pps, pps_lo;
+    size_t off_shard = 0, off_sh_H = 0, off_sh_u = 0;
+    if (sh) {
+        if (!make_shape(T->order, T->dims, Ss)) return fail(h, HOSCF_EINVAL, "invalid slab shape");
+        make_pass_plan(Ss, Tr ? HOSCF_F32 : T->dtype, h->nsm, true, pps);
+        pps_lo = pps;
+        if (Tr) make_pass_plan(Ss, T->dtype, h->nsm, true, pps_lo);
+        off_shard = align_up(extra, 256);
+        off_sh_H = align_up(std::max(pps.bytes, pps_lo.bytes), 256);
+        off_sh_u = off_sh_H + align_up(sizeof(float) * (size_t)Ss.P, 256);
+        extra = off_shard + off_sh_u + align_up(sizeof(float) * (size_t)Ss.n_tot, 256);
+    }
     // the pass region must fit both the low-precision and the FP32 pass
-    st = plan_all(h, T->order, T->dims, Tr ? HOSCF_F32 : T->dtype, true, true, mmax, L,
-                  Tr ? T->dtype : -1, extra);
+    st = plan_all(h, T->order, fdims, Tr ? HOSCF_F32 : T->dtype, sh == nullptr, true, mmax, L,
+                  Tr && !sh ? T->dtype : -1, extra);
     if (st) return st;
     for (Layout& lp : Lpair) lp.off_eig = L.off_extra + off_peig;
     PassPlan pp_lo = L.pp;
-    if (Tr) make_pass_plan(L.s, T->dtype, h->nsm, true, pp_lo);
+    if (Tr && !sh) make_pass_plan(L.s, T->dtype, h->nsm, true, pp_lo);
     const Shape& S = L.s;
     float* H = reinterpret_cast<float*>(h->ws + L.off_H);
     float* ua = reinterpret_cast<float*>(h->ws + L.off_ua);
@@ -566,10 +596,29 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
 
     auto do_pass = [&](const float* u, float* Hdst) -> hoscf_status {
         const hoscf_tensor_desc* TT = use_ref ? Tr : T;
-        const PassPlan& pp = use_ref ? L.pp : (Tr ? pp_lo : L.pp);
-        hoscf_status q = run_ttvc(S, pp, TT->dtype, TT->data, TT->scales, u, Hdst,
-                                  h->ws + L.off_pass, dev_err(h), tmo, s, err);
-        if (q) return fail(h, q, "%s", err.msg);
+        if (sh) {
+            // this rank's slab: its factor rows, its pass, the scatter into
+            // the whole layout, then the SUM over ranks (the caller's collective)
+            char* base = h->ws + L.off_extra + off_shard;
+            float* us = reinterpret_cast<float*>(base + off_sh_u);
+            float* Hs = reinterpret_cast<float*>(base + off_sh_H);
+            const int64_t rows = Ss.dims[0];
+            CK(cudaMemcpyAsync(us, u + sh->row0, sizeof(float) * rows, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(us + rows, u + S.moff[1], sizeof(float) * (S.n_tot - S.moff[1]),
+                               cudaMemcpyDeviceToDevice, s));
+            const PassPlan& pq = use_ref ? pps : (Tr ? pps_lo : pps);
+            hoscf_status q = run_ttvc(Ss, pq, TT->dtype, TT->data, TT->scales, us, Hs, base,
+                                      dev_err(h), tmo, s, err);
+            if (q) return fail(h, q, "%s", err.msg);
+            CK(launch_shard_scatter(S, Ss, sh->row0, Hs, Hdst, s));
+            if (sh->reduce(Hdst, S.P, stream, sh->user) != 0)
+                return fail(h, HOSCF_ECUDA, "the block reduction over ranks failed");
+        } else {
+            const PassPlan& pp = use_ref ? L.pp : (Tr ? pp_lo : L.pp);
+            hoscf_status q = run_ttvc(S, pp, TT->dtype, TT->data, TT->scales, u, Hdst,
+                                      h->ws + L.off_pass, dev_err(h), tmo, s, err);
+            if (q) return fail(h, q, "%s", err.msg);
+        }
         if (h->defl_count > 0) {
             // greedy rank-R: blocks of the deflated tensor at u
             cudaError_t e = launch_deflate(S, Hdst, u, h->defl_u,
@@ -763,6 +812,53 @@ hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const floa
     if (result == HOSCF_NOT_CONVERGED)
         fail(h, HOSCF_NOT_CONVERGED, "not converged after %d iterations (r = %.3e)", iters, resid);
     return result;
+}
+
+hoscf_status hoscf_solve(hoscf_handle* h, const hoscf_tensor_desc* T, const float* u0,
+                         const hoscf_opts* opts, float* u_out, double* sigma_out,
+                         hoscf_info* info, void* stream) {
+    return solve_core(h, T, nullptr, u0, opts, u_out, sigma_out, info, stream);
+}
+
+hoscf_status hoscf_solve_sharded(hoscf_handle* h, const hoscf_tensor_desc* T,
+                                 const hoscf_shard* shard, const float* u0,
+                                 const hoscf_opts* opts, float* u_out, double* sigma_out,
+                                 hoscf_info* info, void* stream) {
+    if (!h) return HOSCF_EINVAL;
+    if (!shard || !shard->reduce) return fail(h, HOSCF_EINVAL, "shard descriptor or reduce callback missing");
+    return solve_core(h, T, shard, u0, opts, u_out, sigma_out, info, stream);
+}
+
+hoscf_status hoscf_ttvc_blocks_slab(hoscf_handle* h, const hoscf_tensor_desc* T, int64_t row0,
+                                    int64_t dim0, const float* u, float* H, void* stream) {
+    if (!h) return HOSCF_EINVAL;
+    hoscf_status st = check_desc(h, T);
+    if (st) return st;
+    if (!u || !H) return fail(h, HOSCF_EINVAL, "u and H must be non-NULL device pointers");
+    if (row0 < 0 || dim0 < 1 || row0 + T->dims[0] > dim0)
+        return fail(h, HOSCF_EINVAL, "slab rows outside mode 1");
+    int64_t fdims[HOSCF_MAX_ORDER];
+    for (int k = 0; k < T->order; ++k) fdims[k] = T->dims[k];
+    fdims[0] = dim0;
+    Shape Sf;
+    if (!make_shape(T->order, fdims, Sf)) return fail(h, HOSCF_EINVAL, "invalid shape");
+    DeviceGuard g(h->device);
+    Layout L;   // the slab: pass scratch, its blocks (off_H) and its factors (off_ua)
+    st = plan_all(h, T->order, T->dims, T->dtype, true, false, 64, L);
+    if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float* us = reinterpret_cast<float*>(h->ws + L.off_ua);
+    float* Hs = reinterpret_cast<float*>(h->ws + L.off_H);
+    const int64_t rows = T->dims[0];
+    CK(cudaMemcpyAsync(us, u + row0, sizeof(float) * rows, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(us + rows, u + dim0, sizeof(float) * (Sf.n_tot - dim0),
+                       cudaMemcpyDeviceToDevice, s));
+    Err err;
+    st = run_ttvc(L.s, L.pp, T->dtype, T->data, T->scales, us, Hs, h->ws + L.off_pass, dev_err(h),
+                  2000000000ull, s, err);
+    if (st) return fail(h, st, "%s", err.msg);
+    CK(launch_shard_scatter(Sf, L.s, row0, Hs, H, s));
+    return HOSCF_OK;
 }
 
 hoscf_status hoscf_solve_batched(hoscf_handle* h, int count, const hoscf_tensor_desc* T,

@@ -556,8 +556,7 @@ hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* con
     a.P_max = P_max;
     a.F_max = F_max;
     a.AB_max = AB_max;
-    cudaError_t e = cudaFuncSetAttribute(batched_hoscf_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(batched_hoscf_kernel);
     int per_sm = 1;
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_hoscf_kernel, threads, smem);

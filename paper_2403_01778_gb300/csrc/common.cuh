@@ -26,6 +26,26 @@ enum DevErr : int {
     DEV_BADARG = 3
 };
 
+// ------------------------------------------------------------------ launch helpers
+// Opt a kernel into the device's largest dynamic shared memory per CTA; each
+// launch still passes its own size (which is what occupancy and the
+// cooperative-launch check use).  Setting the attribute to a per-launch size
+// instead would race between host threads launching the same kernel with
+// different sizes (one thread lowering it between another's set and launch).
+// (The opt-in limit counts the kernel's static shared memory as well.)
+template <typename Kernel>
+inline cudaError_t allow_max_dynamic_smem(Kernel kern) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

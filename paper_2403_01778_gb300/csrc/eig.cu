@@ -1076,8 +1076,7 @@ cudaError_t launch_lanczos(const Shape& s, const LanczosLaunch& l, cudaStream_t 
     a.proj_u = l.proj_u;
     if (l.scale_override != 0.f) a.scale = l.scale_override;
     const size_t sm = l.smem;
-    cudaError_t e = cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    cudaError_t e = allow_max_dynamic_smem(lanczos_kernel);
     if (e != cudaSuccess) return e;
     void* args[] = {&a};
     return cudaLaunchCooperativeKernel((const void*)lanczos_kernel, dim3(l.G), dim3(kEigThreads),

@@ -118,6 +118,10 @@ cudaError_t launch_mode_norms(const Shape& s, const float* u, double* out, cudaS
 cudaError_t launch_scale_modes(const Shape& s, const float* u, const double* nrm2, float* out,
                                cudaStream_t st);
 cudaError_t launch_final_fix(const Shape& s, float* u, double* sigma, cudaStream_t st);
+// shard.cu: scatter a slab's blocks (rows [row0, row0 + slab.dims[0]) of
+// mode 1) into the whole tensor's packed layout, zeros elsewhere.
+cudaError_t launch_shard_scatter(const Shape& full, const Shape& slab, int64_t row0,
+                                 const float* Hs, float* H, cudaStream_t st);
 // ASVD: sign rule for the top singular pair of block (m, n) and the next
 // iterate (the current one with modes m and n replaced).
 cudaError_t launch_asvd_pair_fix(const float* ucur, int64_t n_tot, int64_t om, int64_t im,

@@ -742,7 +742,7 @@ template <typename E, int BM, bool VEC>
 cudaError_t launch_small_k(const SmallPlanInfo& sp, const SmallArgs& a, cudaStream_t st,
                            const KernelEvents* kev) {
     auto k = a.onebar ? ttvc_small_kernel<E, BM, VEC, true> : ttvc_small_kernel<E, BM, VEC, false>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
+    cudaError_t e = allow_max_dynamic_smem(k);
     if (e != cudaSuccess) return e;
     if (kev) cudaEventRecord(kev->begin, st);
     k<<<sp.G, kSmallThreads, sp.smem, st>>>(a);

@@ -1114,8 +1114,7 @@ static cudaError_t launch_tiled_k(const PassPlan& p, const CUtensorMap& map, con
     const size_t smem = 1024 + tiled_smem(MODE == LOAD_SCALAR ? 0 : p.nstage, p.group, ROWS,
                                           (int)sizeof(E), std::is_same<E, fp8_t>::value)
                                    .total;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess) return e;
     if (kev) cudaEventRecord(kev->begin, st);
     kern<<<p.grid, 256, smem, st>>>(map, a);
