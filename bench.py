@@ -192,71 +192,132 @@ def traffic_bytes(dims, dtype):
 
 
 # ------------------------------------------------------------------ CPU baseline
-def cpu_baseline(workload, seconds, seed=0):
-    """FP64 oracle (as it stands) on a bounded slab of the workload: the first
-    S mode-1 slices of the same seeded tensor; one oracle HOSCF step on it
-    (blocks by definition + dense eigen step).  Returns GB/s of tensor bytes."""
+def oracle_step(T, u0, S, threads):
+    """One FP64 oracle HOSCF iteration (Algorithm 1 lines 4-5: the blocks by
+    their definition, eq. 3.3, and the dense largest-magnitude eigen step) on
+    the first S mode-1 slices of T.  Returns (seconds, pass seconds, bytes)."""
     import numpy as np
-    import torch
+    import oracle
+    sub = T if S >= T.shape[0] else np.ascontiguousarray(T[:S])
+    us = [u0[0][:S] / np.linalg.norm(u0[0][:S])] + u0[1:]
+    dims = [S] + list(T.shape[1:])
+    t0 = time.perf_counter()
+    Hp = oracle.blocks(sub, us, nthreads=threads)
+    t1 = time.perf_counter()
+    J = oracle.nepv_matrix(Hp, dims)
+    oracle.largest_magnitude_eigpair(J, np.concatenate(us) / math.sqrt(len(dims)))
+    t2 = time.perf_counter()
+    return t2 - t0, t1 - t0, sub.nbytes
+
+
+def oracle_slices(T, u0, threads, budget_s):
+    """Mode-1 slices whose oracle step fits `budget_s` seconds: the whole
+    tensor when it fits, else a slab sized from a measured slab step."""
+    full, _, _ = oracle_step(T, u0, T.shape[0], threads) if budget_s >= 2.0 else (float("inf"), 0, 0)
+    if full <= budget_s:
+        return T.shape[0], full
+    S = max(1, T.shape[0] // 16)
+    t, _, _ = oracle_step(T, u0, S, threads)
+    return max(1, min(T.shape[0], int(S * budget_s / max(t, 1e-9)))), None
+
+
+def cpu_baseline(workload, seconds, seed=0):
+    """The FP64 oracle (as it stands) on the host cores, on the same step as
+    the GPU leg: one HOSCF iteration over the whole workload tensor (all
+    cores), value = tensor bytes / step time.  Also: the oracle's pass alone,
+    the pass on one thread (a slab), and the per-pass and time-to-residual
+    figures of the paper's small workloads (the 64^3 configuration; 10
+    iterations on each Sec. 6.2 / Table 5 tensor, next to the paper's
+    single-core times)."""
+    import numpy as np
     import oracle
     import workloads as W
-    T = W.config_tensor(workload, seed=seed, device="cpu")
+    T = W.config_tensor(workload, seed=seed, device="cpu").numpy()
     dims = list(T.shape)
     u0 = [v.numpy() for v in W.unit_gaussian_vectors(dims, seed + 1)]
     cores = len(os.sched_getaffinity(0))
-    S = 4
-    elapsed = 0.0
-    while True:
-        sub = np.ascontiguousarray(T[:S].numpy())
-        us = [u0[0][:S] / np.linalg.norm(u0[0][:S])] + u0[1:]
-        t0 = time.perf_counter()
-        Hp = oracle.blocks(sub, us, nthreads=cores)
-        J = oracle.nepv_matrix(Hp, [S] + dims[1:])
-        oracle.largest_magnitude_eigpair(J, np.concatenate(us) / math.sqrt(len(dims)))
-        elapsed = time.perf_counter() - t0
-        if elapsed * 2 > seconds or S * 2 > dims[0]:
-            break
-        S *= 2
+    oracle.build()
+    oracle_step(T, u0, max(1, dims[0] // 64), cores)        # warm (threads, pages)
+    step_s, pass_s, nbytes = oracle_step(T, u0, dims[0], cores)
+    S1 = max(1, dims[0] // 16)
+    sub = np.ascontiguousarray(T[:S1])
+    t0 = time.perf_counter()
+    oracle.blocks(sub, [u0[0][:S1]] + u0[1:], nthreads=1)
+    one = time.perf_counter() - t0
     del T
-    nbytes = sub.nbytes
-    return {"value": nbytes / elapsed / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {S} of {dims[0]} mode-1 slices ({nbytes / 1e6:.0f} MB), one FP64 "
-                      f"HOSCF step (blocks by definition + dense eigh), {elapsed:.2f} s"}
+    small = {}
+    # the 64^3 configuration: time to its tolerance (1e-8 sigma-relative KKT)
+    T1 = W.config_tensor("cfg1_64cube", seed=0).numpy()
+    u1 = [v.numpy() for v in W.unit_gaussian_vectors(T1.shape, 1)]
+    for th in (1, cores):
+        t0 = time.perf_counter()
+        r = oracle.hoscf(T1, u1, tol=1e-8, max_iter=200, nthreads=th, keep_history=False)
+        small[f"cfg1_64cube_threads{th}"] = {"time_to_residual_s": time.perf_counter() - t0,
+                                             "iters": r.iters, "converged": r.converged,
+                                             "per_pass_s": None}
+        t0 = time.perf_counter()
+        oracle.blocks(T1, u1, nthreads=th)
+        small[f"cfg1_64cube_threads{th}"]["per_pass_s"] = time.perf_counter() - t0
+    # the scalability tensors of Sec. 6.2: 10 HOSCF iterations (Table 5 times
+    # 10 iterations of the paper's C++ code on one Xeon 8358P core)
+    table5 = {5: 7.18 + 0.021, 6: 10.07 + 0.011, 7: 12.30 + 0.008, 8: 15.82 + 0.006}
+    for dd in W.table_shapes():
+        Tt = W.gaussian_tensor(dd, 1).numpy()
+        ut = [v.numpy() for v in W.unit_gaussian_vectors(dd, 2)]
+        t0 = time.perf_counter()
+        oracle.hoscf(Tt, ut, tol=0.0, max_iter=10, nthreads=cores, keep_history=False)
+        ten = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.blocks(Tt, ut, nthreads=1)
+        p1 = time.perf_counter() - t0
+        small["x".join(map(str, dd))] = {"ten_iterations_s_all_cores": ten, "per_pass_s_one_thread": p1,
+                                         "paper_table5_ten_iterations_s_one_core": table5[len(dd)]}
+    return {"value": nbytes / step_s / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"the whole {'x'.join(map(str, dims))} tensor ({nbytes / 1e6:.0f} MB): one FP64 "
+                      f"HOSCF iteration (blocks by definition {pass_s:.2f} s + dense eigh "
+                      f"{step_s - pass_s:.2f} s)",
+            "pass_only_GBs": nbytes / pass_s / 1e9,
+            "one_thread_pass_GBs": sub.nbytes / one / 1e9,
+            "one_thread_sample": f"first {S1} of {dims[0]} mode-1 slices",
+            "small_workloads": small}
 
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
+    """The reference arm is the FP64 oracle (there is no other implementation
+    to install): each step is the same HOSCF iteration the GPU leg times, on
+    the host cores - over the whole tensor when the K + W steps fit a few
+    minutes, else over a stated slab of mode-1 slices."""
     if rank != 0:
         return 0
     import numpy as np
     import oracle
     import workloads as W
     oracle.build()
-    T = W.config_tensor(args.workload, seed=0, device="cpu")
+    T = W.config_tensor(args.workload, seed=0, device="cpu").numpy()
     dims = list(T.shape)
     u0 = [v.numpy() for v in W.unit_gaussian_vectors(dims, 1)]
     cores = len(os.sched_getaffinity(0))
-    # each step: one oracle HOSCF step on a bounded slab (sized for ~10 s)
-    S = max(1, min(dims[0], 8))
-    sub = np.ascontiguousarray(T[:S].numpy())
-    us = [u0[0][:S] / np.linalg.norm(u0[0][:S])] + u0[1:]
-    times = []
+    budget = min(10.0, 150.0 / max(1, args.steps + args.warmup))
+    S, _ = oracle_slices(T, u0, cores, budget)
+    times, nbytes = [], 0
     for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        Hp = oracle.blocks(sub, us, nthreads=cores)
-        J = oracle.nepv_matrix(Hp, [S] + dims[1:])
-        oracle.largest_magnitude_eigpair(J, np.concatenate(us) / math.sqrt(len(dims)))
+        t, _, nbytes = oracle_step(T, u0, S, cores)
         if k >= args.warmup:
-            times.append(time.perf_counter() - t0)
+            times.append(t)
     tot = sum(times)
-    v = sub.nbytes * len(times) / tot / 1e9
+    v = nbytes * len(times) / tot / 1e9
+    sample = (f"the whole tensor ({nbytes / 1e6:.0f} MB) per step" if S == dims[0] else
+              f"first {S} of {dims[0]} mode-1 slices ({nbytes / 1e6:.0f} MB) per step")
     line = {"impl": "reference", "metric": "TTVc pass HBM GB/s", "value": v, "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot / len(times) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "dims": dims, "sample_slices": S},
+            "config": {"workload": args.workload, "dims": dims, "sample_slices": S,
+                       "step": "one FP64 oracle HOSCF iteration: blocks by definition (eq. 3.3) "
+                               "+ dense largest-magnitude eigen step"},
             "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {S} of {dims[0]} mode-1 slices per step"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -273,13 +334,15 @@ def _timed(fn, reps=1):
     return (time.perf_counter() - t0) / reps, out
 
 
-def pass_rate(P, dims, device, seed=1):
-    """TTVc pass GB/s on a Gaussian tensor of these dims (L2 flushed)."""
+def pass_rate(P, dims, device, seed=1, T=None, scales=None):
+    """TTVc pass GB/s on a Gaussian tensor of these dims (or on T, in its
+    storage format), L2 flushed; best of 5."""
     import torch
     import workloads as W
-    T = W.gaussian_tensor(dims, seed, device=device)
+    if T is None:
+        T = W.gaussian_tensor(dims, seed, device=device)
     u = torch.cat(W.unit_gaussian_vectors(dims, seed + 1, device=device))
-    H = P.hoscf_ttvc_blocks(T, u)
+    H = P.hoscf_ttvc_blocks(T, u, scales=scales)
     flush = torch.empty(64 * 1024 * 1024, device=device)
     best = float("inf")
     for _ in range(5):
@@ -287,11 +350,12 @@ def pass_rate(P, dims, device, seed=1):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        P.hoscf_ttvc_blocks(T, u, H)
+        P.hoscf_ttvc_blocks(T, u, H, scales=scales)
         e1.record()
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
-    return {"ms": best, "GBs": pass_bytes(dims) / (best / 1e3) / 1e9}
+    nb = pass_bytes(dims, T.element_size()) + (scales.numel() * 4 if scales is not None else 0)
+    return {"ms": best, "GBs": nb / (best / 1e3) / 1e9}
 
 
 def run_extras(P, T, u0, dev):
@@ -303,7 +367,8 @@ def run_extras(P, T, u0, dev):
     import workloads as W
     ex = {}
     # headline workload: HOSCF vs iHOSCF to KKT residual 1e-6
-    for variant in ("hoscf", "ihoscf", "jacobi_hopm"):
+    for variant in ("hoscf", "ihoscf", "jacobi_hopm", "asvd"):
+        P.hoscf_solve(T, u0, tol=1e-6, max_iter=200, variant=variant)     # warm
         t, r = _timed(lambda: P.hoscf_solve(T, u0, tol=1e-6, max_iter=200, variant=variant))
         ex[f"time_to_residual_1e-6_{variant}"] = {
             "seconds": t, "iters": r.iters, "passes": r.passes, "resid": r.resid,
@@ -355,35 +420,53 @@ def run_extras(P, T, u0, dev):
                           "iters": [i[0] for i in gr.infos], "passes": [i[1] for i in gr.infos],
                           "converged": gr.converged,
                           "planted_weights": [2.0 ** -r for r in range(5)]}
-    # precision form: 200^4 planted rank one (sigma 100) + noise of norm 10
+    # precision form: 200^4 planted rank one (sigma 100) + noise of norm 10.
+    # Every result is stated against the FP64 oracle: its own solve on the
+    # FP32 tensor from the same start (sigma*, u*), and its KKT residual
+    # (eq. 2.4) at the returned factors; for the low-precision forms both at
+    # the point where the passes move to the FP32 tensor (before refinement)
+    # and at the end (after)
     T3 = W.config_tensor("cfg3_200p4", seed=0, device=dev)
-    u3 = torch.cat(W.unit_gaussian_vectors(T3.shape, 1, device=dev))
+    u3c = W.unit_gaussian_vectors(T3.shape, 1)
+    u3 = torch.cat(u3c).to(dev)
     prec = {}
     q16, _ = P.hoscf_quantize(T3, "bf16")
     q8, s8 = P.hoscf_quantize(T3, "fp8")
     cases = [("fp32", dict(T=T3)), ("bf16+fp32", dict(T=q16, refine=T3)),
              ("fp8+fp32", dict(T=q8, scales=s8, refine=T3))]
-    T3h = None
+    T3h = T3.cpu().numpy()
+    nth = len(os.sched_getaffinity(0))
+    ref3 = oracle.hoscf(T3h, [v.numpy() for v in u3c], tol=1e-10, max_iter=100, nthreads=nth,
+                        keep_history=False)
+
+    def vs_oracle(res):
+        uf = [v.double().cpu().numpy() for v in res.factors()]
+        g, full = oracle.kkt_vectors(T3h, uf, nthreads=nth)
+        return {"sigma": res.sigma, "sigma_rel_err": abs(res.sigma - ref3.sigma) / ref3.sigma,
+                "factor_err": max(abs(1.0 - float(a @ b)) for a, b in zip(uf, ref3.u)),
+                "oracle_kkt_resid": float(np.linalg.norm(np.concatenate(g) - full * np.concatenate(uf))
+                                          / abs(full))}
     for name, kw in cases:
         Tq = kw.pop("T")
         P.hoscf_solve(Tq, u3, tol=1e-6, max_iter=200, **kw)     # warm
-        t, r = _timed(lambda: P.hoscf_solve(Tq, u3, tol=1e-6, max_iter=200, **kw))
+        t, r = _timed(lambda: P.hoscf_solve(Tq, u3, tol=1e-6, max_iter=200, **kw), reps=3)
         rec = {"seconds": t, "iters": r.iters, "passes": r.passes,
                "passes_fp32": r.passes_refine if name != "fp32" else r.passes,
-               "sigma": r.sigma, "resid": r.resid, "converged": r.converged}
-        # FP64 oracle check of the returned point: KKT residual and sigma from
-        # the FP32 tensor itself
-        if T3h is None:
-            T3h = T3.cpu().numpy()
-        uf = [v.double().cpu().numpy() for v in r.factors()]
-        g, full = oracle.kkt_vectors(T3h, uf, nthreads=len(os.sched_getaffinity(0)))
-        rec["oracle_sigma"] = full
-        rec["oracle_kkt_resid"] = float(np.linalg.norm(np.concatenate(g) - full *
-                                                       np.concatenate(uf)) / abs(full))
+               "resid": r.resid, "converged": r.converged, "after": vs_oracle(r)}
+        if name != "fp32":
+            # the iterate at the switch: the same solve on the low-precision
+            # tensor alone, stopped after as many eigen steps as ran on it
+            lo_iters = r.passes - r.passes_refine - 1
+            lo_kw = {k: v for k, v in kw.items() if k != "refine"}
+            rb = P.hoscf_solve(Tq, u3, tol=1e-6, max_iter=max(0, lo_iters), **lo_kw)
+            rec["before"] = dict(vs_oracle(rb), iters=rb.iters, library_resid=rb.resid)
         prec[name] = rec
     for name in ("bf16+fp32", "fp8+fp32"):
         prec[name]["speedup_vs_fp32"] = prec["fp32"]["seconds"] / prec[name]["seconds"]
+    prec["oracle_solve"] = {"sigma": ref3.sigma, "iters": ref3.iters, "resid": ref3.resid}
     prec["pass_GBs_fp32"] = pass_rate(P, (200, 200, 200, 200), dev)["GBs"]
+    for name, q, sc in (("bf16", q16, None), ("fp8", q8, s8)):
+        prec[f"pass_{name}"] = pass_rate(P, (200, 200, 200, 200), dev, T=q, scales=sc)
     ex["precision_200p4"] = prec
     del T3, q16, q8, s8, T3h
     torch.cuda.empty_cache()
@@ -394,15 +477,26 @@ def run_extras(P, T, u0, dev):
     from paper_2403_01778_gb300 import autotune
     th, _ = autotune.best_threads(Tg, ug)
     P.hoscf_solve_batched(Tg, ug, tol=1e-6, batch_threads=th)
-    tb, (sig, _, infos, st) = _timed(lambda: P.hoscf_solve_batched(Tg, ug, tol=1e-6,
-                                                                    batch_threads=th))
+    reps = []
+    for _ in range(7):
+        tb, (sig, _, infos, st) = _timed(lambda: P.hoscf_solve_batched(Tg, ug, tol=1e-6,
+                                                                        batch_threads=th))
+        reps.append(tb)
+    tb = statistics.median(reps)
     k = 64
-    tp, _ = _timed(lambda: [P.hoscf_solve(Tg[i], ug[i], tol=1e-6) for i in range(0, len(Tg), len(Tg) // k)])
-    per_tensor = tp / len(range(0, len(Tg), len(Tg) // k))
-    ex["batched_1024"] = {"seconds": tb, "tensors_per_s": len(Tg) / tb, "threads": th,
-                          "all_converged": st == 0,
+    idx = list(range(0, len(Tg), len(Tg) // k))
+    for i in idx[:4]:
+        P.hoscf_solve(Tg[i], ug[i], tol=1e-6)                          # warm
+    preps = []
+    for _ in range(5):
+        tp, _ = _timed(lambda: [P.hoscf_solve(Tg[i], ug[i], tol=1e-6) for i in idx])
+        preps.append(tp / len(idx))
+    per_tensor = statistics.median(preps)
+    ex["batched_1024"] = {"seconds": tb, "seconds_reps": reps, "tensors_per_s": len(Tg) / tb,
+                          "threads": th, "all_converged": st == 0,
                           "max_resid": max(inf.resid for inf in infos),
-                          "per_tensor_launch_s": per_tensor,
+                          "per_tensor_launch_s": per_tensor, "per_tensor_reps": preps,
+                          "per_tensor_sample": f"{len(idx)} of {len(Tg)} tensors, median of 5",
                           "per_tensor_tensors_per_s": 1.0 / per_tensor,
                           "speedup": (len(Tg) / tb) * per_tensor}
     del Tg, ug, Ts
@@ -412,11 +506,27 @@ def run_extras(P, T, u0, dev):
         Tgd = W.config_tensor(name, seed=0, device=dev)
         ud = torch.cat(W.unit_gaussian_vectors(Tgd.shape, 1, device=dev))
         w = torch.randn(ud.numel(), generator=torch.Generator(device=dev).manual_seed(2), device=dev)
+        P.hoscf_solve(Tgd, ud, tol=1e-6)                                # warm
         tf, r = _timed(lambda: P.hoscf_solve(Tgd, ud, tol=1e-6))
-        P.hoscf_backward(Tgd, r.u, r.sigma, 1.0, w)
-        tbk, _ = _timed(lambda: P.hoscf_backward(Tgd, r.u, r.sigma, 1.0, w), reps=3)
-        grad[name] = {"dims": list(Tgd.shape), "forward_s": tf, "backward_s": tbk,
-                      "write_GBs": Tgd.numel() * 4 / tbk / 1e9, "iters": r.iters}
+        gT = P.hoscf_backward(Tgd, r.u, r.sigma, 1.0, w)
+        flush = torch.empty(64 * 1024 * 1024, device=dev)
+        bk, wr, adj = [], 0.0, 0.0
+        P.hoscf_profile_enable(dev.index, True)
+        for _ in range(5):
+            flush.zero_()                       # the write is timed with L2 flushed
+            tbk, _ = _timed(lambda: P.hoscf_backward(Tgd, r.u, r.sigma, 1.0, w, grad_T=gT))
+            bk.append(tbk)
+        P.hoscf_profile_enable(dev.index, False)
+        nw, wr = P.hoscf_profile_read(dev.index, P.PROFILE_GRAD_WRITE)
+        na, adj = P.hoscf_profile_read(dev.index, P.PROFILE_ADJOINT)
+        wr_ms, adj_ms = wr / max(1, nw), adj / max(1, na)
+        peak, _ = load_peaks()
+        wbytes = Tgd.numel() * 4 + 4 * sum(Tgd.shape)
+        grad[name] = {"dims": list(Tgd.shape), "forward_s": tf, "backward_s": statistics.median(bk),
+                      "grad_write_ms": wr_ms, "grad_write_GBs": wbytes / (wr_ms / 1e3) / 1e9,
+                      "grad_write_frac_of_hbm_peak": wbytes / (wr_ms / 1e3) / 1e9 / peak,
+                      "adjoint_solve_ms": adj_ms, "iters": r.iters}
+        del gT, flush
         del Tgd
     ex["differentiation"] = grad
     # the pass on the paper's other shapes (Table 5 scalability tensors etc.)

@@ -346,20 +346,24 @@ hoscf_status hoscf_solve_greedy(hoscf_handle* h, const hoscf_tensor_desc* T, int
 
 /*
  * hoscf_profile_enable / hoscf_profile_read - a measurement aid with no
- * counterpart in the paper: device time of the pass's streaming kernel alone
- * (the tiled, small-face or copy kernel, without the partial-sum reductions
- * that follow it), for roofline figures.
- *   enable   nonzero: from now on every hoscf_ttvc_blocks call on this handle
- *            records a CUDA event pair on its stream around that kernel
- *            (the first 65536 calls; earlier records are discarded);
+ * counterpart in the paper: device time of single kernels for roofline
+ * figures, recorded as CUDA event pairs on the launch stream.
+ *   enable   nonzero: from now on record (earlier records are discarded), for
+ *            at most 65536 calls of each kind: which = 0 the pass's streaming
+ *            kernel of every hoscf_ttvc_blocks call (the tiled, small-face
+ *            or copy kernel, without the partial-sum reductions that follow
+ *            it); which = 1 the gradient write of every hoscf_backward call
+ *            (its coefficient and write kernels); which = 2 its adjoint
+ *            solve (the pass at the solution and the Lanczos solve);
  *            zero: stop recording (records are kept for reading).
- *   count    host: number of recorded calls.
- *   total_ms host: sum of their kernel durations in milliseconds; the call
- *            waits for the recorded events to complete.
- * Errors: EINVAL (NULL handle or pointer), ECUDA.
+ *   which    0, 1 or 2 as above.
+ *   count    host: number of recorded calls of that kind.
+ *   total_ms host: sum of their durations in milliseconds; the call waits
+ *            for the recorded events to complete.
+ * Errors: EINVAL (NULL handle or pointer, `which` out of range), ECUDA.
  */
 hoscf_status hoscf_profile_enable(hoscf_handle* h, int enable);
-hoscf_status hoscf_profile_read(hoscf_handle* h, int* count, double* total_ms);
+hoscf_status hoscf_profile_read(hoscf_handle* h, int which, int* count, double* total_ms);
 
 /*
  * hoscf_selftest_timeout - exercises the library's failure path for device

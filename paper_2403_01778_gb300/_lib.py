@@ -100,7 +100,7 @@ def load():
     lib.hoscf_solve_sharded.argtypes = [c_void_p, P(TensorDesc), P(Shard), c_void_p, P(Opts),
                                         c_void_p, P(c_double), P(Info), c_void_p]
     lib.hoscf_profile_enable.argtypes = [c_void_p, c_int]
-    lib.hoscf_profile_read.argtypes = [c_void_p, P(c_int), P(c_double)]
+    lib.hoscf_profile_read.argtypes = [c_void_p, c_int, P(c_int), P(c_double)]
     lib.hoscf_selftest_timeout.argtypes = [c_void_p, c_int, c_int64, c_void_p]
     lib.hoscf_solve_greedy.argtypes = [c_void_p, P(TensorDesc), c_int, c_void_p, P(Opts),
                                        c_void_p, P(c_double), P(Info), P(c_double), c_void_p]

@@ -122,18 +122,22 @@ def hoscf_ttvc_blocks(T: torch.Tensor, u: torch.Tensor, H: torch.Tensor | None =
     return H
 
 
+PROFILE_PASS_KERNEL, PROFILE_GRAD_WRITE, PROFILE_ADJOINT = 0, 1, 2
+
+
 def hoscf_profile_enable(device: int = 0, enable: bool = True) -> None:
-    """Start (clearing earlier records) or stop timing the pass's streaming
-    kernel in every hoscf_ttvc_blocks call on this device's handle."""
+    """Start (clearing earlier records) or stop timing, on this device's
+    handle, the pass's streaming kernel of every hoscf_ttvc_blocks call and
+    the gradient write and adjoint solve of every hoscf_backward call."""
     h = handle(device)
     _check(_lib.load().hoscf_profile_enable(h, 1 if enable else 0), h)
 
 
-def hoscf_profile_read(device: int = 0) -> tuple[int, float]:
-    """(number of timed calls, total streaming-kernel milliseconds)."""
+def hoscf_profile_read(device: int = 0, which: int = PROFILE_PASS_KERNEL) -> tuple[int, float]:
+    """(number of timed calls, total milliseconds) of one recorded kind."""
     h = handle(device)
     n, ms = ctypes.c_int(0), ctypes.c_double(0.0)
-    _check(_lib.load().hoscf_profile_read(h, ctypes.byref(n), ctypes.byref(ms)), h)
+    _check(_lib.load().hoscf_profile_read(h, int(which), ctypes.byref(n), ctypes.byref(ms)), h)
     return n.value, ms.value
 
 

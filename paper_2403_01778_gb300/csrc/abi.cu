@@ -15,6 +15,8 @@
 
 using namespace hoscf;
 
+constexpr int kProfKinds = 3;      // measurement aid: pass kernel, gradient write, adjoint solve
+
 struct hoscf_handle {
     int device = 0;
     int nsm = 0;
@@ -28,11 +30,13 @@ struct hoscf_handle {
     // tensors every pass subtracts from the blocks (sigmas in the workspace head)
     const float* defl_u = nullptr;
     int defl_count = 0;
-    // measurement aid: events around the streaming kernel of each
-    // hoscf_ttvc_blocks call while enabled
+    // measurement aid: while enabled, events around (0) the streaming kernel
+    // of each hoscf_ttvc_blocks call, (1) the gradient write of each
+    // hoscf_backward call, (2) its adjoint solve (the pass at the solution
+    // and the Lanczos solve)
     bool prof_on = false;
-    size_t prof_n = 0;
-    std::vector<KernelEvents> prof;
+    size_t prof_n[kProfKinds] = {0, 0, 0};
+    std::vector<KernelEvents> prof[kProfKinds];
     BatchGraphCache graphs;       // batched solve: instantiated graphs of recent batches
     char msg[512] = {0};
 };
@@ -214,6 +218,22 @@ hoscf_status dev_status(hoscf_handle* h, int code) {
     return fail(h, HOSCF_ECUDA, "device error code %d", code);
 }
 
+// Measurement aid: the next event pair of list `which` while recording is
+// on (nullptr otherwise, or once kProfMax pairs are taken).
+hoscf_status prof_slot(hoscf_handle* h, int which, const KernelEvents** out) {
+    *out = nullptr;
+    if (!h->prof_on || h->prof_n[which] >= kProfMax) return HOSCF_OK;
+    std::vector<KernelEvents>& list = h->prof[which];
+    if (h->prof_n[which] == list.size()) {
+        KernelEvents e;
+        CK(cudaEventCreate(&e.begin));
+        CK(cudaEventCreate(&e.end));
+        list.push_back(e);
+    }
+    *out = &list[h->prof_n[which]++];
+    return HOSCF_OK;
+}
+
 // Eigen step launcher (shared by hoscf_eig_step and the solve driver).
 hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const double* x0,
                         const float* u0, double* x_out, float* u_out, double* lambda_out,
@@ -316,10 +336,11 @@ hoscf_status hoscf_destroy(hoscf_handle* h) {
         if (h->pinned_big) cudaFreeHost(h->pinned_big);
         h->graphs.release();
         if (h->own) cudaStreamDestroy(h->own);
-        for (KernelEvents& e : h->prof) {
-            cudaEventDestroy(e.begin);
-            cudaEventDestroy(e.end);
-        }
+        for (auto& list : h->prof)
+            for (KernelEvents& e : list) {
+                cudaEventDestroy(e.begin);
+                cudaEventDestroy(e.end);
+            }
     }
     delete h;
     return HOSCF_OK;
@@ -376,15 +397,8 @@ hoscf_status hoscf_ttvc_blocks(hoscf_handle* h, const hoscf_tensor_desc* T, cons
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Err err;
     const KernelEvents* kev = nullptr;
-    if (h->prof_on && h->prof_n < kProfMax) {
-        if (h->prof_n == h->prof.size()) {
-            KernelEvents e;
-            CK(cudaEventCreate(&e.begin));
-            CK(cudaEventCreate(&e.end));
-            h->prof.push_back(e);
-        }
-        kev = &h->prof[h->prof_n++];
-    }
+    st = prof_slot(h, 0, &kev);
+    if (st) return st;
     st = run_ttvc(L.s, L.pp, T->dtype, T->data, T->scales, u, H, h->ws + L.off_pass, dev_err(h),
                   2000000000ull, s, err, kev);
     if (st) return fail(h, st, "%s", err.msg);
@@ -409,21 +423,22 @@ hoscf_status hoscf_device_status(hoscf_handle* h, void* stream) {
 hoscf_status hoscf_profile_enable(hoscf_handle* h, int enable) {
     if (!h) return HOSCF_EINVAL;
     h->prof_on = enable != 0;
-    if (h->prof_on) h->prof_n = 0;
+    if (h->prof_on)
+        for (size_t& n : h->prof_n) n = 0;
     return HOSCF_OK;
 }
 
-hoscf_status hoscf_profile_read(hoscf_handle* h, int* count, double* total_ms) {
-    if (!h || !count || !total_ms) return HOSCF_EINVAL;
+hoscf_status hoscf_profile_read(hoscf_handle* h, int which, int* count, double* total_ms) {
+    if (!h || !count || !total_ms || which < 0 || which >= kProfKinds) return HOSCF_EINVAL;
     DeviceGuard g(h->device);
     double tot = 0.0;
-    for (size_t i = 0; i < h->prof_n; ++i) {
+    for (size_t i = 0; i < h->prof_n[which]; ++i) {
         float ms = 0.f;
-        CK(cudaEventSynchronize(h->prof[i].end));
-        CK(cudaEventElapsedTime(&ms, h->prof[i].begin, h->prof[i].end));
+        CK(cudaEventSynchronize(h->prof[which][i].end));
+        CK(cudaEventElapsedTime(&ms, h->prof[which][i].begin, h->prof[which][i].end));
         tot += ms;
     }
-    *count = (int)h->prof_n;
+    *count = (int)h->prof_n[which];
     *total_ms = tot;
     return HOSCF_OK;
 }
@@ -944,6 +959,10 @@ hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const f
         const double bnorm2 = h->h_pinned[0];
         if (!std::isfinite(bnorm2)) return fail(h, HOSCF_NONFINITE, "non-finite grad_u");
         if (bnorm2 > 0.0) {
+            const KernelEvents* kadj = nullptr;
+            st = prof_slot(h, 2, &kadj);
+            if (st) return st;
+            if (kadj) CK(cudaEventRecord(kadj->begin, s));
             st = run_ttvc(S, L.pp, HOSCF_F32, T->data, nullptr, u, H, h->ws + L.off_pass,
                           dev_err(h), 2000000000ull, s, err);
             if (st) return fail(h, st, "%s", err.msg);
@@ -953,6 +972,7 @@ hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const f
             st = eig_launch(h, L, H, b, nullptr, av, nullptr, nullptr, &o, 0, 0.0, s, 0.0, 2,
                             (float)(-sigma), u, 1.0f, 1e-6);
             if (st) return st;
+            if (kadj) CK(cudaEventRecord(kadj->end, s));
             CK(cudaMemcpyAsync(h->h_pinned, scal, sizeof(double) * SC_COUNT,
                                cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(h->h_pinned + 32, h->ws + kOffErr, sizeof(int),
@@ -972,7 +992,10 @@ hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const f
         }
     }
     float* coef = reinterpret_cast<float*>(h->ws + L.off_extra);
-    CK(launch_grad_write(S, u, aptr, grad_sigma, coef, grad_T, s));
+    const KernelEvents* kw = nullptr;
+    st = prof_slot(h, 1, &kw);
+    if (st) return st;
+    CK(launch_grad_write(S, u, aptr, grad_sigma, coef, grad_T, s, kw));
     CK(cudaStreamSynchronize(s));
     return result;
 }

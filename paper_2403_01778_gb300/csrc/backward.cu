@@ -123,7 +123,7 @@ cudaError_t launch_tangent_project(const Shape& s, const float* u, const float* 
 }
 
 cudaError_t launch_grad_write(const Shape& s, const float* u, const double* a, double c,
-                              float* coef, float* out, cudaStream_t st) {
+                              float* coef, float* out, cudaStream_t st, const KernelEvents* kev) {
     GradArgs g;
     memset(&g, 0, sizeof(g));
     g.d = s.d;
@@ -141,10 +141,12 @@ cudaError_t launch_grad_write(const Shape& s, const float* u, const double* a, d
     float* coef1 = coef;
     float* coef2 = coef + s.O;
     const int64_t cb = std::min<int64_t>(4096, (s.O + 255) / 256);
+    if (kev) cudaEventRecord(kev->begin, st);
     grad_coef_kernel<<<(unsigned)std::max<int64_t>(cb, 1), 256, 0, st>>>(u, a, g, coef1, coef2);
     g.OT = std::max<int64_t>(16, (s.O + 65534) / 65535);
     dim3 grid((unsigned)((g.F + 255) / 256), (unsigned)((s.O + g.OT - 1) / g.OT));
     grad_write_kernel<<<grid, 256, 0, st>>>(u, a, coef1, coef2, g, out);
+    if (kev) cudaEventRecord(kev->end, st);
     return cudaGetLastError();
 }
 

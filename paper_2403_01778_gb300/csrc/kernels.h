@@ -49,7 +49,8 @@ hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* con
 cudaError_t launch_tangent_project(const Shape& s, const float* u, const float* w, double* b,
                                    double* bnorm2, cudaStream_t st);
 cudaError_t launch_grad_write(const Shape& s, const float* u, const double* a, double c,
-                              float* coef, float* out, cudaStream_t st);
+                              float* coef, float* out, cudaStream_t st,
+                              const KernelEvents* kev = nullptr);
 
 // quant.cu
 cudaError_t launch_quantize(const float* x, int64_t n, int dtype, void* q, float* scales,

@@ -74,7 +74,7 @@ def test_null_and_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.hoscf_backward(None, None, None, 0.0, 0.0, None, None, None) == EINVAL
     assert lib.hoscf_profile_enable(None, 1) == EINVAL
     n, ms = ctypes.c_int(), ctypes.c_double()
-    assert lib.hoscf_profile_read(None, ctypes.byref(n), ctypes.byref(ms)) == EINVAL
+    assert lib.hoscf_profile_read(None, 0, ctypes.byref(n), ctypes.byref(ms)) == EINVAL
     assert lib.hoscf_ttvc_blocks_static(None, None, None, None, None) == EINVAL
     assert lib.hoscf_device_status(None, None) == EINVAL
     assert lib.hoscf_selftest_timeout(None, 0, 1000, None) == EINVAL
@@ -196,3 +196,20 @@ def test_binding_rejects_bad_tensors_before_any_device_call():
         P.hoscf_quantize(torch.zeros(8), "bf16")                            # host tensor
     with pytest.raises(ValueError):
         P.hoscf_ttvc_blocks(torch.zeros(dims), torch.zeros(15))             # host tensor
+
+
+def test_reference_arm_times_the_oracle_step_on_the_host(capsys):
+    """--impl reference: the FP64 oracle's HOSCF iteration (blocks by
+    definition + dense eigen step) on the host cores, over the whole tensor
+    when the steps fit their budget; one JSON line with the contract's keys."""
+    import json
+    import bench
+    args = argparse.Namespace(workload="cfg1_64cube", steps=2, warmup=1, gpus=1)
+    assert bench.run_reference(args, rank=0, world=1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "GB/s"
+    assert line["config"]["sample_slices"] == 64                 # the whole 64^3 tensor
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["steps"] == 2 and line["warmup"] == 1

@@ -96,3 +96,29 @@ def test_kernel_timing_aid_counts_each_pass():
     pkg.hoscf_profile_enable(0, True)       # re-enabling clears the records
     pkg.hoscf_profile_enable(0, False)
     assert pkg.hoscf_profile_read(0)[0] == 0
+
+
+def test_timing_aid_records_the_backward_write_and_adjoint_solve():
+    """Kinds 1 and 2 of the timing aid: one gradient-write record per
+    hoscf_backward call, one adjoint-solve record per call that solves
+    (grad_u given), each a positive duration within the call's wall time."""
+    pkg = P()
+    dims = (20, 24, 28)
+    T, _ = W.planted_cp(dims, [1.0], seed=11, noise_abs=0.05)
+    Tg = T.cuda()
+    r = pkg.hoscf_solve(Tg, torch.cat(W.unit_gaussian_vectors(dims, 12)).cuda(), tol=1e-6)
+    w = torch.randn(sum(dims), generator=torch.Generator().manual_seed(3)).cuda()
+    pkg.hoscf_profile_enable(0, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pkg.hoscf_backward(Tg, r.u, r.sigma, 1.0, w)
+    pkg.hoscf_backward(Tg, r.u, r.sigma, 1.0, None)      # d sigma / dT only: no solve
+    e1.record()
+    pkg.hoscf_profile_enable(0, False)
+    torch.cuda.synchronize()
+    nw, wms = pkg.hoscf_profile_read(0, pkg.PROFILE_GRAD_WRITE)
+    na, ams = pkg.hoscf_profile_read(0, pkg.PROFILE_ADJOINT)
+    assert (nw, na) == (2, 1)
+    assert 0.0 < wms and 0.0 < ams and wms + ams <= e0.elapsed_time(e1)
+    assert pkg.hoscf_profile_read(0, pkg.PROFILE_PASS_KERNEL)[0] == 0
