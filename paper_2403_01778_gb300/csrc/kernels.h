@@ -13,6 +13,27 @@ struct KernelEvents {
     cudaEvent_t begin = nullptr, end = nullptr;
 };
 
+// narrow.cu: the streaming kernel for BF16 / FP8 with full-row tiles
+struct NarrowArgs {
+    const void* T;
+    const float* scales;   // FP8 only: one per 128 flat elements
+    int64_t O, A, B;
+    int64_t items, W, P;   // (tile, outer index) items as the tiled kernel, one column tile
+    const float* w;        // O outer weights
+    const float* uA;       // factor of mode d-2 (length A)
+    const float* uB;       // factor of mode d-1 (length B)
+    float* hp;             // grid x 2 x FA x 256 face partials
+    float* y1p;            // O x A
+    float* y2p;            // TA x O x B
+    int* err;
+    uint64_t timeout_ns;
+    int nstage;            // ring slots per warp
+    int group;             // items per column-sum exchange
+    int FA;                // rows per tile (split over the 8 warps)
+};
+cudaError_t launch_narrow(const PassPlan& p, int dtype, const NarrowArgs& a, cudaStream_t st,
+                          const KernelEvents* kev);
+
 // ttvc.cu
 hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* data,
                       const float* scales, const float* u, float* H, char* ws, int* dev_err,

@@ -76,6 +76,8 @@ struct PassPlan {
     SmallPlanInfo sp;
     bool tma = false;
     bool vec = false;         // rows allow 4-element vector loads (B % 4 == 0)
+    bool narrow = false;      // full-row kernel for BF16 / FP8 (see NarrowSmem)
+    int slot_bytes = 0;       // narrow: bytes of one warp ring slot (rows + scales)
     int rows = 8;             // rows per consumer warp; FA = 8 * rows
     int FA = 64, FB = 128;
     int64_t TA = 1, TB = 1, TT = 1, items = 0, W = 0;
@@ -138,6 +140,60 @@ HOSCF_HD inline TiledSmem tiled_smem(int S, int G, int rows, int es, bool fp8) {
 }
 
 
+
+// Shared-memory layout of the narrow-format kernel (BF16 / FP8 with
+// 128 <= B <= 256, B % 8 == 0), from a 1024-byte aligned base: each of the 8
+// warps owns S ring slots, each holding its rows x B elements of one outer
+// index (one bulk copy, rounded out to 16-byte granules) and, for FP8, the
+// scale groups those rows span (a second bulk copy); one mbarrier per slot;
+// a rows x 36 float transpose per warp for its row sums; the per-warp u_A
+// entries; the double-buffered column-sum exchange [2][G][8][256] floats and
+// its item table.
+struct NarrowSmem {
+    size_t slot, data, bars, ysc, ua, y2, off, cnt, total;
+};
+
+// Rows per warp at most of the narrow kernel's two-CTAs-per-SM variant
+// (registers <= 128); the one-CTA variant takes 13 or 16.
+constexpr int kNarrowRowsOcc2 = 7;
+#ifndef HOSCF_NARROW_OCC
+#define HOSCF_NARROW_OCC 1   // CTAs per SM of the narrow kernel (1 or 2)
+#endif
+
+// A slot's data: 16 zero bytes (the pad lanes past the row end read), then
+// the rows copied from the 16-byte granule below the band's first element
+// (the copy is at most the band plus 30 bytes of rounding).
+HOSCF_HD inline size_t narrow_slot_data(int rows, int64_t B, int es) {
+    return ((size_t)(48 + rows * B * es) + 15) & ~(size_t)15;
+}
+
+HOSCF_HD inline size_t narrow_slot_bytes(int rows, int64_t B, int es, bool fp8) {
+    // scale groups a band of rows * B flat elements can touch, plus the
+    // 16-byte rounding of their copy on both ends
+    const size_t ng = fp8 ? (size_t)(rows * B) / 128 + 2 + 8 : 0;
+    return narrow_slot_data(rows, B, es) + (((ng * 4) + 15) & ~(size_t)15);
+}
+
+HOSCF_HD inline NarrowSmem narrow_smem(int S, int G, int rows, int64_t B, int es, bool fp8) {
+    NarrowSmem L;
+    L.slot = narrow_slot_bytes(rows, B, es, fp8);
+    L.data = narrow_slot_data(rows, B, es);
+    size_t o = (size_t)8 * S * L.slot;
+    L.bars = o;
+    o += (size_t)8 * S * 8;
+    L.ysc = o;
+    o += (size_t)8 * rows * kRowSumStride * 4;
+    L.ua = o;
+    o += (size_t)8 * 16 * 4;
+    L.y2 = o;
+    o += (size_t)2 * G * 8 * 256 * 4;
+    L.off = o;
+    o += (size_t)2 * G * 8;
+    L.cnt = o;
+    o += (size_t)2 * G * 4;
+    L.total = o;
+    return L;
+}
 
 // Eigen-step configuration (cooperative Lanczos over G CTAs).
 struct EigPlan {

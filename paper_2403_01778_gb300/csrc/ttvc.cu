@@ -88,9 +88,22 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
         p.bytes = off;
         return true;
     }
-    // CTAs per SM (see TiledOcc): 2 for the narrow formats, which then get
-    // half the shared memory and at most 13 rows per warp.
-    const int occ = es == 4 ? 1 : 2;
+    // Narrow formats with rows of 128 .. 256 elements, a multiple of 8: the
+    // full-row kernel (narrow.cu), 8 columns per lane, HOSCF_NARROW_OCC CTAs
+    // per SM (2: at most kNarrowRowsOcc2 rows per warp; 1: 13 or 16).
+    p.narrow = es < 4 && s.B % 8 == 0 && s.B >= 128 && s.B <= 256;
+    // CTAs per SM (see TiledOcc): 2 for the narrow formats in the tiled
+    // kernel, which then get half the shared memory and at most 13 rows per warp.
+    const int occ = es == 4 ? 1 : (p.narrow ? HOSCF_NARROW_OCC : 2);
+    if (p.narrow) {
+        // rows per warp at most, then the fewest tiles and their rows split
+        // evenly over the 8 warps (no idle warp for e.g. A = 200)
+        int rmax = kNarrowRowsOcc2;
+        if (occ == 1) rmax = (s.A + 103) / 104 <= (s.A + 127) / 128 ? 13 : 16;
+        const int64_t ta = (s.A + 8 * rmax - 1) / (8 * rmax);
+        p.rows = rmax;
+        p.FA = (int)((s.A + ta - 1) / ta);
+    } else
     // rows per warp: the candidate whose tiles waste the fewest rows of A,
     // the taller tile on ties (fewer column partials, per-item work spread
     // over more rows)
@@ -108,9 +121,9 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
             }
         }
         p.rows = best;
+        p.FA = 8 * p.rows;
     }
-    p.FA = 8 * p.rows;
-    p.FB = 128;
+    p.FB = p.narrow ? 256 : 128;
     p.TA = (s.A + p.FA - 1) / p.FA;
     p.TB = (s.B + p.FB - 1) / p.FB;
     p.TT = p.TA * p.TB;
@@ -173,7 +186,33 @@ bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p
         }
         if (G < 1) return false;
         p.group = G;
-        if (p.tma || p.vec) {
+        if (p.narrow) {
+            // ring depth first (up to 8 items in flight per warp), then the group
+            const size_t ncap = occ == 1 ? 227 * 1024 - 1024 : 113 * 1024 - 1024;
+            int Sn = 0, Gn = 0, bestn = -1;
+            for (int g = 8; g >= 1; g /= 2) {
+                int sg = 16;
+                while (sg >= 3 && narrow_smem(sg, g, p.rows, s.B, es, fp8).total > ncap) --sg;
+                if (sg < 3) continue;
+                const int score = std::min(sg, 8) * 100 + std::min(g, 4) * 10 + g;
+                if (score > bestn) {
+                    bestn = score;
+                    Sn = sg;
+                    Gn = g;
+                }
+            }
+            if (Gn < 1) {
+                p.narrow = false;   // cannot happen for B <= 256; keep the tiled kernel
+            } else {
+                p.group = Gn;
+                p.nstage = Sn;
+                p.slot_bytes = (int)narrow_slot_bytes(p.rows, s.B, es, fp8);
+                p.smem = 1024 + narrow_smem(Sn, Gn, p.rows, s.B, es, fp8).total;
+                p.tma = false;
+            }
+        }
+        if (p.narrow) {
+        } else if (p.tma || p.vec) {
             p.nstage = S;
             p.smem = 1024 + tiled_smem(S, G, p.rows, es, fp8).total;
         } else {
@@ -734,7 +773,8 @@ __device__ __forceinline__ float4 sum_strided4(const float* __restrict__ x, size
 
 __global__ void __launch_bounds__(256) reduce_pass_kernel(const ReduceArgs r) {
     const int col = threadIdx.x & 127;
-    const int64_t nuF = r.TT * r.FA;
+    const int CU = r.FB / 128;                       // 128-column units per tile row
+    const int64_t nuF = r.TT * r.FA * CU;
     // y1 / y2 units: 128 threads x 4 consecutive entries (16-byte loads, up
     // to eight partials in flight) when n % 4 == 0 and both arrays start
     // 16-byte aligned, else 128 x 1
@@ -747,16 +787,17 @@ __global__ void __launch_bounds__(256) reduce_pass_kernel(const ReduceArgs r) {
     // face units: 4 rows x 128 columns, 4 consecutive columns per thread
     // (16-byte loads) when the tile is 128 wide and rows and partials are
     // 16-byte aligned; else one row of 128 columns
-    const bool vF = r.FB == 128 && (r.B & 3) == 0 &&
+    const bool vF = (r.B & 3) == 0 &&
                     ((reinterpret_cast<uintptr_t>(r.hp) | reinterpret_cast<uintptr_t>(r.face)) & 15u) == 0;
     const int64_t FA4 = (r.FA + 3) / 4;
-    const int64_t nuFv = vF ? r.TT * FA4 : nuF;
+    const int64_t nuFv = vF ? r.TT * FA4 * CU : nuF;
     const int64_t total = nuFv + nu1 + nu2;
     for (int64_t u0 = blockIdx.x * 2 + (threadIdx.x >> 7); u0 < total; u0 += (int64_t)gridDim.x * 2) {
         if (vF && u0 < nuFv) {
-            const int64_t t = u0 / FA4;
-            const int rr = (int)(u0 - t * FA4) * 4 + (col >> 5);
-            const int cb = (col & 31) * 4;
+            const int64_t t = u0 / (FA4 * CU);
+            const int64_t rq = u0 - t * FA4 * CU;
+            const int rr = (int)(rq / CU) * 4 + (col >> 5);
+            const int cb = (int)(rq % CU) * 128 + (col & 31) * 4;
             const int64_t ta = t / r.TB, tb = t - (t / r.TB) * r.TB;
             const int64_t aa = ta * r.FA + rr, bb = tb * r.FB + cb;
             if (rr >= r.FA || aa >= r.A || bb >= r.B) continue;
@@ -773,14 +814,16 @@ __global__ void __launch_bounds__(256) reduce_pass_kernel(const ReduceArgs r) {
         }
         const int64_t u = vF ? u0 - nuFv + nuF : u0;   // index in the unvectorised numbering
         if (u < nuF) {
-            const int64_t t = u / r.FA;
-            const int rr = (int)(u - t * r.FA);
+            const int64_t t = u / ((int64_t)r.FA * CU);
+            const int64_t rq = u - t * r.FA * CU;
+            const int rr = (int)(rq / CU);
+            const int cc = (int)(rq % CU) * 128 + col;
             const int64_t ta = t / r.TB, tb = t - (t / r.TB) * r.TB;
-            const int64_t aa = ta * r.FA + rr, bb = tb * r.FB + col;
-            if (aa >= r.A || col >= r.FB || bb >= r.B) continue;
+            const int64_t aa = ta * r.FA + rr, bb = tb * r.FB + cc;
+            if (aa >= r.A || cc >= r.FB || bb >= r.B) continue;
             const int64_t c_lo = r.P > 0 ? t * r.P : (t * r.O) / r.W;
             const int64_t c_hi = r.P > 0 ? t * r.P + r.P - 1 : ((t + 1) * r.O - 1) / r.W;
-            const size_t inner = (size_t)rr * r.FB + col, tile = (size_t)r.FA * r.FB;
+            const size_t inner = (size_t)rr * r.FB + cc, tile = (size_t)r.FA * r.FB;
             const float first =
                 r.hp[((size_t)c_lo * 2 + (r.P == 0 && c_lo * r.W < t * r.O ? 1 : 0)) * tile + inner];
             r.face[aa * r.B + bb] =
@@ -1214,6 +1257,29 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
     a.group = p.group;
     a.P = p.P;
 
+    if (p.narrow) {
+        NarrowArgs na;
+        na.T = data;
+        na.scales = scales;
+        na.O = s.O;
+        na.A = s.A;
+        na.B = s.B;
+        na.items = p.items;
+        na.W = p.W;
+        na.P = p.P;
+        na.w = wptr;
+        na.uA = a.uA;
+        na.uB = a.uB;
+        na.hp = a.hp;
+        na.y1p = a.y1p;
+        na.y2p = a.y2p;
+        na.err = dev_err;
+        na.timeout_ns = timeout_ns;
+        na.nstage = p.nstage;
+        na.group = p.group;
+        na.FA = p.FA;
+        HOSCF_CK(launch_narrow(p, dtype, na, st, kev));
+    } else {
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
     bool use_tma = p.tma;
@@ -1249,6 +1315,7 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
     } else {
         HOSCF_CK(launch_tiled<fp8_t>(p, mode, map, a, st, kev));
     }
+    }
     // face block (d-2, d-1) and the row / column sums y1 (O x A), y2 (O x B):
     // for d == 3 these are H_{0,1} and H_{0,2} themselves
     float* y1 = s.d == 3 ? H + s.boff[block_index(3, 0, 1)] : reinterpret_cast<float*>(ws + p.off_y1);
@@ -1274,7 +1341,7 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         ra.y2 = y2;
         ra.n2 = s.O * s.B;
         ra.np2 = p.TA;
-        const int64_t units = p.TT * p.FA + (ra.n1 + 127) / 128 + (ra.n2 + 127) / 128;
+        const int64_t units = p.TT * p.FA * (p.FB / 128) + (ra.n1 + 127) / 128 + (ra.n2 + 127) / 128;
         const int64_t g = std::min<int64_t>((units + 1) / 2, 16 * (int64_t)std::max(1, p.nsm));
         reduce_pass_kernel<<<(unsigned)std::max<int64_t>(1, g), 256, 0, st>>>(ra);
         HOSCF_CK(cudaGetLastError());
