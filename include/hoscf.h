@@ -50,7 +50,8 @@ typedef enum {
 typedef enum {
     HOSCF_F32 = 0,             /* IEEE float32 */
     HOSCF_BF16 = 1,            /* bfloat16, no scale */
-    HOSCF_F8E4M3 = 2           /* FP8 e4m3 (fn), one float32 scale per 128 consecutive elements */
+    HOSCF_F8E4M3 = 2,          /* FP8 e4m3 (fn), one float32 scale per 128 consecutive elements */
+    HOSCF_F16 = 3              /* IEEE binary16, no scale */
 } hoscf_dtype;
 
 typedef enum {
@@ -309,8 +310,9 @@ hoscf_status hoscf_backward(hoscf_handle* h, const hoscf_tensor_desc* T, const f
 
 /*
  * hoscf_quantize - FP32 tensor to the precision-form storage (no paper
- * counterpart).  x: device, n floats.  dtype BF16: q receives n uint16
- * (round to nearest even).  dtype F8E4M3: q receives n bytes and scales
+ * counterpart).  x: device, n floats.  dtype BF16 or F16: q receives n
+ * uint16 (round to nearest even; F16 beyond 65504 becomes infinity as IEEE
+ * rounding prescribes).  dtype F8E4M3: q receives n bytes and scales
  * ceil(n/128) floats: scale = fp32(amax/448) per 128-element group (1 for an
  * all-zero group), code = saturating round-to-nearest-even e4m3 of
  * fp32(x/scale).  Asynchronous on `stream`.
@@ -395,7 +397,7 @@ hoscf_status hoscf_selftest_timeout(hoscf_handle* h, int kind, int64_t timeout_n
  * start-up - and so cannot create an hoscf_handle (a handle allocates its
  * workspace with cudaMalloc).
  *   T, u, H  as for hoscf_ttvc_blocks (the caller still owns and passes the
- *            inputs and the output); F32 and BF16 tensors.
+ *            inputs and the output); F32, BF16 and F16 tensors.
  *   status   device, 1 int, or NULL: written in stream order after the pass
  *            with 0 (H is valid) or HOSCF_TIMEOUT's device code (a bounded
  *            wait of the pass gave up; H is invalid).  With NULL such a

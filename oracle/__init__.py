@@ -38,7 +38,7 @@ What each function follows
                           is formed explicitly (the definition).
 ``adjoint``               not in the paper: the implicit-function adjoint of the
                           KKT system (2.4), checked against finite differences.
-``quantize_*``            not in the paper: BF16 (round to nearest even) and
+``quantize_*``            not in the paper: BF16 and IEEE FP16 (round to nearest even) and
                           FP8-e4m3 (per-128-element FP32 scales, saturating,
                           round to nearest even) storage, from the formats'
                           definitions.
@@ -616,6 +616,44 @@ def quantize_bf16(x) -> np.ndarray:
 def dequantize_bf16(q) -> np.ndarray:
     q = np.asarray(q, dtype=np.uint16).astype(np.uint32) << 16
     return q.view(np.float32).astype(np.float64)
+
+
+def f16_table() -> np.ndarray:
+    """Value of each of the 65536 IEEE binary16 patterns: 1 sign bit, 5
+    exponent bits (bias 15), 10 mantissa bits; exponent 0 = subnormal
+    (m / 1024) 2^-14, exponent 31 = infinity (m = 0) or NaN."""
+    code = np.arange(65536, dtype=np.int64)
+    s = np.where(code & 0x8000, -1.0, 1.0)
+    e = (code >> 10) & 0x1F
+    m = (code & 0x3FF).astype(np.float64)
+    val = np.where(e == 0, (m / 1024.0) * 2.0 ** -14, (1.0 + m / 1024.0) * 2.0 ** (e - 15.0))
+    val = np.where(e == 31, np.where(m == 0, np.inf, np.nan), val)
+    return s * val
+
+
+def quantize_f16(x) -> np.ndarray:
+    """FP32 -> IEEE binary16 bit patterns (uint16), round to nearest, ties to
+    even: the nearer of the two patterns around |x| in exact (FP64)
+    arithmetic, the even one (mantissa's last bit 0) on a tie.  Past the
+    largest finite value 65504 the next pattern is infinity, whose distance
+    is measured from 2^16 (the value the exponent range would give it), so
+    |x| >= 65520 rounds to infinity.  Inputs must be finite."""
+    x = np.asarray(x, dtype=np.float32).astype(np.float64)
+    if not np.all(np.isfinite(x)):
+        raise ValueError("quantize_f16 expects finite inputs")
+    pos = f16_table()[:0x7C01].copy()       # codes 0x0000 .. 0x7C00 (+inf), increasing
+    pos[0x7C00] = 2.0 ** 16
+    a = np.abs(x)
+    k = np.clip(np.searchsorted(pos, a, side="left"), 1, 0x7C00)   # pos[k-1] < a <= pos[k]
+    lo, hi = pos[k - 1], pos[k]
+    dlo, dhi = a - lo, hi - a
+    take_hi = (hi == a) | (dhi < dlo) | ((dhi == dlo) & ((k & 1) == 0))
+    code = np.where(a == 0, 0, np.where(take_hi, k, k - 1))
+    return (code | np.where(np.signbit(x), 0x8000, 0)).astype(np.uint16)
+
+
+def dequantize_f16(q) -> np.ndarray:
+    return f16_table()[np.asarray(q, dtype=np.uint16).astype(np.int64)]
 
 
 def e4m3_table() -> np.ndarray:

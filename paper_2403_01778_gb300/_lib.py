@@ -17,7 +17,7 @@ HOSCF_NOT_CONVERGED, HOSCF_NONFINITE, HOSCF_TIMEOUT, HOSCF_EUNSUPPORTED = 4, 5, 
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "NOT_CONVERGED",
                 5: "NONFINITE", 6: "TIMEOUT", 7: "EUNSUPPORTED"}
 
-HOSCF_F32, HOSCF_BF16, HOSCF_F8E4M3 = 0, 1, 2
+HOSCF_F32, HOSCF_BF16, HOSCF_F8E4M3, HOSCF_F16 = 0, 1, 2, 3
 VARIANTS = {"hoscf": 0, "ihoscf": 1, "ihoscf_prev": 2, "jacobi_hopm": 3, "asvd": 4}
 MAX_ORDER = 8
 

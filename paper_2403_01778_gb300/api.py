@@ -2,8 +2,8 @@
 
 Tensors are torch CUDA tensors (PyTorch supplies device memory and the
 current stream); every computation runs in libhoscf.so.  A tensor may be
-float32, bfloat16, or FP8-e4m3 (torch.float8_e4m3fn or uint8 codes, with a
-float32 ``scales`` tensor of one scale per 128 consecutive elements).
+float32, bfloat16, float16, or FP8-e4m3 (torch.float8_e4m3fn or uint8 codes,
+with a float32 ``scales`` tensor of one scale per 128 consecutive elements).
 """
 from __future__ import annotations
 
@@ -62,6 +62,8 @@ def _dtype_code(T: torch.Tensor):
         return _lib.HOSCF_F32
     if T.dtype == torch.bfloat16:
         return _lib.HOSCF_BF16
+    if T.dtype == torch.float16:
+        return _lib.HOSCF_F16
     if T.dtype in (torch.uint8, getattr(torch, "float8_e4m3fn", None)):
         return _lib.HOSCF_F8E4M3
     raise TypeError(f"unsupported tensor dtype {T.dtype}")
@@ -351,7 +353,8 @@ def hoscf_solve_greedy(T: torch.Tensor, R: int, u0: torch.Tensor, tol=1e-6, max_
 
 
 def hoscf_quantize(x: torch.Tensor, dtype: str, stream=None):
-    """FP32 -> ("bf16": bfloat16 tensor) or ("fp8": uint8 e4m3 codes, float32 scales)."""
+    """FP32 -> ("bf16": bfloat16 tensor), ("f16": float16 tensor) or ("fp8":
+    uint8 e4m3 codes, float32 scales)."""
     x = x.contiguous()
     if x.dtype != torch.float32 or not x.is_cuda:
         raise ValueError("x must be a float32 CUDA tensor")
@@ -360,6 +363,11 @@ def hoscf_quantize(x: torch.Tensor, dtype: str, stream=None):
     if dtype == "bf16":
         q = torch.empty(x.shape, device=x.device, dtype=torch.bfloat16)
         _check(_lib.load().hoscf_quantize(h, ctypes.c_void_p(x.data_ptr()), n, _lib.HOSCF_BF16,
+                                          ctypes.c_void_p(q.data_ptr()), None, _stream_ptr(stream)), h)
+        return q, None
+    if dtype == "f16":
+        q = torch.empty(x.shape, device=x.device, dtype=torch.float16)
+        _check(_lib.load().hoscf_quantize(h, ctypes.c_void_p(x.data_ptr()), n, _lib.HOSCF_F16,
                                           ctypes.c_void_p(q.data_ptr()), None, _stream_ptr(stream)), h)
         return q, None
     if dtype == "fp8":

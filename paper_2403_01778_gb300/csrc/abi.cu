@@ -140,7 +140,8 @@ hoscf_status check_desc(hoscf_handle* h, const hoscf_tensor_desc* T) {
     if (!T) return fail(h, HOSCF_EINVAL, "tensor descriptor is NULL");
     if (!dims_valid(T->order, T->dims)) return fail(h, HOSCF_EINVAL, "order must be 2..%d and dims >= 1", HOSCF_MAX_ORDER);
     if (!T->data) return fail(h, HOSCF_EINVAL, "tensor data is NULL");
-    if (T->dtype != HOSCF_F32 && T->dtype != HOSCF_BF16 && T->dtype != HOSCF_F8E4M3)
+    if (T->dtype != HOSCF_F32 && T->dtype != HOSCF_BF16 && T->dtype != HOSCF_F8E4M3 &&
+        T->dtype != HOSCF_F16)
         return fail(h, HOSCF_EINVAL, "unknown dtype %d", (int)T->dtype);
     if (T->dtype == HOSCF_F8E4M3 && !T->scales) return fail(h, HOSCF_EINVAL, "FP8 tensor needs scales");
     if ((reinterpret_cast<uintptr_t>(T->data) & 15) != 0)
@@ -1098,8 +1099,8 @@ hoscf_status hoscf_quantize(hoscf_handle* h, const float* x, int64_t n, int dtyp
                             float* scales, void* stream) {
     if (!h) return HOSCF_EINVAL;
     if (n < 0 || (n > 0 && (!x || !q))) return fail(h, HOSCF_EINVAL, "bad quantize arguments");
-    if (dtype != HOSCF_BF16 && dtype != HOSCF_F8E4M3)
-        return fail(h, HOSCF_EINVAL, "quantize dtype must be BF16 or F8E4M3");
+    if (dtype != HOSCF_BF16 && dtype != HOSCF_F8E4M3 && dtype != HOSCF_F16)
+        return fail(h, HOSCF_EINVAL, "quantize dtype must be BF16, F16 or F8E4M3");
     if (dtype == HOSCF_F8E4M3 && n > 0 && !scales) return fail(h, HOSCF_EINVAL, "FP8 needs scales");
     DeviceGuard g(h->device);
     CK(launch_quantize(x, n, dtype, q, scales, reinterpret_cast<cudaStream_t>(stream)));

@@ -257,6 +257,7 @@ struct ElemTraits<float> {
 };
 
 struct bf16_t { uint16_t bits; };
+struct f16_t { uint16_t bits; };
 struct fp8_t { uint8_t bits; };
 
 template <>

@@ -108,6 +108,10 @@ __device__ __forceinline__ float elem_value<bf16_t>(const bf16_t* p, const float
     return __uint_as_float(static_cast<uint32_t>(b) << 16);
 }
 template <>
+__device__ __forceinline__ float elem_value<f16_t>(const f16_t* p, const float*, int64_t i) {
+    return __half2float(__ushort_as_half(reinterpret_cast<const unsigned short*>(p)[i]));
+}
+template <>
 __device__ __forceinline__ float elem_value<fp8_t>(const fp8_t* p, const float* scales, int64_t i) {
     const uint8_t c = reinterpret_cast<const uint8_t*>(p)[i];
     const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)c, __NV_E4M3);
@@ -159,6 +163,8 @@ cudaError_t launch_sumsq(int dtype, const void* data, const float* scales, int64
         sumsq_kernel<float><<<nparts, 256, 0, st>>>((const float*)data, scales, n, part);
     else if (dtype == HOSCF_BF16)
         sumsq_kernel<bf16_t><<<nparts, 256, 0, st>>>((const bf16_t*)data, scales, n, part);
+    else if (dtype == HOSCF_F16)
+        sumsq_kernel<f16_t><<<nparts, 256, 0, st>>>((const f16_t*)data, scales, n, part);
     else
         sumsq_kernel<fp8_t><<<nparts, 256, 0, st>>>((const fp8_t*)data, scales, n, part);
     sum_parts_kernel<<<1, 32, 0, st>>>(part, nparts, out);

@@ -1,5 +1,5 @@
-// Streaming pass for the narrow storage formats (BF16, FP8-e4m3 with one FP32
-// scale per 128 consecutive elements) when the face row is 128 .. 256
+// Streaming pass for the narrow storage formats (BF16, FP16, FP8-e4m3 with
+// one FP32 scale per 128 consecutive elements) when the face row is 128 .. 256
 // elements long and a multiple of 8 (e.g. the 200^4 precision workload).
 // Same factorisation and outputs as the tiled kernel in ttvc.cu (eq. 3.3):
 //     face[a][b] += w_o T[o][a][b],  y1[o][a] = sum_b T u_B[b],  y2[o][b] = sum_a T u_A[a],
@@ -39,6 +39,13 @@ __device__ __forceinline__ void unpack8(const bf16_t* p, float2 (&x)[4]) {
     const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) x[j] = make_float2(__uint_as_float(w[j] << 16), __uint_as_float(w[j] & 0xffff0000u));
+}
+
+__device__ __forceinline__ void unpack8(const f16_t* p, float2 (&x)[4]) {
+    const uint4 q = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = __half22float2(*reinterpret_cast<const __half2*>(&w[j]));
 }
 
 __device__ __forceinline__ void unpack8(const fp8_t* p, float2 (&x)[4]) {
@@ -358,6 +365,7 @@ static cudaError_t launch_narrow_rows(const PassPlan& p, const NarrowArgs& a, cu
 cudaError_t launch_narrow(const PassPlan& p, int dtype, const NarrowArgs& a, cudaStream_t st,
                           const KernelEvents* kev) {
     if (dtype == HOSCF_BF16) return launch_narrow_rows<bf16_t>(p, a, st, kev);
+    if (dtype == HOSCF_F16) return launch_narrow_rows<f16_t>(p, a, st, kev);
     return launch_narrow_rows<fp8_t>(p, a, st, kev);
 }
 

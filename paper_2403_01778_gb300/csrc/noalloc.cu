@@ -60,7 +60,7 @@ extern "C" hoscf_status hoscf_ttvc_blocks_static(const hoscf_tensor_desc* T, con
     using namespace hoscf;
     if (!T || !u || !H || !T->data || !T->dims) return HOSCF_EINVAL;
     if (T->order < 2 || T->order > HOSCF_MAX_ORDER) return HOSCF_EINVAL;
-    if (T->dtype != HOSCF_F32 && T->dtype != HOSCF_BF16) return HOSCF_EINVAL;
+    if (T->dtype != HOSCF_F32 && T->dtype != HOSCF_BF16 && T->dtype != HOSCF_F16) return HOSCF_EINVAL;
     if ((reinterpret_cast<uintptr_t>(T->data) & 15) != 0) return HOSCF_EINVAL;
     Shape s;
     if (!make_shape(T->order, T->dims, s)) return HOSCF_EINVAL;

@@ -1,5 +1,6 @@
-// Precision-form storage (no paper counterpart): FP32 -> BF16 (round to
-// nearest even) and FP32 -> FP8-e4m3 with one FP32 scale per 128 consecutive
+// Precision-form storage (no paper counterpart): FP32 -> BF16 or IEEE FP16
+// (round to nearest even; FP16 overflows to infinity beyond 65504 as IEEE
+// rounding prescribes) and FP32 -> FP8-e4m3 with one FP32 scale per 128 consecutive
 // elements of the flat (row-major) order:
 //   scale = fp32(amax / 448)  (1 for an all-zero group)
 //   code  = e4m3(fp32(x / scale)), round to nearest even, saturating at 448.
@@ -8,6 +9,7 @@
 // codes are reproducible bit for bit.
 #include <algorithm>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include "common.cuh"
@@ -21,6 +23,12 @@ __global__ void quant_bf16_kernel(const float* __restrict__ x, int64_t n, uint16
         const __nv_bfloat16 b = __float2bfloat16_rn(x[i]);
         q[i] = *reinterpret_cast<const uint16_t*>(&b);
     }
+}
+
+__global__ void quant_f16_kernel(const float* __restrict__ x, int64_t n, uint16_t* __restrict__ q) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = __half_as_ushort(__float2half_rn(x[i]));
 }
 
 // One warp per 128-element group; lane l handles elements 4l..4l+3.
@@ -58,6 +66,9 @@ cudaError_t launch_quantize(const float* x, int64_t n, int dtype, void* q, float
     if (dtype == HOSCF_BF16) {
         const int64_t blocks = std::min<int64_t>((n + 255) / 256, 65535);
         quant_bf16_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, static_cast<uint16_t*>(q));
+    } else if (dtype == HOSCF_F16) {
+        const int64_t blocks = std::min<int64_t>((n + 255) / 256, 65535);
+        quant_f16_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, n, static_cast<uint16_t*>(q));
     } else {
         const int64_t groups = (n + 127) / 128;
         const int64_t blocks = std::min<int64_t>((groups * 32 + 255) / 256, 65535);

@@ -153,7 +153,9 @@ __global__ void small_reduce_kernel(const float* __restrict__ patch, const int* 
 static uint32_t small_magic(uint32_t d) {
     return d <= 1 ? 0u : (uint32_t)((1ull << 32) / d + 1);
 }
-static int small_es(int dtype) { return dtype == HOSCF_F32 ? 4 : (dtype == HOSCF_BF16 ? 2 : 1); }
+static int small_es(int dtype) {
+    return dtype == HOSCF_F32 ? 4 : (dtype == HOSCF_BF16 || dtype == HOSCF_F16) ? 2 : 1;
+}
 static uint32_t al16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
 
 // Patch rows for a range of L faces, offsets and the shared-memory layout.
@@ -370,6 +372,8 @@ cudaError_t run_small(const Shape& s, const SmallPlanInfo& sp, int dtype, const 
         e = launch_small_f32(sp, a, vec, st, kev);
     else if (dtype == HOSCF_BF16)
         e = launch_small_bf16(sp, a, vec, st, kev);
+    else if (dtype == HOSCF_F16)
+        e = launch_small_f16(sp, a, vec, st, kev);
     else
         e = launch_small_bm<fp8_t, false>(sp, a, st, kev);
     if (e != cudaSuccess) return e;

@@ -66,6 +66,10 @@ __device__ __forceinline__ float lds_elem<bf16_t>(const unsigned char* p) {
     return __uint_as_float(static_cast<uint32_t>(*reinterpret_cast<const uint16_t*>(p)) << 16);
 }
 template <>
+__device__ __forceinline__ float lds_elem<f16_t>(const unsigned char* p) {
+    return __half2float(__ushort_as_half(*reinterpret_cast<const unsigned short*>(p)));
+}
+template <>
 __device__ __forceinline__ float lds_elem<fp8_t>(const unsigned char* p) {
     const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)*p, __NV_E4M3);
     return __half2float(*reinterpret_cast<const __half*>(&h));
@@ -77,6 +81,11 @@ __device__ __forceinline__ float4 lds_row4(const unsigned char* row, int c, int 
     if constexpr (VEC) {
         if constexpr (sizeof(E) == 4) {
             return *reinterpret_cast<const float4*>(row + 16 * c);
+        } else if constexpr (std::is_same<E, f16_t>::value) {
+            const uint2 v = *reinterpret_cast<const uint2*>(row + 8 * c);
+            const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+            return make_float4(a.x, a.y, b.x, b.y);
         } else {
             const uint2 v = *reinterpret_cast<const uint2*>(row + 8 * c);
             return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
@@ -98,6 +107,8 @@ template <typename E>
 __device__ __forceinline__ float2 lds_pair(const unsigned char* p) {
     if constexpr (sizeof(E) == 4) {
         return *reinterpret_cast<const float2*>(p);
+    } else if constexpr (std::is_same<E, f16_t>::value) {
+        return __half22float2(*reinterpret_cast<const __half2*>(p));
     } else {
         const uint32_t v = *reinterpret_cast<const uint32_t*>(p);
         return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
@@ -780,5 +791,7 @@ cudaError_t launch_small_f32(const SmallPlanInfo& sp, const SmallArgs& a, bool v
                              const KernelEvents* kev);
 cudaError_t launch_small_bf16(const SmallPlanInfo& sp, const SmallArgs& a, bool vec, cudaStream_t st,
                               const KernelEvents* kev);
+cudaError_t launch_small_f16(const SmallPlanInfo& sp, const SmallArgs& a, bool vec, cudaStream_t st,
+                             const KernelEvents* kev);
 
 }  // namespace hoscf

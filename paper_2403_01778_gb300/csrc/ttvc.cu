@@ -68,7 +68,9 @@ bool make_shape(int d, const int64_t* dims, Shape& s) {
     return true;
 }
 
-static int elem_size(int dtype) { return dtype == HOSCF_F32 ? 4 : (dtype == HOSCF_BF16 ? 2 : 1); }
+static int elem_size(int dtype) {
+    return dtype == HOSCF_F32 ? 4 : (dtype == HOSCF_BF16 || dtype == HOSCF_F16) ? 2 : 1;
+}
 
 bool make_pass_plan(const Shape& s, int dtype, int nsm, bool tma_ok, PassPlan& p) {
     p = PassPlan();
@@ -322,14 +324,27 @@ __device__ __forceinline__ void unpack4(uint32_t q, float (&v)[4]) {   // 4 x fp
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+__device__ __forceinline__ void unpack4_f16(uint2 q, float (&v)[4]) {   // 4 x IEEE half
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 template <typename E> struct Pack4;
 template <> struct Pack4<float> { using T = float4; };
 template <> struct Pack4<bf16_t> { using T = uint2; };
+template <> struct Pack4<f16_t> { using T = uint2; };
 template <> struct Pack4<fp8_t> { using T = uint32_t; };
+
+// Four consecutive elements of type E (packed as Pack4<E>::T) -> float.
+template <typename E>
+__device__ __forceinline__ void unpack4e(typename Pack4<E>::T q, float (&v)[4]) { unpack4(q, v); }
+template <>
+__device__ __forceinline__ void unpack4e<f16_t>(uint2 q, float (&v)[4]) { unpack4_f16(q, v); }
 
 template <typename E>
 __device__ __forceinline__ void load4_smem(const E* row, int col, float (&v)[4]) {
-    unpack4(*reinterpret_cast<const typename Pack4<E>::T*>(row + col), v);
+    unpack4e<E>(*reinterpret_cast<const typename Pack4<E>::T*>(row + col), v);
 }
 
 template <typename E>
@@ -340,6 +355,11 @@ template <>
 __device__ __forceinline__ float load1_global<bf16_t>(const bf16_t* p) {
     const uint16_t b = __ldcs(reinterpret_cast<const unsigned short*>(p));
     return __uint_as_float(static_cast<uint32_t>(b) << 16);
+}
+template <>
+__device__ __forceinline__ float load1_global<f16_t>(const f16_t* p) {
+    const unsigned short b = __ldcs(reinterpret_cast<const unsigned short*>(p));
+    return __half2float(__ushort_as_half(b));
 }
 template <>
 __device__ __forceinline__ float load1_global<fp8_t>(const fp8_t* p) {
@@ -578,7 +598,7 @@ __global__ void __launch_bounds__(256, TiledOcc<E>::value)
         for (int r = 0; r < ROWS; ++r) {
             float v[4];
             if (RING) {
-                unpack4(*reinterpret_cast<const P4*>(ring + (size_t)cs * SLOT + r * FB + 4 * lane), v);
+                unpack4e<E>(*reinterpret_cast<const P4*>(ring + (size_t)cs * SLOT + r * FB + 4 * lane), v);
                 if (F8) {
                     const float* sp = sscl + ((size_t)cs * ROWS + r) * 2;
                     const float sc = ((g_lo + 4 * lane) & ~127) ? sp[1] : sp[0];
@@ -1110,6 +1130,13 @@ __global__ void bf16_to_f32_kernel(const uint16_t* __restrict__ src, float* __re
         dst[i] = __uint_as_float(static_cast<uint32_t>(src[i]) << 16);
 }
 
+__global__ void f16_to_f32_kernel(const uint16_t* __restrict__ src, float* __restrict__ dst,
+                                  int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __half2float(__ushort_as_half(src[i]));
+}
+
 // ---------------------------------------------------------------- host
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -1214,6 +1241,9 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         } else if (dtype == HOSCF_BF16) {
             bf16_to_f32_kernel<<<grid_for(s.N, 256, 4096), 256, 0, st>>>((const uint16_t*)data, H,
                                                                          s.N);
+        } else if (dtype == HOSCF_F16) {
+            f16_to_f32_kernel<<<grid_for(s.N, 256, 4096), 256, 0, st>>>((const uint16_t*)data, H,
+                                                                        s.N);
         } else {
             fp8_to_f32_kernel<<<grid_for(s.N, 256, 4096), 256, 0, st>>>((const uint8_t*)data,
                                                                         scales, H, s.N);
@@ -1298,6 +1328,7 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
                                                                : CU_TENSOR_MAP_L2_PROMOTION_NONE;
         CUtensorMapDataType dt = dtype == HOSCF_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : dtype == HOSCF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : dtype == HOSCF_F16  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                        : CU_TENSOR_MAP_DATA_TYPE_UINT8;
         if (!enc || (reinterpret_cast<uintptr_t>(data) & 15) != 0 ||
             enc(&map, dt, 3, const_cast<void*>(data), gdim, gstr, box, estr,
@@ -1312,6 +1343,8 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         HOSCF_CK(launch_tiled<float>(p, mode, map, a, st, kev));
     } else if (dtype == HOSCF_BF16) {
         HOSCF_CK(launch_tiled<bf16_t>(p, mode, map, a, st, kev));
+    } else if (dtype == HOSCF_F16) {
+        HOSCF_CK(launch_tiled<f16_t>(p, mode, map, a, st, kev));
     } else {
         HOSCF_CK(launch_tiled<fp8_t>(p, mode, map, a, st, kev));
     }

@@ -57,6 +57,9 @@ def oracle_slab(T32, dims, fmt, f):
     if fmt == "bf16":
         x = flat[torch.from_numpy(f.ravel()).cuda()].cpu().numpy()
         return oracle.dequantize_bf16(oracle.quantize_bf16(x)).reshape(f.shape)
+    if fmt == "f16":
+        x = flat[torch.from_numpy(f.ravel()).cuda()].cpu().numpy()
+        return oracle.dequantize_f16(oracle.quantize_f16(x)).reshape(f.shape)
     # fp8: quantise every 128-element group that holds a slab element
     grp = np.unique(f.ravel() // 128)
     idx = (grp[:, None] * 128 + np.arange(128)[None, :]).ravel()
@@ -70,6 +73,7 @@ def oracle_slab(T32, dims, fmt, f):
 @pytest.mark.parametrize("name,fmt,per_block", [("cfg2a_1024cube_rank5", "fp32", 6),
                                                 ("cfg3_200p4", "fp32", 3),
                                                 ("cfg3_200p4", "bf16", 2),
+                                                ("cfg3_200p4", "f16", 2),
                                                 ("cfg3_200p4", "fp8", 2)])
 def test_blocks_sampled_at_full_size(name, fmt, per_block):
     dims = tuple(W.CONFIGS[name]["dims"])

@@ -34,6 +34,16 @@ def test_quantize_bf16_bit_exact():
     assert np.array_equal(got, oracle.quantize_bf16(x).ravel())
 
 
+def test_quantize_f16_bit_exact():
+    """Including subnormal codes (tiny values) and overflow to infinity."""
+    x = W.gaussian_tensor((3, 1000, 37), 11).numpy() * 50
+    x.reshape(-1)[:1000] *= 1e-6
+    x.reshape(-1)[1000:1010] = [65504, 65519, 65520, -70000, 1e5, 2 ** -24, 2 ** -25, 0.0, -0.0, 1.0]
+    q, _ = P().hoscf_quantize(torch.from_numpy(x).cuda(), "f16")
+    got = q.view(torch.int16).cpu().numpy().view(np.uint16).ravel()
+    assert np.array_equal(got, oracle.quantize_f16(x).ravel())
+
+
 @pytest.mark.parametrize("n", [128 * 7, 1000, 129, 1])
 def test_quantize_e4m3_bit_exact(n):
     x = W.gaussian_tensor((n,), 2).numpy() * 3
@@ -55,9 +65,12 @@ def bound(Tq, u):
 
 
 @pytest.mark.parametrize("dims", [(5, 64, 200), (9, 48, 128), (7, 33, 100), (9, 10, 11, 12), (5, 6, 40, 36),
-                                  (4, 5, 6, 24, 20), (3, 200, 200)])
-@pytest.mark.parametrize("fmt", ["fp8", "bf16"])
+                                  (4, 5, 6, 24, 20), (3, 200, 200), (30, 20), (6, 40, 256), (4, 17, 136)])
+@pytest.mark.parametrize("fmt", ["fp8", "bf16", "f16"])
 def test_blocks_low_precision_match_dequantised_oracle(dims, fmt):
+    """Every load path of every storage format: the full-row kernel (rows of
+    128 .. 256, a multiple of 8), the tiled kernel (TMA, cp.async, plain
+    loads), the small-face kernel and the order-2 copy."""
     T = W.gaussian_tensor(dims, 3) * 7
     u = [v.numpy().astype(np.float64) for v in W.unit_gaussian_vectors(dims, 4)]
     if fmt == "fp8":
@@ -65,6 +78,11 @@ def test_blocks_low_precision_match_dequantised_oracle(dims, fmt):
         Tq = oracle.dequantize_e4m3_scaled(codes, scales).reshape(dims)
         Tg = torch.from_numpy(codes.reshape(dims)).cuda()
         sg = torch.from_numpy(scales).cuda()
+    elif fmt == "f16":
+        q = oracle.quantize_f16(T.numpy())
+        Tq = oracle.dequantize_f16(q).reshape(dims)
+        Tg = torch.from_numpy(q.view(np.int16)).cuda().view(torch.float16).reshape(dims)
+        sg = None
     else:
         q = oracle.quantize_bf16(T.numpy())
         Tq = oracle.dequantize_bf16(q).reshape(dims)
@@ -76,7 +94,7 @@ def test_blocks_low_precision_match_dequantised_oracle(dims, fmt):
     assert np.all(np.abs(Hg - Hr) <= bound(Tq, u))
 
 
-@pytest.mark.parametrize("fmt", ["fp8", "bf16"])
+@pytest.mark.parametrize("fmt", ["fp8", "bf16", "f16"])
 def test_low_precision_solve_with_fp32_refinement(fmt):
     """Planted rank one (sigma = 100) plus noise of norm 10, like the 200^4
     precision workload at 40^4: iterate on the low-precision copy, refine on

@@ -378,6 +378,25 @@ def test_bf16_rounding_definition():
     assert np.array_equal(oracle.quantize_bf16(x), ref)
 
 
+def test_f16_rounding_definition():
+    """IEEE binary16 round-to-nearest-even worked by hand (ties at 1 + 2^-11
+    and 1 + 3 * 2^-11, the largest finite 65504, the overflow threshold
+    65520, the smallest subnormal 2^-24 and the tie below it), then against
+    numpy's and torch's own FP32 -> FP16 conversions on Gaussian values over
+    many magnitudes."""
+    vals = np.array([1.0, 1 + 2 ** -11, 1 + 3 * 2 ** -11, -(1 + 2 ** -11), 65504.0, 65519.0, 65520.0,
+                     2.0 ** -24, 2.0 ** -25, 1.5 * 2.0 ** -25, 0.0, -0.0], dtype=np.float32)
+    q = oracle.quantize_f16(vals)
+    assert [hex(v) for v in q] == ["0x3c00", "0x3c00", "0x3c02", "0xbc00", "0x7bff", "0x7bff", "0x7c00",
+                                   "0x1", "0x0", "0x1", "0x0", "0x8000"]
+    assert oracle.dequantize_f16(q[7:8])[0] == 2.0 ** -24 and np.isinf(oracle.dequantize_f16(q[6:7])[0])
+    rng = np.random.default_rng(82)
+    x = (rng.standard_normal(8192) * 10.0 ** rng.integers(-8, 5, 8192)).astype(np.float32)
+    assert np.array_equal(oracle.quantize_f16(x), x.astype(np.float16).view(np.uint16))
+    ref = torch.from_numpy(x).to(torch.float16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(oracle.quantize_f16(x), ref)
+
+
 def test_e4m3_definition():
     tab = oracle.e4m3_table()
     assert tab[0x7E] == 448.0 and tab[0x38] == 1.0 and tab[0x08] == 2.0 ** -6
