@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             } else if (k >= 2) {
                 // FP32 pair to decide; the FP64 refinement only once accepted
                 if (warp == 0) {
-                    RitzOut t = ritz_extreme_fp32(alpha, beta, k, beta_last, rscratch);
+                    RitzOut t = ritz_extreme_fp32(alpha, beta, k, beta_last, rscratch, a.eig_tol, last);
                     const bool acc = t.resid <= a.eig_tol * fabs(t.theta) || last;
                     if (acc) t = ritz_refine_fp64(alpha, beta, k, beta_last, sv, rscratch);
                     if (lane == 0) {

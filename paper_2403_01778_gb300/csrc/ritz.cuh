@@ -189,6 +189,35 @@ struct RitzOut {
     double resid;   // |beta_k * s_k| / ||s||
 };
 
+// |s_k| of the unit eigenvector of the k x k tridiagonal T for its extreme
+// eigenvalue near th, without the vector: with p_j the leading principal
+// minors of T - th I, s_k^2 = -p_{k-1}(th) / p_k'(th), from the pivots
+// q_j = p_j / p_{j-1} and the ratios r_j = p_j' / p_j of one pass,
+//   q_j = (a_j - th) - b_{j-1}^2 / q_{j-1},
+//   p_j' / p_{j-1} = -1 + (a_j - th) r_{j-1} - b_{j-1}^2 r_{j-2} / q_{j-1},
+//   r_j = (p_j' / p_{j-1}) / q_j.
+// At an extreme eigenvalue every pivot q_j (j < k) has one sign and stays
+// away from zero (the eigenvalues of T_j lie strictly inside by interlacing),
+// so the pass is stable; it is accurate as long as th resolves the distance
+// from the eigenvalue to the nearest eigenvalue of T_{k-1}, i.e. while the
+// Ritz vector is far from converged.  One thread (FP32).
+static __device__ float ritz_last_component(const float* al, const float* be2, int k, float th) {
+    float q = al[0] - th;
+    float r1 = -1.f / q, r2 = 0.f;   // r_1, r_0
+    float num = -1.f;                // p_1' / p_0
+    for (int j = 1; j < k; ++j) {
+        const float aj = al[j] - th;
+        num = -1.f + aj * r1 - be2[j - 1] * __fdividef(r2, q);
+        if (j + 1 < k) {
+            const float qn = aj - __fdividef(be2[j - 1], q);
+            r2 = r1;
+            r1 = __fdividef(num, qn);
+            q = qn;
+        }
+    }
+    return sqrtf(1.f / fabsf(num));
+}
+
 // Largest-magnitude Ritz pair of T_k (alpha, beta in FP64, k >= 1), FP32
 // part: the extreme eigenvalue (multisection on both ends, ties to the
 // positive end) and its eigenvector by inverse iteration, left (unit max
@@ -198,8 +227,14 @@ struct RitzOut {
 // off the inverse-iteration vector.  Enough to decide convergence; the FP64
 // refined pair comes from ritz_refine_fp64 on the same scratch.  Called by
 // one full warp.
+// When the eigenvector is not needed (need_vec false) and the estimate of
+// ritz_last_component at both ends of the eigenvalue's FP32 bracket agrees
+// (within a factor 2) on a residual above 4 * tol_rel * |theta| - a pair
+// that is clearly not converged - the inverse iteration is skipped and that
+// estimate returned (the caller only learns "not converged").
 static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* beta, int k,
-                                            double beta_k, float* scratch) {
+                                            double beta_k, float* scratch, double tol_rel = 0.0,
+                                            bool need_vec = true) {
     const int lane = threadIdx.x & 31;
     float* al = scratch;
     float* be = al + kMaxLanczos;
@@ -237,14 +272,32 @@ static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* b
     const float tmin = __shfl_sync(HOSCF_FULLMASK, ext, 16);
     // ties between +l and -l go to the positive end
     const float theta32 = (tmax >= -tmin) ? tmax : tmin;
+    __shared__ float s_est;
     if (lane == 0) {
-        if (k == 1) {
-            sv[0] = 1.f;
-        } else {
-            tridiag_inverse_iteration(al, be, k, theta32, bound, sv, wa, wb, wc, wd, piv);
+        s_est = -1.f;
+        if (!need_vec && k >= 2) {
+            const float h = 4.8e-7f * fabsf(theta32) + 1e-30f;
+            const float e0 = ritz_last_component(al, be2, k, theta32 - h);
+            const float e1 = ritz_last_component(al, be2, k, theta32 + h);
+            const float lim = (float)(4.0 * tol_rel) * fabsf(theta32) / (float)fabs(beta_k);
+            if (isfinite(e0) && isfinite(e1) && fminf(e0, e1) > lim && fmaxf(e0, e1) <= 2.f * fminf(e0, e1))
+                s_est = fminf(e0, e1);
+        }
+        if (s_est < 0.f) {
+            if (k == 1) {
+                sv[0] = 1.f;
+            } else {
+                tridiag_inverse_iteration(al, be, k, theta32, bound, sv, wa, wb, wc, wd, piv);
+            }
         }
     }
     __syncwarp();
+    if (s_est >= 0.f) {
+        RitzOut ro;
+        ro.theta = theta32;
+        ro.resid = fabs(beta_k) * (double)s_est;
+        return ro;
+    }
     float ss = 0.f;
     for (int i = lane; i < k; i += 32) ss = fmaf(sv[i], sv[i], ss);
     ss = warp_sum(ss);
