@@ -198,9 +198,9 @@ struct RitzOut {
 //   r_j = (p_j' / p_{j-1}) / q_j.
 // At an extreme eigenvalue every pivot q_j (j < k) has one sign and stays
 // away from zero (the eigenvalues of T_j lie strictly inside by interlacing),
-// so the pass is stable; it is accurate as long as th resolves the distance
-// from the eigenvalue to the nearest eigenvalue of T_{k-1}, i.e. while the
-// Ritz vector is far from converged.  One thread (FP32).
+// so the pass is stable; in FP32 it is accurate while |s_k| >= ~3e-3 and
+// flattens out near sqrt(eps32) below that (measured on Lanczos
+// tridiagonals), so only values well above that floor are used.  One thread.
 static __device__ float ritz_last_component(const float* al, const float* be2, int k, float th) {
     float q = al[0] - th;
     float r1 = -1.f / q, r2 = 0.f;   // r_1, r_0
@@ -229,9 +229,10 @@ static __device__ float ritz_last_component(const float* al, const float* be2, i
 // one full warp.
 // When the eigenvector is not needed (need_vec false) and the estimate of
 // ritz_last_component at both ends of the eigenvalue's FP32 bracket agrees
-// (within a factor 2) on a residual above 4 * tol_rel * |theta| - a pair
-// that is clearly not converged - the inverse iteration is skipped and that
-// estimate returned (the caller only learns "not converged").
+// (within a factor 2) on |s_k| >= 1e-2 and a residual above 4 * tol_rel *
+// |theta| - a pair that is clearly not converged - the inverse iteration is
+// skipped and that estimate returned (the caller only learns "not
+// converged").
 static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* beta, int k,
                                             double beta_k, float* scratch, double tol_rel = 0.0,
                                             bool need_vec = true) {
@@ -280,7 +281,8 @@ static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* b
             const float e0 = ritz_last_component(al, be2, k, theta32 - h);
             const float e1 = ritz_last_component(al, be2, k, theta32 + h);
             const float lim = (float)(4.0 * tol_rel) * fabsf(theta32) / (float)fabs(beta_k);
-            if (isfinite(e0) && isfinite(e1) && fminf(e0, e1) > lim && fmaxf(e0, e1) <= 2.f * fminf(e0, e1))
+            if (isfinite(e0) && isfinite(e1) && fminf(e0, e1) >= 1e-2f && fminf(e0, e1) > lim &&
+                fmaxf(e0, e1) <= 2.f * fminf(e0, e1))
                 s_est = fminf(e0, e1);
         }
         if (s_est < 0.f) {
