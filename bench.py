@@ -488,12 +488,13 @@ def run_extras(P, T, u0, dev):
     Tg = [X.cuda() for X in Ts]
     ug = [torch.cat(W.unit_gaussian_vectors(X.shape, 1000 + i)).cuda() for i, X in enumerate(Ts)]
     from paper_2403_01778_gb300 import autotune
-    th, _ = autotune.best_threads(Tg, ug)
-    P.hoscf_solve_batched(Tg, ug, tol=1e-6, batch_threads=th)
+    (th, fc), tune = autotune.best_config(Tg, ug)
+    P.hoscf_solve_batched(Tg, ug, tol=1e-6, batch_threads=th, batch_faces=fc)
     reps = []
     for _ in range(7):
         tb, (sig, _, infos, st) = _timed(lambda: P.hoscf_solve_batched(Tg, ug, tol=1e-6,
-                                                                        batch_threads=th))
+                                                                        batch_threads=th,
+                                                                        batch_faces=fc))
         reps.append(tb)
     tb = statistics.median(reps)
     k = 64
@@ -506,7 +507,8 @@ def run_extras(P, T, u0, dev):
         preps.append(tp / len(idx))
     per_tensor = statistics.median(preps)
     ex["batched_1024"] = {"seconds": tb, "seconds_reps": reps, "tensors_per_s": len(Tg) / tb,
-                          "threads": th, "all_converged": st == 0,
+                          "threads": th, "faces_per_group": fc, "autotune_seconds": tune.get("seconds"),
+                          "all_converged": st == 0,
                           "max_resid": max(inf.resid for inf in infos),
                           "per_tensor_launch_s": per_tensor, "per_tensor_reps": preps,
                           "per_tensor_sample": f"{len(idx)} of {len(Tg)} tensors, median of 5",

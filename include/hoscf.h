@@ -92,6 +92,9 @@ typedef struct {
     int64_t timeout_ns;        /* bound on every device-side wait (0 = 2 s) */
     int batch_threads;         /* hoscf_solve_batched: threads per CTA (256, 512 or 1024;
                                   0 = 512); chosen by the package's autotuner */
+    int batch_faces;           /* hoscf_solve_batched: at most this many faces (T[o][:][:],
+                                  o over the leading modes) staged and folded per group,
+                                  1 .. 32 (0 = 32); chosen by the autotuner */
 } hoscf_opts;
 
 typedef struct {

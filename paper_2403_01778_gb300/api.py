@@ -398,7 +398,7 @@ def hoscf_backward(T: torch.Tensor, u: torch.Tensor, sigma: float, grad_sigma: f
 
 
 def hoscf_solve_batched(tensors, u0s, tol=1e-6, max_iter=200, eig_tol=None, timeout_ns=None,
-                        batch_threads=None, stream=None):
+                        batch_threads=None, batch_faces=None, stream=None):
     """Many small independent F32 tensors (orders 3-4) in one persistent,
     graph-captured launch.  Returns (sigmas, factor tensors, infos, status)."""
     cnt = len(tensors)
@@ -413,6 +413,8 @@ def hoscf_solve_batched(tensors, u0s, tol=1e-6, max_iter=200, eig_tol=None, time
     o = _opts(tol, max_iter, None, eig_tol, None, None, None, timeout_ns)
     if batch_threads is not None:
         o.batch_threads = int(batch_threads)
+    if batch_faces is not None:
+        o.batch_faces = int(batch_faces)
     dev = tensors[0].device.index
     h = handle(dev)
     st = _lib.load().hoscf_solve_batched(h, cnt, arr, pin, ctypes.byref(o), pout, sig, infos,

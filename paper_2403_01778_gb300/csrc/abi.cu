@@ -362,6 +362,7 @@ hoscf_status hoscf_opts_default(hoscf_opts* o) {
     o->switch_tol = 1e-3;
     o->timeout_ns = 2000000000;   // 2 s per bounded device wait
     o->batch_threads = 0;
+    o->batch_faces = 0;
     return HOSCF_OK;
 }
 
@@ -891,6 +892,8 @@ hoscf_status hoscf_solve_batched(hoscf_handle* h, int count, const hoscf_tensor_
     const int threads = o.batch_threads == 0 ? 512 : o.batch_threads;
     if (threads != 256 && threads != 512 && threads != 1024)
         return fail(h, HOSCF_EINVAL, "batch_threads must be 256, 512 or 1024");
+    if (o.batch_faces < 0 || o.batch_faces > 32)
+        return fail(h, HOSCF_EINVAL, "batch_faces must be 0 .. 32");
     DeviceGuard g(h->device);
     // descriptors + results: ~100 bytes per tensor, staged through pinned
     // memory; the workspace head (status word, barrier state) is left alone

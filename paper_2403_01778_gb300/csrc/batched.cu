@@ -60,6 +60,7 @@ struct BatchArgs {
     double eig_adapt;
     int mmax;
     int n_max, P_max, F_max, AB_max;
+    int faces;             // at most this many faces per staged group (1 .. 32)
 };
 
 struct BShape {
@@ -70,6 +71,11 @@ struct BShape {
 };
 
 __device__ __forceinline__ int bidx(int d, int m, int n) { return m * d - m * (m + 1) / 2 + (n - m - 1); }
+
+// Floats of each of the row-sum and column-sum regions: room for the sums of
+// a group of faces (at least 1024, so groups of up to 32 faces of up to 32
+// rows / columns fit).
+HOSCF_HD inline int batch_ycap(int ab_max) { return std::max((ab_max + 3) & ~3, 1024); }
 
 __device__ __forceinline__ int bmode(const BShape& s, int q) {
     int m = 0;
@@ -100,72 +106,133 @@ __device__ __forceinline__ double cta_sum_d(double v, double* red) {
     return t;
 }
 
-// All blocks of one tensor into H (shared memory), one pass over T.
+// All blocks of one tensor into H (shared memory), one pass over T.  Faces
+// T[o][:][:] arrive in groups of K consecutive outer indices (K faces fill
+// one staging buffer, at most 32), double-buffered in shared memory by
+// cp.async (group g + 1 lands while group g is folded; 16-byte copies when
+// the group is 16-byte aligned, else 4-byte), two CTA barriers per group.
+// Per group: the face block H_{d-2,d-1} += sum_k w_k T_k (each entry owned
+// by one thread, faces in order); the row sums y1_k[a] = T_k[a][:] . u_B by
+// one warp per row; the column sums y2_k[b] = u_A . T_k[:][b] by one thread
+// per (k, b), or - one big face per group - by groups of threads over
+// interleaved rows, added in group order.  Every block entry is updated by
+// one thread in face order: the blocks are deterministic.
 __device__ void batch_blocks(const BShape& s, const float* __restrict__ T, const float* u, float* H,
-                             float* face, float* y1, float* y2, float* red) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+                             float* faces, int fstride, float* y1, float* y2, int ycap, float* part,
+                             float* red, int kmax) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int d = s.d;
     const int A = s.dims[d - 2], B = s.dims[d - 1], F = A * B;
     const int O = (d == 3) ? s.dims[0] : s.dims[0] * s.dims[1];
     const float* uA = u + s.moff[d - 2];
     const float* uB = u + s.moff[d - 1];
+    const int K = max(1, min(min(kmax, fstride / F), min(ycap / A, ycap / B)));
+    const int ngrp = (O + K - 1) / K;
+    const bool v16 = ((K * F) & 3) == 0 && (F & 3) == 0 && (reinterpret_cast<uintptr_t>(T) & 15) == 0;
+    // column-sum groups for one face per group: thread t -> column t % B,
+    // rows t / B, t / B + ng, ...
+    const int ng = max(1, nt / B);
+    const int gb = tid % B, gg = tid / B;
     for (int i = tid; i < s.P; i += nt) H[i] = 0.f;
     float* Hf = H + s.boff[bidx(d, d - 2, d - 1)];
-    __syncthreads();
-    for (int o = 0; o < O; ++o) {
-        const float* src = T + (size_t)o * F;
-        for (int f = tid; f < F; f += nt) face[f] = __ldcs(src + f);
-        __syncthreads();
-        int i0, i1 = 0;
-        float w;
-        if (d == 3) {
-            i0 = o;
-            w = u[i0];
+    auto outer_w = [&](int o) {
+        if (d == 3) return u[o];
+        const int a0 = o / s.dims[1], a1 = o - a0 * s.dims[1];
+        return u[a0] * u[s.moff[1] + a1];
+    };
+    auto stage = [&](int g) {
+        const int o0 = g * K, kk = min(K, O - o0);
+        const float* src = T + (size_t)o0 * F;
+        float* dst = faces + (size_t)(g & 1) * fstride;
+        const int cnt = kk * F;
+        if (v16) {
+            for (int f4 = tid; f4 < (cnt >> 2); f4 += nt) cp_async<16>(dst + 4 * f4, src + 4 * f4, true);
         } else {
-            i0 = o / s.dims[1];
-            i1 = o - i0 * s.dims[1];
-            w = u[i0] * u[s.moff[1] + i1];
+            for (int f = tid; f < cnt; f += nt) cp_async<4>(dst + f, src + f, true);
         }
-        for (int f = tid; f < F; f += nt) Hf[f] = fmaf(w, face[f], Hf[f]);
-        for (int a = tid; a < A; a += nt) {
-            float t = 0.f;
-            for (int b = 0; b < B; ++b) t = fmaf(face[a * B + b], uB[b], t);
-            y1[a] = t;
-        }
-        for (int b = tid; b < B; b += nt) {
-            float t = 0.f;
-            for (int a = 0; a < A; ++a) t = fmaf(face[a * B + b], uA[a], t);
-            y2[b] = t;
-        }
-        __syncthreads();
-        if (d == 3) {
-            // H01[o][a] = y1[a], H02[o][b] = y2[b]
-            float* H01 = H + s.boff[0] + (size_t)o * A;
-            float* H02 = H + s.boff[1] + (size_t)o * B;
-            for (int a = tid; a < A; a += nt) H01[a] = y1[a];
-            for (int b = tid; b < B; b += nt) H02[b] = y2[b];
+        cp_async_commit();
+    };
+    stage(0);
+    for (int g = 0; g < ngrp; ++g) {
+        if (g + 1 < ngrp) {
+            stage(g + 1);
+            cp_async_wait_group<1>();   // this thread's copies of group g have landed
         } else {
-            const float u0v = u[i0], u1v = u[s.moff[1] + i1];
-            float* H02 = H + s.boff[bidx(4, 0, 2)] + (size_t)i0 * A;
-            float* H12 = H + s.boff[bidx(4, 1, 2)] + (size_t)i1 * A;
-            float* H03 = H + s.boff[bidx(4, 0, 3)] + (size_t)i0 * B;
-            float* H13 = H + s.boff[bidx(4, 1, 3)] + (size_t)i1 * B;
-            for (int a = tid; a < A; a += nt) {
-                H02[a] = fmaf(u1v, y1[a], H02[a]);
-                H12[a] = fmaf(u0v, y1[a], H12[a]);
+            cp_async_wait_group<0>();
+        }
+        __syncthreads();               // everyone's copies of group g are visible (and H zeroed)
+        const float* fb = faces + (size_t)(g & 1) * fstride;
+        const int o0 = g * K, kk = min(K, O - o0);
+        for (int f = tid; f < F; f += nt) {
+            float h = Hf[f];
+            for (int k = 0; k < kk; ++k) h = fmaf(outer_w(o0 + k), fb[k * F + f], h);
+            Hf[f] = h;
+        }
+        for (int row = warp; row < kk * A; row += nw) {
+            const float* fr = fb + (size_t)row * B;     // face row (k, a): k * F + a * B
+            float t = 0.f;
+            for (int b = lane; b < B; b += 32) t = fmaf(fr[b], uB[b], t);
+            t = warp_sum(t);
+            if (lane == 0) y1[row] = t;
+        }
+        if (kk == 1) {
+            if (gg < ng) {
+                float t = 0.f;
+                for (int a = gg; a < A; a += ng) t = fmaf(fb[a * B + gb], uA[a], t);
+                part[gg * B + gb] = t;
             }
+        } else {
+            for (int kb = tid; kb < kk * B; kb += nt) {
+                const int k = kb / B, b = kb - k * B;
+                const float* fk = fb + (size_t)k * F + b;
+                float t = 0.f;
+                for (int a = 0; a < A; ++a) t = fmaf(fk[a * B], uA[a], t);
+                y2[kb] = t;
+            }
+        }
+        __syncthreads();               // y1, y2 (or the column partials) are complete
+        if (kk == 1) {
             for (int b = tid; b < B; b += nt) {
-                H03[b] = fmaf(u1v, y2[b], H03[b]);
-                H13[b] = fmaf(u0v, y2[b], H13[b]);
+                float t = 0.f;
+                for (int q = 0; q < ng; ++q) t += part[q * B + b];
+                y2[b] = t;   // read below only by the thread that wrote it
             }
-            // H01[i0][i1] = r_o = <y1, uA>
-            float r = 0.f;
-            for (int a = tid; a < A; a += nt) r = fmaf(y1[a], uA[a], r);
-            r = cta_sum(r, red);
-            if (tid == 0) H[s.boff[0] + i0 * s.dims[1] + i1] = r;
         }
-        __syncthreads();
+        if (d == 3) {
+            // H01[o][a] = y1_k[a], H02[o][b] = y2_k[b]
+            for (int ka = tid; ka < kk * A; ka += nt) H[s.boff[0] + (size_t)o0 * A + ka] = y1[ka];
+            for (int kb = tid; kb < kk * B; kb += nt) H[s.boff[1] + (size_t)o0 * B + kb] = y2[kb];
+        } else {
+            // rows i0 = o / I_1, i1 = o % I_1 of H02, H12 (from y1) and H03, H13
+            // (from y2); a thread owns one column and walks the group's faces in order
+            for (int a = tid; a < A; a += nt)
+                for (int k = 0; k < kk; ++k) {
+                    const int o = o0 + k, i0 = o / s.dims[1], i1 = o - i0 * s.dims[1];
+                    const float yv = y1[k * A + a];
+                    H[s.boff[bidx(4, 0, 2)] + i0 * A + a] = fmaf(u[s.moff[1] + i1], yv, H[s.boff[bidx(4, 0, 2)] + i0 * A + a]);
+                    H[s.boff[bidx(4, 1, 2)] + i1 * A + a] = fmaf(u[i0], yv, H[s.boff[bidx(4, 1, 2)] + i1 * A + a]);
+                }
+            for (int b = tid; b < B; b += nt)
+                for (int k = 0; k < kk; ++k) {
+                    const int o = o0 + k, i0 = o / s.dims[1], i1 = o - i0 * s.dims[1];
+                    const float yv = y2[k * B + b];
+                    H[s.boff[bidx(4, 0, 3)] + i0 * B + b] = fmaf(u[s.moff[1] + i1], yv, H[s.boff[bidx(4, 0, 3)] + i0 * B + b]);
+                    H[s.boff[bidx(4, 1, 3)] + i1 * B + b] = fmaf(u[i0], yv, H[s.boff[bidx(4, 1, 3)] + i1 * B + b]);
+                }
+            // H01[i0][i1] = r_o = <y1_k, uA>, one warp per face
+            for (int k = warp; k < kk; k += nw) {
+                float r = 0.f;
+                for (int a = lane; a < A; a += 32) r = fmaf(y1[k * A + a], uA[a], r);
+                r = warp_sum(r);
+                if (lane == 0) H[s.boff[0] + o0 + k] = r;
+            }
+        }
+        // the next group's first barrier orders these reads of y1, y2, part and
+        // the staging buffer before they are overwritten (the copy into this
+        // buffer is issued after that barrier)
     }
+    __syncthreads();
+    (void)red;
 }
 
 // y = J v  (J = blocks / (d-1), symmetric, zero diagonal blocks); thread per row.
@@ -195,7 +262,9 @@ __device__ void batch_matvec(const BShape& s, const float* H, const float* v, fl
 struct BatchSmem {
     float* u;      // n
     float* H;      // P
-    float* face;   // max(F, (mmax+1) n)   (face staging; Lanczos basis later)
+    float* face;   // max(2 F', (mmax+1) n)   (two face buffers of F' = F rounded
+                   // up to 4 floats; the Lanczos basis later)
+    float* part;   // 1024 (column-sum partials of the face fold)
     float* y1;     // AB_max
     float* y2;     // AB_max
     float* w;      // n
@@ -224,9 +293,11 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
         S.u = S.rscratch + 9 * kMaxLanczos;
         S.w = S.u + ((a.n_max + 3) & ~3);
         S.y1 = S.w + ((a.n_max + 3) & ~3);
-        S.y2 = S.y1 + ((a.AB_max + 3) & ~3);
-        S.H = S.y2 + ((a.AB_max + 3) & ~3);
+        S.y2 = S.y1 + batch_ycap(a.AB_max);
+        S.H = S.y2 + batch_ycap(a.AB_max);
         S.face = S.H + ((a.P_max + 3) & ~3);
+        const int basis = max(2 * ((a.F_max + 3) & ~3), (a.mmax + 1) * a.n_max);
+        S.part = S.face + ((basis + 3) & ~3);
     }
     __shared__ int s_item;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -271,7 +342,8 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
         int iters = 0, passes = 0;
         double sigma = 0.0, resid = INFINITY;
         while (status == 0) {
-            batch_blocks(sh, it.T, S.u, S.H, S.face, S.y1, S.y2, S.red);
+            batch_blocks(sh, it.T, S.u, S.H, S.face, (a.F_max + 3) & ~3, S.y1, S.y2, batch_ycap(a.AB_max),
+                         S.part, S.red, a.faces);
             ++passes;
             // ---- certificate at x = u / sqrt(d): rho = x^T J x, KKT residual
             float* V = S.face;   // (mmax+1) x n basis
@@ -376,14 +448,21 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
                 }
                 const bool last = last_basis || k >= mmax || !(beta_last > 1e-30);
                 if (k >= 2 && (k <= 6 || (k & 1) == 0 || last)) {
+                    // FP32 pair to decide; the FP64 refinement only once accepted
                     __shared__ RitzOut s_ro;
+                    __shared__ int s_acc;
                     if (warp == 0) {
-                        RitzOut rr = ritz_largest_magnitude(S.alpha, S.beta, k, beta_last, S.sv, S.rscratch);
-                        if (lane == 0) s_ro = rr;
+                        RitzOut rr = ritz_extreme_fp32(S.alpha, S.beta, k, beta_last, S.rscratch, etol, last);
+                        const bool acc = rr.resid <= etol * fabs(rr.theta) || last;
+                        if (acc) rr = ritz_refine_fp64(S.alpha, S.beta, k, beta_last, S.sv, S.rscratch);
+                        if (lane == 0) {
+                            s_ro = rr;
+                            s_acc = acc ? 1 : 0;
+                        }
                     }
                     __syncthreads();
                     ro = s_ro;
-                    if (ro.resid <= etol * fabs(ro.theta) || last) done = true;
+                    if (s_acc) done = true;
                 } else if (last) {
                     if (tid == 0) S.sv[0] = 1.0;
                     __syncthreads();
@@ -452,10 +531,10 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
 
 // ---------------------------------------------------------------- host
 static size_t batch_smem(int n_max, int P_max, int F_max, int AB_max, int mmax) {
-    const int basis = std::max(F_max, (mmax + 1) * n_max);
+    const int basis = std::max(2 * ((F_max + 3) & ~3), (mmax + 1) * n_max);
     return sizeof(double) * (64 + 3 * kMaxLanczos) +
            sizeof(float) * (64 + kMaxLanczos + 8 + 9 * kMaxLanczos + 2 * ((n_max + 3) & ~3) +
-                            2 * ((AB_max + 3) & ~3) + ((P_max + 3) & ~3) + ((basis + 3) & ~3)) +
+                            2 * batch_ycap(AB_max) + ((P_max + 3) & ~3) + ((basis + 3) & ~3) + 1024) +
            64;
 }
 
@@ -552,6 +631,7 @@ hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* con
     a.eig_tol = o.eig_tol > 0 ? o.eig_tol : 1e-10;
     a.eig_adapt = o.eig_adapt;
     a.mmax = mmax;
+    a.faces = o.batch_faces > 0 ? std::min(32, o.batch_faces) : 32;
     a.n_max = n_max;
     a.P_max = P_max;
     a.F_max = F_max;

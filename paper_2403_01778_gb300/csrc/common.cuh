@@ -113,6 +113,16 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Close the group of this thread's cp.async issued since the last commit;
+// wait until at most N of its committed groups are still in flight.
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // The barrier receives one arrival (counted in its init count) once every
 // cp.async this thread issued before has landed.
 __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {

@@ -77,7 +77,23 @@ def test_autotuner_picks_a_candidate(tmp_path, monkeypatch):
     from paper_2403_01778_gb300 import autotune
     monkeypatch.setattr(autotune, "_CACHE", str(tmp_path / "at.json"))
     Ts, u0 = small_batch(4, 6, 2)
-    th, rec = autotune.best_threads(Ts, u0)
-    assert th in autotune.CANDIDATES
-    th2, _ = autotune.best_threads(Ts, u0)      # cached
-    assert th2 == th
+    (th, fc), rec = autotune.best_config(Ts, u0)
+    assert th in autotune.CANDIDATES and fc in autotune.FACE_CANDIDATES
+    assert len(rec["seconds"]) == len(autotune.CANDIDATES) * len(autotune.FACE_CANDIDATES)
+    (th2, fc2), _ = autotune.best_config(Ts, u0)      # cached
+    assert (th2, fc2) == (th, fc)
+
+
+@pytest.mark.parametrize("faces", [1, 3, 32])
+def test_faces_per_group_match_the_oracle(faces):
+    """The number of faces staged per group changes the schedule (and, for a
+    group of one face, the order of the column sums): every setting reaches
+    the oracle's solution, and a repeated call is bit-identical."""
+    Ts, u0 = small_batch(5, 6, 6)
+    s1, u1, _, st = P().hoscf_solve_batched(Ts, u0, tol=1e-6, batch_faces=faces)
+    assert st == 0
+    s2, u2, _, _ = P().hoscf_solve_batched(Ts, u0, tol=1e-6, batch_faces=faces)
+    assert s1 == s2 and all(torch.equal(a, b) for a, b in zip(u1, u2))
+    for T, u, s, uo in list(zip(Ts, u0, s1, u1))[:6]:
+        dims = T.shape
+        check_item(T, [u[sum(dims[:k]):sum(dims[:k + 1])] for k in range(len(dims))], s, uo)
