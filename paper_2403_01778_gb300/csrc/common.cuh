@@ -256,6 +256,50 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned nblocks, 
     return s_ok != 0;
 }
 
+// The same barrier in two halves, so that a CTA can work between its arrival
+// and its wait: grid_arrive publishes the CTA's earlier writes and counts it
+// in (after a CTA barrier); grid_wait polls (bounded) until every CTA of
+// this epoch has arrived.  Each grid_arrive must be followed by exactly one
+// grid_wait, or by the CTA leaving the kernel.
+__device__ __forceinline__ void grid_arrive(unsigned* count, unsigned& epoch) {
+    __syncthreads();
+    ++epoch;
+    if (threadIdx.x == 0)
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned* count, unsigned nblocks, unsigned epoch, int* err,
+                                          uint64_t limit_ns) {
+    __shared__ int s_okw;
+    if (threadIdx.x == 0) {
+        const unsigned target = epoch * nblocks;
+        auto seen = [count]() {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            return v;
+        };
+        int ok = 1;
+        if ((int)(seen() - target) < 0) {
+            const uint64_t t0 = global_timer_ns();
+            unsigned spins = 0;
+            while ((int)(seen() - target) < 0) {
+                __nanosleep(20);
+                if ((++spins & 255u) == 0) {
+                    if (*(volatile int*)err) { ok = 0; break; }
+                    if (global_timer_ns() - t0 > limit_ns) {
+                        atomicCAS(err, 0, (int)DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        s_okw = ok;
+    }
+    __syncthreads();
+    return s_okw != 0;
+}
+
 // ------------------------------------------------------------------ element loads
 template <typename E>
 struct ElemTraits;

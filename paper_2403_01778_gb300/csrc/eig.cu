@@ -638,7 +638,23 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         __syncthreads();
         // convergence test on the largest-magnitude Ritz pair
         const bool last = (k == a.mmax) || (k == n) || !(beta_last > 1e-30);
-        if (check_now(k) || last) {
+        const bool chk = check_now(k) || last;
+        // On a check step of a multi-CTA eigen step, the next basis vector is
+        // published and the exchange barrier entered before the check, so the
+        // check (one warp, identical in every CTA) overlaps the other CTAs'
+        // arrivals; if it stops the iteration, every CTA leaves without waiting.
+        const bool spec = chk && !last && G > 1 && !a.rqi;
+        if (spec) {
+            const float inv = 1.0f / (float)beta_last;
+            float* dst = vslot(j + 1);
+            for (int q = tid; q < nr; q += kEigThreads) {
+                const float v = Yl[q] * inv;
+                Vl[(size_t)(j + 1) * R + q] = v;
+                dst[r0 + q] = v;
+            }
+            grid_arrive(a.bar, bar_epoch);
+        }
+        if (chk) {
             __shared__ RitzOut s_ro;
             __shared__ int s_acc;
             if (a.rqi) {
@@ -677,14 +693,18 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             }
         }
         if (!done) {
-            const float inv = 1.0f / (float)beta_last;
-            float* dst = vslot(j + 1);
-            for (int q = tid; q < nr; q += kEigThreads) {
-                const float v = Yl[q] * inv;
-                Vl[(size_t)(j + 1) * R + q] = v;
-                dst[r0 + q] = v;
+            if (spec) {
+                if (!grid_wait(a.bar, G, bar_epoch, a.err, a.timeout_ns)) return;
+            } else {
+                const float inv = 1.0f / (float)beta_last;
+                float* dst = vslot(j + 1);
+                for (int q = tid; q < nr; q += kEigThreads) {
+                    const float v = Yl[q] * inv;
+                    Vl[(size_t)(j + 1) * R + q] = v;
+                    dst[r0 + q] = v;
+                }
+                if (!eig_sync(a, G, bar_epoch)) return;
             }
-            if (!eig_sync(a, G, bar_epoch)) return;
         }
     }
     // ---- Ritz vector x = V[0..k-1] s for my rows (FP64 accumulation); block
