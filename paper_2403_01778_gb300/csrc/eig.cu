@@ -10,7 +10,8 @@
 //
 // Lanczos runs as one cooperative kernel over G CTAs: rows are split across
 // CTAs, every step does one mat-vec and one full (classical Gram-Schmidt)
-// reorthogonalisation against the whole FP64 basis, with two grid barriers.
+// reorthogonalisation against the whole basis (FP32 rows kept by each CTA),
+// with two grid barriers.
 // Scalars (dot products, the tridiagonal matrix, Ritz values) are reduced in
 // a fixed order and recomputed identically by every CTA, so all CTAs take the
 // same decisions without another barrier.
