@@ -300,6 +300,41 @@ __device__ __forceinline__ bool grid_wait(unsigned* count, unsigned nblocks, uns
     return s_okw != 0;
 }
 
+// grid_wait for a group of warps of the CTA: thread `leader` polls, then the
+// group's nthreads threads meet at named barrier `bar_id` (not 0, which
+// __syncthreads uses).  Same bound and error handling as grid_wait.
+__device__ __forceinline__ bool grid_wait_group(unsigned* count, unsigned nblocks, unsigned epoch,
+                                                int* err, uint64_t limit_ns, int leader,
+                                                int bar_id, int nthreads, int* ok_out) {
+    if ((int)threadIdx.x == leader) {
+        const unsigned target = epoch * nblocks;
+        auto seen = [count]() {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            return v;
+        };
+        int ok = 1;
+        if ((int)(seen() - target) < 0) {
+            const uint64_t t0 = global_timer_ns();
+            unsigned spins = 0;
+            while ((int)(seen() - target) < 0) {
+                __nanosleep(20);
+                if ((++spins & 255u) == 0) {
+                    if (*(volatile int*)err) { ok = 0; break; }
+                    if (global_timer_ns() - t0 > limit_ns) {
+                        atomicCAS(err, 0, (int)DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        *ok_out = ok;
+    }
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthreads) : "memory");
+    return *ok_out != 0;
+}
+
 // ------------------------------------------------------------------ element loads
 template <typename E>
 struct ElemTraits;

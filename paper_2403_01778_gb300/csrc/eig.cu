@@ -198,11 +198,13 @@ __device__ void fill_cache_rows(const EigArgs& a, int r0, int r1, float* cache,
 // sums the four rows over the lanes with six shuffles.
 // With vec4 (every mode offset a multiple of 4, so every row, its column
 // runs and the vector are 16-byte aligned) the loads are 16 bytes wide.
+// Warps w0 .. w0 + nw - 1 take part (all by default); every row's sum is the
+// same whichever warp computes it.
 __device__ void matvec_rows_cached(const EigArgs& a, const float* __restrict__ vf, int r0, int r1,
                                    const float* __restrict__ cache, const int64_t* crow,
-                                   float* yrow, bool vec4) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int RW = (r1 - r0 + kEigWarps - 1) / kEigWarps;
+                                   float* yrow, bool vec4, int w0 = 0, int nw = kEigWarps) {
+    const int warp = (int)(threadIdx.x >> 5) - w0, lane = threadIdx.x & 31;
+    const int RW = (r1 - r0 + nw - 1) / nw;
     const int qb = r0 + warp * RW, qe = min(r1, qb + RW);
     for (int q = qb; q < qe;) {
         const int m = mode_of(a, q);
@@ -296,6 +298,47 @@ __device__ void reduce_partials(const T* pb, int ps, int G, int cnt, T* out, T* 
             for (int w = 1; w < kEigWarps; ++w) t += sc[w * 32 + lane];
             out[i] = t;
         }
+    }
+    __syncthreads();
+}
+
+// FP64 form of reduce_partials for cnt <= 32 values, laid out for the fewest
+// FP64 instructions (an FP64 instruction occupies the pipe for ~64 cycles
+// on this part whatever its active lanes): each value has L lanes (L the
+// largest power of two with L * cnt <= 32); lane s of value i in warp w adds
+// the partials of CTAs w + 8 (s + L t), t = 0, 1, ...; a butterfly adds the
+// L lane sums and warp 0 adds the 8 warp sums in warp order.  Every CTA
+// computes the same values in the same order.
+__device__ void reduce_partials_d(const double* pb, int ps, int G, int cnt, double* out,
+                                  double* scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int L = 32;
+    while (L > 1 && L * cnt > 32) L >>= 1;
+    const int i = lane / L, sub = lane - i * L;
+    const int stride = kEigWarps * L;
+    const int nt = (G + stride - 1) / stride;   // terms per lane (uniform)
+    double s = 0.0;
+    if (i < cnt) {
+        const int c0 = warp + kEigWarps * sub;
+        for (int t0 = 0; t0 < nt; t0 += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + (t0 + u) * stride;
+                v[u] = (t0 + u < nt && c < G) ? __ldcg(pb + (size_t)c * ps + i) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (t0 + u < nt) s += v[u];
+        }
+    }
+    for (int o = L >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(HOSCF_FULLMASK, s, o);
+    if (sub == 0 && i < cnt) scratch[warp * 32 + i] = s;
+    __syncthreads();
+    if (warp == 0 && lane < cnt) {
+        double t = scratch[lane];
+        for (int w = 1; w < kEigWarps; ++w) t += scratch[w * 32 + lane];
+        out[lane] = t;
     }
     __syncthreads();
 }
@@ -404,44 +447,70 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     if (!eig_sync(a, G, bar_epoch)) return;
 
     int k = 0;
+    // the last off-diagonal beta_k: FP32 in every thread (FP64 only where a
+    // single warp needs it), FP64 for the start's b0
     double beta_last = 0.0;
+    float beta_f = 0.f;
     RitzOut ro;
     ro.theta = 0.0;
     ro.resid = 0.0;
     bool done = false;
     bool hopm_out = false;
-    for (int j = 0; j < a.mmax && !done; ++j) {
-        // every CTA gets the whole current vector
-        const float* src = vslot(j);
+    float wscale = 1.0f;   // normalisation of the published vector (first Lanczos vector only)
+    // every CTA gets the whole vector of slot (jj & 1), scaled by ws; threads
+    // t0 .. t0 + nt - 1 take part
+    auto read_vec = [&](int jj, float ws, int t0, int nt) {
+        const float* src = vslot(jj);
+        const int t = tid - t0;
         if (vec4) {
             const float4* s4 = reinterpret_cast<const float4*>(src);
             float4* d4 = reinterpret_cast<float4*>(vf);
             const int n4 = n >> 2;
-            for (int q0 = tid; q0 < n4; q0 += 4 * kEigThreads) {
-                float4 t[4];
+            for (int q0 = t; q0 < n4; q0 += 4 * nt) {
+                float4 tv[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (q0 + u * kEigThreads < n4) t[u] = __ldcg(s4 + q0 + u * kEigThreads);
+                    if (q0 + u * nt < n4) tv[u] = __ldcg(s4 + q0 + u * nt);
+                if (ws != 1.0f) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        tv[u] = make_float4(tv[u].x * ws, tv[u].y * ws, tv[u].z * ws, tv[u].w * ws);
+                }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (q0 + u * kEigThreads < n4) d4[q0 + u * kEigThreads] = t[u];
+                    if (q0 + u * nt < n4) d4[q0 + u * nt] = tv[u];
             }
         } else {
-            for (int q0 = tid; q0 < n; q0 += 8 * kEigThreads) {
-                float t[8];
+            for (int q0 = t; q0 < n; q0 += 8 * nt) {
+                float tv[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (q0 + u * kEigThreads < n) t[u] = __ldcg(src + q0 + u * kEigThreads);
+                    if (q0 + u * nt < n) tv[u] = __ldcg(src + q0 + u * nt);
+                if (ws != 1.0f) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) tv[u] *= ws;
+                }
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (q0 + u * kEigThreads < n) vf[q0 + u * kEigThreads] = t[u];
+                    if (q0 + u * nt < n) vf[q0 + u * nt] = tv[u];
             }
         }
-        __syncthreads();
-        if (cache)
-            matvec_rows_cached(a, vf, r0, r1, cache, crow, Yl, vec4_mv);
-        else
-            matvec_rows(a, vf, r0, r1, nullptr, crow, false, j == 0 ? &hd[0] : nullptr, Yl);
+    };
+    // set when warps 1..7 already read the next vector and formed its
+    // mat-vec during the previous step's Ritz check (see below)
+    bool pre = false;
+    __shared__ int s_okg;
+    for (int j = 0; j < a.mmax && !done; ++j) {
+        if (!pre) {
+            read_vec(j, wscale, 0, kEigThreads);
+            wscale = 1.0f;
+            __syncthreads();
+            if (cache)
+                matvec_rows_cached(a, vf, r0, r1, cache, crow, Yl, vec4_mv);
+            else
+                matvec_rows(a, vf, r0, r1, nullptr, crow, false, j == 0 ? &hd[0] : nullptr, Yl);
+        }
+        pre = false;
         __syncthreads();
         if (j == 0) {
             // FP64 certificate of the start point x0 (unnormalised):
@@ -457,7 +526,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                     if (lane == 0) pdd[(size_t)24 * G + (size_t)c * kMaxOrder + m] = t;
                 }
                 if (!eig_sync(a, G, bar_epoch)) return;
-                reduce_partials<double>(pdd + (size_t)24 * G, kMaxOrder, G, a.d, mu_s, rp_d);
+                reduce_partials_d(pdd + (size_t)24 * G, kMaxOrder, G, a.d, mu_s, rp_d);
                 for (int q = tid; q < nr; q += kEigThreads) {
                     const int m = mode_of(a, q + r0);
                     Yl[q] = (float)((double)Yl[q] - mu_s[m] * (double)a.proj_u[q + r0]);
@@ -471,63 +540,106 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 sxx += x * x;
                 syy += y * y;
             }
+            // FP64 warp sums only in the warps that hold rows (FP64 instructions
+            // cost the same with no active data)
+            const int nwr = min(kEigWarps, (nr + 31) >> 5);
             __shared__ double red[3][kEigWarps];
-            sxy = warp_sum_d(sxy);
-            sxx = warp_sum_d(sxx);
-            syy = warp_sum_d(syy);
-            if (lane == 0) {
-                red[0][warp] = sxy;
-                red[1][warp] = sxx;
-                red[2][warp] = syy;
+            if (warp < nwr) {
+                sxy = warp_sum_d(sxy);
+                sxx = warp_sum_d(sxx);
+                syy = warp_sum_d(syy);
+                if (lane == 0) {
+                    red[0][warp] = sxy;
+                    red[1][warp] = sxx;
+                    red[2][warp] = syy;
+                }
             }
             __syncthreads();
             if (tid < 3) {
                 double t = 0.0;
-                for (int w8 = 0; w8 < kEigWarps; ++w8) t += red[tid][w8];
+                for (int w8 = 0; w8 < nwr; ++w8) t += red[tid][w8];
                 pdd[(size_t)c * 4 + tid] = t;
             }
             if (tid == 3) pdd[(size_t)c * 4 + 3] = hd[0];
             if (!eig_sync(a, G, bar_epoch)) return;
-            reduce_partials<double>(pdd, 4, G, 4, hd + 1, rp_d);   // hd[1..4]
-            const double xy = hd[1], xx = hd[2], yy = hd[3];
-            if (!(xx > 0.0) || !isfinite(xx) || !isfinite(yy)) {
+            reduce_partials_d(pdd, 4, G, 4, hd + 1, rp_d);   // hd[1..4]
+            // FP64 scalar work once per CTA (FP64 is a narrow pipe on this
+            // part), the results broadcast through shared memory; every CTA
+            // computes the same values, so every decision below is uniform
+            __shared__ double s_sc[4];   // rho, 1/|x0|, b0, r
+            __shared__ int s_flag;       // 0 go on, 1 non-finite, 2 start point certified
+            __shared__ float s_b0f;
+            if (tid == 0) {
+                const double xy = hd[1], xx = hd[2], yy = hd[3];
+                const bool bad = !(xx > 0.0) || !isfinite(xx) || !isfinite(yy);
+                s_flag = bad ? 1 : 0;
+                s_sc[0] = bad ? 0.0 : xy / xx;
+                s_sc[1] = bad ? 0.0 : 1.0 / sqrt(xx);
+            }
+            __syncthreads();
+            if (s_flag) {
                 if (tid == 0) atomicCAS(a.err, 0, (int)DEV_NONFINITE);
                 return;
             }
-            const double rho = xy / xx;
+            const double rho = s_sc[0], inv = s_sc[1];
             // ||J v0 - rho v0||^2 = (yy - xy^2/xx) / xx, evaluated as a sum of
-            // squares to avoid cancellation
-            const double inv = 1.0 / sqrt(xx);
+            // squares to avoid cancellation; in the same sweep the Lanczos start
+            // v0 = x0/|x0|, w = J v0 - rho v0 (FP32).  w is published
+            // unnormalised with the partial sums, so the norm's reduction rides
+            // on the exchange barrier of the first Lanczos vector.
+            const float finv = (float)inv, frho = (float)rho;
+            float* wdst = vslot(1);
             double sw = 0.0;
             for (int q = tid; q < nr; q += kEigThreads) {
-                const double w = ((double)Yl[q] - rho * (double)Vl[q]) * inv;
+                const float yq = Yl[q], vq = Vl[q];
+                const double w = ((double)yq - rho * (double)vq) * inv;
                 sw += w * w;
+                if (a.hopm) xrow[q] = (double)yq;
+                const float v = vq * finv;
+                const float wq = yq * finv - frho * v;
+                Vl[q] = v;
+                Yl[q] = wq;
+                wdst[r0 + q] = wq;
             }
-            sw = warp_sum_d(sw);
-            if (lane == 0) red[0][warp] = sw;
+            if (warp < nwr) {
+                sw = warp_sum_d(sw);
+                if (lane == 0) red[0][warp] = sw;
+            }
             __syncthreads();
             if (tid == 0) {
                 double t = 0.0;
-                for (int w8 = 0; w8 < kEigWarps; ++w8) t += red[0][w8];
+                for (int w8 = 0; w8 < nwr; ++w8) t += red[0][w8];
                 pdd[(size_t)(G + c) * 4] = t;
             }
             if (!eig_sync(a, G, bar_epoch)) return;
-            reduce_partials<double>(pdd + (size_t)G * 4, 4, G, 1, hd + 5, rp_d);
-            const double b0 = sqrt(fmax(hd[5], 0.0));
-            const double jfro = sqrt(hd[4]) * (double)a.scale;
-            const double r = (rho != 0.0) ? sqrt_d * b0 / fabs(rho) : INFINITY;
-            if (c == 0 && tid == 0) {
-                a.scal[SC_SIGMA] = rho;
-                a.scal[SC_KKT] = r;
-                a.scal[SC_R41] = b0 / (jfro + fabs(rho));
-                a.scal[SC_JFRO] = jfro;
-                a.scal[SC_CONVERGED] = 0.0;
+            reduce_partials_d(pdd + (size_t)G * 4, 4, G, 1, hd + 5, rp_d);
+            if (tid == 0) {
+                const double b0 = sqrt(fmax(hd[5], 0.0));
+                const double jfro = sqrt(hd[4]) * (double)a.scale;
+                const double r = (rho != 0.0) ? sqrt_d * b0 / fabs(rho) : INFINITY;
+                s_sc[2] = b0;
+                s_sc[3] = r;
+                // inexact eigen steps: the Ritz tolerance follows the residual
+                s_sc[0] = (a.adapt > 0.0 && rho != 0.0) ? fmax(a.eig_tol, fmin(1e-3, a.adapt * r))
+                                                        : a.eig_tol;
+                s_flag = (!isfinite(rho) || !isfinite(b0)) ? 1
+                         : (a.check && rho != 0.0 && r <= a.kkt_tol) ? 2 : 0;
+                s_b0f = (float)b0;
+                if (c == 0) {
+                    a.scal[SC_SIGMA] = rho;
+                    a.scal[SC_KKT] = r;
+                    a.scal[SC_R41] = b0 / (jfro + fabs(rho));
+                    a.scal[SC_JFRO] = jfro;
+                    a.scal[SC_CONVERGED] = 0.0;
+                }
             }
-            if (!isfinite(rho) || !isfinite(b0)) {
+            __syncthreads();
+            const double b0 = s_sc[2], tol_adapted = s_sc[0];
+            if (s_flag == 1) {
                 if (tid == 0) atomicCAS(a.err, 0, (int)DEV_NONFINITE);
                 return;
             }
-            if (a.check && rho != 0.0 && r <= a.kkt_tol) {
+            if (s_flag == 2) {
                 // the start point is certified: no eigen step
                 if (c == 0 && tid == 0) {
                     a.scal[SC_CONVERGED] = 1.0;
@@ -539,25 +651,19 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             }
             if (a.hopm) {
                 // Jacobi-HOPM: y = J x0 has blocks g_n / sqrt(d) (g_n = A x_{k!=n} u^(k))
-                for (int q = tid; q < nr; q += kEigThreads) xrow[q] = (double)Yl[q];
                 ro.theta = rho;
                 ro.resid = b0;
                 hopm_out = true;
                 break;
             }
-            if (a.adapt > 0.0 && rho != 0.0) a.eig_tol = fmax(a.eig_tol, fmin(1e-3, a.adapt * r));
-            // Lanczos start: v0 = x0/|x0|, w = J v0 - rho v0 (FP32)
-            const float finv = (float)inv, frho = (float)rho;
-            for (int q = tid; q < nr; q += kEigThreads) {
-                const float v = Vl[q] * finv;
-                Vl[q] = v;
-                Yl[q] = Yl[q] * finv - frho * v;
-            }
+            a.eig_tol = tol_adapted;
             if (tid == 0) {
                 alpha[0] = rho;
                 beta[0] = b0;
             }
             beta_last = b0;
+            beta_f = s_b0f;
+            wscale = 1.0f / beta_f;   // the published w is normalised when read
             k = 1;
         } else {
             // partial dots over my rows: h_i = V[i].y (i <= j), yy, and with a
@@ -602,7 +708,9 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 for (int i = 0; i <= j; ++i) w = fmaf(-hsum[i], Vl[(size_t)i * R + q], w);
                 Yl[q] = w;
             }
-            double alj = hsum[j];
+            const float h1 = hsum[j];
+            float h2 = 0.f;
+            bool two = false;
             if (b2 < 0.25f * yy) {
                 // heavy cancellation: second Gram-Schmidt pass with exact norm
                 __syncthreads();
@@ -622,31 +730,35 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 float ssq2 = 0.f;
                 for (int i = 0; i <= j; ++i) ssq2 = fmaf(hsum[i], hsum[i], ssq2);
                 b2 = hsum[j + 1] - ssq2;
-                alj += hsum[j];
+                h2 = hsum[j];
+                two = true;
                 for (int q = tid; q < nr; q += kEigThreads) {
                     float w = Yl[q];
                     for (int i = 0; i <= j; ++i) w = fmaf(-hsum[i], Vl[(size_t)i * R + q], w);
                     Yl[q] = w;
                 }
             }
-            beta_last = (double)sqrtf(fmaxf(b2, 0.f));
+            beta_f = sqrtf(fmaxf(b2, 0.f));
             if (tid == 0) {
-                alpha[j] = alj;
-                beta[j] = beta_last;
+                alpha[j] = two ? (double)h1 + (double)h2 : (double)h1;
+                beta[j] = (double)beta_f;
             }
             k = j + 1;
         }
         __syncthreads();
         // convergence test on the largest-magnitude Ritz pair
-        const bool last = (k == a.mmax) || (k == n) || !(beta_last > 1e-30);
+        const bool last = (k == a.mmax) || (k == n) || !(beta_f > 1e-30f);
         const bool chk = check_now(k) || last;
         // On a check step of a multi-CTA eigen step, the next basis vector is
         // published and the exchange barrier entered before the check, so the
         // check (one warp, identical in every CTA) overlaps the other CTAs'
         // arrivals; if it stops the iteration, every CTA leaves without waiting.
         const bool spec = chk && !last && G > 1 && !a.rqi;
+        // with the rows cached, the check (warp 0) also overlaps the next
+        // step's exchange wait, vector read and mat-vec (warps 1..7)
+        const bool ovl = spec && k >= 2 && cache != nullptr;
         if (spec) {
-            const float inv = 1.0f / (float)beta_last;
+            const float inv = 1.0f / beta_f;
             float* dst = vslot(j + 1);
             for (int q = tid; q < nr; q += kEigThreads) {
                 const float v = Yl[q] * inv;
@@ -666,17 +778,27 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                         w + 2 * kMaxLanczos, w + 3 * kMaxLanczos, w + 4 * kMaxLanczos,
                         reinterpret_cast<int*>(w + 5 * kMaxLanczos), &s_znorm);
                     s_ro.theta = alpha[0];
-                    s_ro.resid = beta_last * rel;   // relative Galerkin residual of the solve
+                    s_ro.resid = (double)beta_f * rel;   // relative Galerkin residual of the solve
                 }
             } else if (k >= 2) {
                 // FP32 pair to decide; the FP64 refinement only once accepted
                 if (warp == 0) {
-                    RitzOut t = ritz_extreme_fp32(alpha, beta, k, beta_last, rscratch, a.eig_tol, last);
+                    const double bk = (double)beta_f;
+                    RitzOut t = ritz_extreme_fp32(alpha, beta, k, bk, rscratch, a.eig_tol, last);
                     const bool acc = t.resid <= a.eig_tol * fabs(t.theta) || last;
-                    if (acc) t = ritz_refine_fp64(alpha, beta, k, beta_last, sv, rscratch);
+                    if (acc) t = ritz_refine_fp64(alpha, beta, k, bk, sv, rscratch);
                     if (lane == 0) {
                         s_ro = t;
                         s_acc = acc ? 1 : 0;
+                    }
+                } else if (ovl) {
+                    // meanwhile warps 1..7 wait for the exchange, read the next
+                    // vector and form its mat-vec (discarded if the check stops)
+                    if (grid_wait_group(a.bar, G, bar_epoch, a.err, a.timeout_ns, 32, 2,
+                                        kEigThreads - 32, &s_okg)) {
+                        read_vec(j + 1, 1.0f, 32, kEigThreads - 32);
+                        asm volatile("bar.sync 2, %0;" ::"r"(kEigThreads - 32) : "memory");
+                        matvec_rows_cached(a, vf, r0, r1, cache, crow, Yl, vec4_mv, 1, kEigWarps - 1);
                     }
                 }
             } else if (tid == 0) {
@@ -693,11 +815,19 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 if (ro.resid <= a.eig_tol * scale_t || last) done = true;
             }
         }
-        if (!done) {
+        if (ovl) {
+            if (!s_okg) return;   // the exchange wait gave up (the code is in the status word)
+            pre = !done;
+        } else if (!done) {
             if (spec) {
                 if (!grid_wait(a.bar, G, bar_epoch, a.err, a.timeout_ns)) return;
+            } else if (j == 0) {
+                // the start block published w with its norm's partial sums and
+                // passed that exchange barrier already
+                const float inv = 1.0f / beta_f;
+                for (int q = tid; q < nr; q += kEigThreads) Vl[(size_t)R + q] = Yl[q] * inv;
             } else {
-                const float inv = 1.0f / (float)beta_last;
+                const float inv = 1.0f / beta_f;
                 float* dst = vslot(j + 1);
                 for (int q = tid; q < nr; q += kEigThreads) {
                     const float v = Yl[q] * inv;
@@ -749,20 +879,25 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         if (lane == 0) pdd[(size_t)8 * G + (size_t)c * (kMaxOrder + 1) + i] = s;
     }
     if (!eig_sync(a, G, bar_epoch)) return;
-    reduce_partials<double>(pdd + (size_t)8 * G, kMaxOrder + 1, G, d + 1, hd + 6, rp_d);
+    reduce_partials_d(pdd + (size_t)8 * G, kMaxOrder + 1, G, d + 1, hd + 6, rp_d);
+    // the scale factors once per CTA (lanes of warp 0), then one multiply per
+    // entry: x_out = sgn x / |x|, u_out = sgn x_n / |x_n| per block
     const double* bn = hd + 6;
-    double tot = 0.0;
-    for (int m = 0; m < d; ++m) tot += bn[m];
-    const double sgn = (!hopm_out && bn[d] < 0.0) ? -1.0 : 1.0;   // HOPM keeps g's sign
-    const double invx = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
-    for (int q = r0 + tid; q < r1; q += kEigThreads) {
-        const double x = xval(q - r0) * sgn;
-        if (a.x_out) a.x_out[q] = x * invx;
-        if (a.u_out) {
-            const int m = mode_of(a, q);
-            const double nb = bn[m];
-            a.u_out[q] = nb > 0.0 ? (float)(x / sqrt(nb)) : 0.f;
+    __shared__ double s_xs[kMaxOrder + 1];   // [0..d-1] block factors, [d] whole-vector factor
+    if (warp == 0) {
+        const double sgn = (!hopm_out && bn[d] < 0.0) ? -1.0 : 1.0;   // HOPM keeps g's sign
+        if (lane < d) s_xs[lane] = bn[lane] > 0.0 ? sgn / sqrt(bn[lane]) : 0.0;
+        if (lane == 0) {
+            double tot = 0.0;
+            for (int m = 0; m < d; ++m) tot += bn[m];
+            s_xs[d] = tot > 0.0 ? sgn / sqrt(tot) : 0.0;
         }
+    }
+    __syncthreads();
+    for (int q = r0 + tid; q < r1; q += kEigThreads) {
+        const double x = xval(q - r0);
+        if (a.x_out) a.x_out[q] = x * s_xs[d];
+        if (a.u_out) a.u_out[q] = (float)(x * s_xs[mode_of(a, q)]);
     }
     if (c == 0 && tid == 0) {
         a.scal[SC_LAMBDA] = ro.theta;
