@@ -660,6 +660,10 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             if (tid == 0) {
                 alpha[0] = rho;
                 beta[0] = b0;
+                // the FP32 tridiagonal of the Ritz checks, kept one entry per step
+                rscratch[0] = (float)rho;
+                rscratch[kMaxLanczos] = s_b0f;
+                rscratch[2 * kMaxLanczos] = s_b0f * s_b0f;
             }
             beta_last = b0;
             beta_f = s_b0f;
@@ -740,8 +744,12 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             }
             beta_f = sqrtf(fmaxf(b2, 0.f));
             if (tid == 0) {
-                alpha[j] = two ? (double)h1 + (double)h2 : (double)h1;
+                const double aj = two ? (double)h1 + (double)h2 : (double)h1;
+                alpha[j] = aj;
                 beta[j] = (double)beta_f;
+                rscratch[j] = (float)aj;
+                rscratch[kMaxLanczos + j] = beta_f;
+                rscratch[2 * kMaxLanczos + j] = beta_f * beta_f;
             }
             k = j + 1;
         }
@@ -784,7 +792,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 // FP32 pair to decide; the FP64 refinement only once accepted
                 if (warp == 0) {
                     const double bk = (double)beta_f;
-                    RitzOut t = ritz_extreme_fp32(alpha, beta, k, bk, rscratch, a.eig_tol, last);
+                    RitzOut t = ritz_extreme_core(k, bk, rscratch, a.eig_tol, last);
                     const bool acc = t.resid <= a.eig_tol * fabs(t.theta) || last;
                     if (acc) t = ritz_refine_fp64(alpha, beta, k, bk, sv, rscratch);
                     if (lane == 0) {

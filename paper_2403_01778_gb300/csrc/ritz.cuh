@@ -47,6 +47,71 @@ static __device__ float extreme_eig(const float* al, const float* be2, int k, fl
     return 0.5f * (lo + hi);
 }
 
+// Sturm count without divisions for k <= KM, on T scaled by a power of two so
+// that every entry is at most 1 in magnitude (x in the same units): the
+// leading principal minors p_i of T - x I, p_i = (a_i - x) p_{i-1} -
+// b_{i-1}^2 p_{i-2} (p_0 = 1), change sign once per eigenvalue below x, a
+// zero minor taking the sign opposite to its predecessor's (the limit of the
+// pivot form's replacement of a zero pivot by a small negative one).
+// |p_i| <= (1 + sqrt 2)^i, so nothing overflows for KM <= 32; a pair of
+// minors that falls below 2^-32 is rescaled by 2^32 at once (the recurrence
+// is homogeneous in the pair), which keeps clustered spectra, whose minors
+// shrink by a small factor per step, clear of underflow.
+template <int KM>
+static __device__ __forceinline__ int sturm_count_poly(const float (&a)[KM], const float (&b2)[KM],
+                                                       int k, float x) {
+    float pp = 1.f, pc = a[0] - x;
+    bool nc = pc < 0.f || pc == 0.f;   // p_0 > 0
+    int c = nc ? 1 : 0;
+#pragma unroll
+    for (int i = 1; i < KM; ++i) {
+        if (i < k) {
+            const float pn = fmaf(a[i] - x, pc, -b2[i - 1] * pp);
+            pp = pc;
+            pc = pn;
+            const bool nn = pn < 0.f || (pn == 0.f && !nc);
+            c += nn != nc ? 1 : 0;
+            nc = nn;
+            if (fmaxf(fabsf(pp), fabsf(pc)) < 0x1p-32f) {
+                pp *= 0x1p32f;
+                pc *= 0x1p32f;
+            }
+        }
+    }
+    return c;
+}
+
+// extreme_eig for k <= KM with sturm_count_poly: the entries are scaled by
+// scale = 2^-e (exact) so that the Gershgorin bound is below 1, the
+// multisection runs on [-1, 1] and the result is scaled back.
+template <int KM>
+static __device__ float extreme_eig_poly(const float* al, const float* be2, int k, float scale,
+                                         bool want_max, int sublane, unsigned halfmask) {
+    float a[KM], b2[KM];
+    const float s2 = scale * scale;
+#pragma unroll
+    for (int i = 0; i < KM; ++i) {
+        a[i] = i < k ? al[i] * scale : 0.f;
+        b2[i] = i < k - 1 ? be2[i] * s2 : 0.f;
+    }
+    float lo = -1.f, hi = 1.f;
+    for (int round = 0; round < 7; ++round) {
+        const float w = (hi - lo) * (1.f / 17.f);
+        const float x = lo + w * (float)(sublane + 1);
+        const int c = sturm_count_poly<KM>(a, b2, k, x);
+        const bool hit = want_max ? (c == k) : (c >= 1);
+        const unsigned bal = __ballot_sync(halfmask, hit);
+        const unsigned mine = (halfmask == 0xffffu) ? bal : (bal >> 16);
+        const int first = mine ? __ffs(mine) - 1 : 16;
+        const float nlo = lo + w * (float)first;
+        const float nhi = (first == 16) ? hi : lo + w * (float)(first + 1);
+        lo = nlo;
+        hi = nhi;
+        if (hi - lo <= 4.f * 1.2e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
+    }
+    return 0.5f * (lo + hi) / scale;
+}
+
 // Eigenvector of the tridiagonal T for eigenvalue approx theta: two steps of
 // inverse iteration with partial-pivot LU (FP32).  s has k entries, unit norm.
 static __device__ void tridiag_inverse_iteration(const float* al, const float* be, int k, float theta,
@@ -202,17 +267,18 @@ struct RitzOut {
 // flattens out near sqrt(eps32) below that (measured on Lanczos
 // tridiagonals), so only values well above that floor are used.  One thread.
 static __device__ float ritz_last_component(const float* al, const float* be2, int k, float th) {
-    float q = al[0] - th;
-    float r1 = -1.f / q, r2 = 0.f;   // r_1, r_0
-    float num = -1.f;                // p_1' / p_0
+    float rq = __fdividef(1.f, al[0] - th);   // 1 / q_1
+    float r1 = -rq, r2 = 0.f;                 // r_1, r_0
+    float num = -1.f;                         // p_1' / p_0
     for (int j = 1; j < k; ++j) {
         const float aj = al[j] - th;
-        num = -1.f + aj * r1 - be2[j - 1] * __fdividef(r2, q);
+        const float bq = be2[j - 1] * rq;     // b_{j-1}^2 / q_{j-1}
+        num = -1.f + aj * r1 - bq * r2;
         if (j + 1 < k) {
-            const float qn = aj - __fdividef(be2[j - 1], q);
+            const float rqn = __fdividef(1.f, aj - bq);
             r2 = r1;
-            r1 = __fdividef(num, qn);
-            q = qn;
+            r1 = num * rqn;
+            rq = rqn;
         }
     }
     return sqrtf(1.f / fabsf(num));
@@ -233,9 +299,15 @@ static __device__ float ritz_last_component(const float* al, const float* be2, i
 // |theta| - a pair that is clearly not converged - the inverse iteration is
 // skipped and that estimate returned (the caller only learns "not
 // converged").
-static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* beta, int k,
-                                            double beta_k, float* scratch, double tol_rel = 0.0,
-                                            bool need_vec = true) {
+// The same with the FP32 tridiagonal already in scratch (al = scratch[0..k),
+// be = scratch[k'..], be2 = scratch[2k'..], k' = kMaxLanczos; be[k-1] and
+// be2[k-1] are not read): callers that build T one step at a time keep those
+// arrays current instead of converting alpha and beta at every check.
+// poly selects the division-free multisection for k <= 32 (its register
+// arrays suit kernels with registers to spare; the pivot form otherwise).
+static __device__ RitzOut ritz_extreme_core(int k, double beta_k, float* scratch,
+                                            double tol_rel = 0.0, bool need_vec = true,
+                                            bool poly = true) {
     const int lane = threadIdx.x & 31;
     float* al = scratch;
     float* be = al + kMaxLanczos;
@@ -248,13 +320,7 @@ static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* b
     int* piv = reinterpret_cast<int*>(wd + kMaxLanczos);
     float bound = 0.f;
     for (int i = lane; i < k; i += 32) {
-        al[i] = (float)alpha[i];
-        be[i] = (i < k - 1) ? (float)beta[i] : 0.f;
-        be2[i] = be[i] * be[i];
-    }
-    __syncwarp();
-    for (int i = lane; i < k; i += 32) {
-        const float r = fabsf(al[i]) + fabsf(be[i]) + (i > 0 ? fabsf(be[i - 1]) : 0.f);
+        const float r = fabsf(al[i]) + (i < k - 1 ? fabsf(be[i]) : 0.f) + (i > 0 ? fabsf(be[i - 1]) : 0.f);
         bound = fmaxf(bound, r);
     }
     for (int o = 16; o > 0; o >>= 1) bound = fmaxf(bound, __shfl_xor_sync(HOSCF_FULLMASK, bound, o));
@@ -266,6 +332,17 @@ static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* b
     float ext;
     if (k == 1) {
         ext = al[0];
+    } else if (poly && k <= 32) {
+        // power-of-two scale putting the Gershgorin bound below 1
+        int e;
+        frexpf(bound, &e);
+        const float scale = ldexpf(1.f, -e);
+        if (k <= 8)
+            ext = extreme_eig_poly<8>(al, be2, k, scale, !upper, lane & 15, hm);
+        else if (k <= 16)
+            ext = extreme_eig_poly<16>(al, be2, k, scale, !upper, lane & 15, hm);
+        else
+            ext = extreme_eig_poly<32>(al, be2, k, scale, !upper, lane & 15, hm);
     } else {
         ext = extreme_eig(al, be2, k, -bound, bound, !upper, lane & 15, hm, pivmin);
     }
@@ -273,33 +350,35 @@ static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* b
     const float tmin = __shfl_sync(HOSCF_FULLMASK, ext, 16);
     // ties between +l and -l go to the positive end
     const float theta32 = (tmax >= -tmin) ? tmax : tmin;
-    __shared__ float s_est;
-    if (lane == 0) {
-        s_est = -1.f;
-        if (!need_vec && k >= 2) {
-            const float h = 4.8e-7f * fabsf(theta32) + 1e-30f;
-            const float e0 = ritz_last_component(al, be2, k, theta32 - h);
-            const float e1 = ritz_last_component(al, be2, k, theta32 + h);
-            const float lim = (float)(4.0 * tol_rel) * fabsf(theta32) / (float)fabs(beta_k);
-            if (isfinite(e0) && isfinite(e1) && fminf(e0, e1) >= 1e-2f && fminf(e0, e1) > lim &&
-                fmaxf(e0, e1) <= 2.f * fminf(e0, e1))
-                s_est = fminf(e0, e1);
-        }
-        if (s_est < 0.f) {
-            if (k == 1) {
-                sv[0] = 1.f;
-            } else {
-                tridiag_inverse_iteration(al, be, k, theta32, bound, sv, wa, wb, wc, wd, piv);
-            }
-        }
+    // the cheap estimate at both ends of the bracket, on lanes 0 and 1
+    float est = -1.f;
+    if (!need_vec && k >= 2 && lane < 2) {
+        const float h = 4.8e-7f * fabsf(theta32) + 1e-30f;
+        est = ritz_last_component(al, be2, k, lane == 0 ? theta32 - h : theta32 + h);
     }
-    __syncwarp();
+    const float e0 = __shfl_sync(HOSCF_FULLMASK, est, 0);
+    const float e1 = __shfl_sync(HOSCF_FULLMASK, est, 1);
+    float s_est = -1.f;
+    if (!need_vec && k >= 2) {
+        const float lim = __fdividef((float)(4.0 * tol_rel) * fabsf(theta32), (float)fabs(beta_k));
+        if (isfinite(e0) && isfinite(e1) && fminf(e0, e1) >= 1e-2f && fminf(e0, e1) > lim &&
+            fmaxf(e0, e1) <= 2.f * fminf(e0, e1))
+            s_est = fminf(e0, e1);
+    }
     if (s_est >= 0.f) {
         RitzOut ro;
         ro.theta = theta32;
         ro.resid = fabs(beta_k) * (double)s_est;
         return ro;
     }
+    if (lane == 0) {
+        if (k == 1) {
+            sv[0] = 1.f;
+        } else {
+            tridiag_inverse_iteration(al, be, k, theta32, bound, sv, wa, wb, wc, wd, piv);
+        }
+    }
+    __syncwarp();
     float ss = 0.f;
     for (int i = lane; i < k; i += 32) ss = fmaf(sv[i], sv[i], ss);
     ss = warp_sum(ss);
@@ -307,6 +386,22 @@ static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* b
     ro.theta = theta32;
     ro.resid = fabs(beta_k) * (double)(fabsf(sv[k - 1]) * rsqrtf(ss));
     return ro;
+}
+
+static __device__ RitzOut ritz_extreme_fp32(const double* alpha, const double* beta, int k,
+                                            double beta_k, float* scratch, double tol_rel = 0.0,
+                                            bool need_vec = true) {
+    const int lane = threadIdx.x & 31;
+    float* al = scratch;
+    float* be = al + kMaxLanczos;
+    float* be2 = be + kMaxLanczos;
+    for (int i = lane; i < k; i += 32) {
+        al[i] = (float)alpha[i];
+        be[i] = (i < k - 1) ? (float)beta[i] : 0.f;
+        be2[i] = be[i] * be[i];
+    }
+    __syncwarp();
+    return ritz_extreme_core(k, beta_k, scratch, tol_rel, need_vec, false);
 }
 
 // FP64 refinement of the pair ritz_extreme_fp32 left in scratch: Rayleigh
