@@ -643,6 +643,8 @@ def run_ours(args, rank, world, local_rank):
     P.hoscf_profile_enable(local_rank, False)
     n_kern, kern_ms = P.hoscf_profile_read(local_rank)
     kern_avg = kern_ms / max(1, n_kern)
+    n_eig, eig_ms = P.hoscf_profile_read(local_rank, P.PROFILE_EIG_STEP)
+    eig_avg = eig_ms / max(1, n_eig)
     if dist:
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
@@ -713,6 +715,9 @@ def run_ours(args, rank, world, local_rank):
                                    "recorded by the library on the launch stream)",
                          "peak_kind": peak_kind},
             "pass_ms_avg": pass_avg,
+            # the eigen step (J-row build + Lanczos kernel), CUDA events the
+            # library records on the launch stream
+            "eig_step_ms_avg": eig_avg,
             "pass_GBs": nb / (pass_avg / 1e3) / 1e9,
             "e2e": e2e,
             "clocks": clocks,

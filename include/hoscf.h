@@ -360,8 +360,12 @@ hoscf_status hoscf_solve_greedy(hoscf_handle* h, const hoscf_tensor_desc* T, int
  *            it); which = 1 the gradient write of every hoscf_backward call
  *            (its coefficient and write kernels); which = 2 its adjoint
  *            solve (the pass at the solution and the Lanczos solve);
+ *            which = 3 every eigen, RQI or comparison-method step (the
+ *            J-row build and the Lanczos kernel) of hoscf_eig_step,
+ *            hoscf_rqi_step, the solvers' iterations and the adjoint solve
+ *            of hoscf_backward;
  *            zero: stop recording (records are kept for reading).
- *   which    0, 1 or 2 as above.
+ *   which    0 .. 3 as above.
  *   count    host: number of recorded calls of that kind.
  *   total_ms host: sum of their durations in milliseconds; the call waits
  *            for the recorded events to complete.

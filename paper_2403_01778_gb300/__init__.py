@@ -12,5 +12,5 @@ from .api import (HoscfError, SolveResult, handle, hoscf_backward, hoscf_device_
                   hoscf_ttvc_blocks, hoscf_ttvc_blocks_static, hoscf_workspace_size, n_blocks,
                   n_tot, hoscf_create_handle, hoscf_destroy_handle, shard_rows, allreduce_blocks,
                   hoscf_ttvc_blocks_slab, hoscf_solve_sharded, PROFILE_PASS_KERNEL,
-                  PROFILE_GRAD_WRITE, PROFILE_ADJOINT)
+                  PROFILE_GRAD_WRITE, PROFILE_ADJOINT, PROFILE_EIG_STEP)
 from .autograd import HOSCFFunction, hoscf  # noqa: F401

@@ -124,7 +124,7 @@ def hoscf_ttvc_blocks(T: torch.Tensor, u: torch.Tensor, H: torch.Tensor | None =
     return H
 
 
-PROFILE_PASS_KERNEL, PROFILE_GRAD_WRITE, PROFILE_ADJOINT = 0, 1, 2
+PROFILE_PASS_KERNEL, PROFILE_GRAD_WRITE, PROFILE_ADJOINT, PROFILE_EIG_STEP = 0, 1, 2, 3
 
 
 def hoscf_profile_enable(device: int = 0, enable: bool = True) -> None:

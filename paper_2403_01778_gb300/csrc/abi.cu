@@ -15,7 +15,7 @@
 
 using namespace hoscf;
 
-constexpr int kProfKinds = 3;      // measurement aid: pass kernel, gradient write, adjoint solve
+constexpr int kProfKinds = 4;      // measurement aid: pass kernel, gradient write, adjoint solve, eigen step
 
 struct hoscf_handle {
     int device = 0;
@@ -35,7 +35,7 @@ struct hoscf_handle {
     // hoscf_backward call, (2) its adjoint solve (the pass at the solution
     // and the Lanczos solve)
     bool prof_on = false;
-    size_t prof_n[kProfKinds] = {0, 0, 0};
+    size_t prof_n[kProfKinds] = {0, 0, 0, 0};
     std::vector<KernelEvents> prof[kProfKinds];
     BatchGraphCache graphs;       // batched solve: instantiated graphs of recent batches
     char msg[512] = {0};
@@ -244,6 +244,10 @@ hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const 
                         double tol_override = 0.0, int hopm = 0) {
     char* eb = h->ws + L.off_eig;
     float* Jr = reinterpret_cast<float*>(eb + L.ep.off_jr);
+    const KernelEvents* kev = nullptr;
+    hoscf_status ps = prof_slot(h, 3, &kev);
+    if (ps) return ps;
+    if (kev) cudaEventRecord(kev->begin, st);
     cudaError_t e = launch_build_jr(L.s, H, Jr, reinterpret_cast<unsigned*>(h->ws + kOffBar), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "build_jr");
     LanczosLaunch ll;
@@ -276,6 +280,7 @@ hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const 
     ll.smem = L.ep.smem;
     e = launch_lanczos(L.s, ll, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "lanczos");
+    if (kev) cudaEventRecord(kev->end, st);
     return HOSCF_OK;
 }
 

@@ -209,6 +209,29 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// 1/sqrt(x) and 1/x in FP64 from the FP32 hardware approximation and two
+// Newton steps (each squares the relative error: ~1e-7, ~1e-14, then below
+// FP64 rounding) - far fewer FP64 instructions than the correctly rounded
+// routines, whose results they match to a few ulps; arguments outside FP32's
+// normal range take those routines.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    if (!(x >= 1.2e-38 && x <= 3.0e38)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf((float)x);
+    const double hx = 0.5 * x;
+    y = y * fma(-hx * y, y, 1.5);
+    y = y * fma(-hx * y, y, 1.5);
+    return y;
+}
+
+__device__ __forceinline__ double rcp_nr(double x) {
+    const double ax = fabs(x);
+    if (!(ax >= 1.2e-38 && ax <= 3.0e38)) return 1.0 / x;
+    double y = (double)__fdividef(1.f, (float)x);
+    y = y * fma(-x, y, 2.0);
+    y = y * fma(-x, y, 2.0);
+    return y;
+}
+
 // ------------------------------------------------------------------ grid barrier
 // Software barrier across the co-resident CTAs of a cooperative launch.
 // `*count` is zero when the launch starts (the launcher's preceding kernel

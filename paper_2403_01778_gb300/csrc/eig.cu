@@ -500,6 +500,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     // mat-vec during the previous step's Ritz check (see below)
     bool pre = false;
     __shared__ int s_okg;
+    float gs2_frac = 0.25f;   // second Gram-Schmidt pass when b2 < gs2_frac * yy (set at the start)
     for (int j = 0; j < a.mmax && !done; ++j) {
         if (!pre) {
             read_vec(j, wscale, 0, kEigThreads);
@@ -573,8 +574,8 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 const double xy = hd[1], xx = hd[2], yy = hd[3];
                 const bool bad = !(xx > 0.0) || !isfinite(xx) || !isfinite(yy);
                 s_flag = bad ? 1 : 0;
-                s_sc[0] = bad ? 0.0 : xy / xx;
-                s_sc[1] = bad ? 0.0 : 1.0 / sqrt(xx);
+                s_sc[0] = bad ? 0.0 : xy * rcp_nr(xx);
+                s_sc[1] = bad ? 0.0 : rsqrt_nr(xx);
             }
             __syncthreads();
             if (s_flag) {
@@ -614,9 +615,10 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             if (!eig_sync(a, G, bar_epoch)) return;
             reduce_partials_d(pdd + (size_t)G * 4, 4, G, 1, hd + 5, rp_d);
             if (tid == 0) {
-                const double b0 = sqrt(fmax(hd[5], 0.0));
-                const double jfro = sqrt(hd[4]) * (double)a.scale;
-                const double r = (rho != 0.0) ? sqrt_d * b0 / fabs(rho) : INFINITY;
+                const double h5 = fmax(hd[5], 0.0);
+                const double b0 = h5 > 0.0 ? h5 * rsqrt_nr(h5) : 0.0;
+                const double jfro = (hd[4] > 0.0 ? hd[4] * rsqrt_nr(hd[4]) : 0.0) * (double)a.scale;
+                const double r = (rho != 0.0) ? sqrt_d * b0 * rcp_nr(fabs(rho)) : INFINITY;
                 s_sc[2] = b0;
                 s_sc[3] = r;
                 // inexact eigen steps: the Ritz tolerance follows the residual
@@ -628,7 +630,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 if (c == 0) {
                     a.scal[SC_SIGMA] = rho;
                     a.scal[SC_KKT] = r;
-                    a.scal[SC_R41] = b0 / (jfro + fabs(rho));
+                    a.scal[SC_R41] = b0 * rcp_nr(jfro + fabs(rho));
                     a.scal[SC_JFRO] = jfro;
                     a.scal[SC_CONVERGED] = 0.0;
                 }
@@ -657,6 +659,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 break;
             }
             a.eig_tol = tol_adapted;
+            gs2_frac = fminf(0.25f, __fdividef(6e-6f, (float)tol_adapted));
             if (tid == 0) {
                 alpha[0] = rho;
                 beta[0] = b0;
@@ -715,7 +718,13 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             const float h1 = hsum[j];
             float h2 = 0.f;
             bool two = false;
-            if (b2 < 0.25f * yy) {
+            // Cancellation leaves b2 = yy - ssq with an error of ~eps32 yy, so
+            // beta (and the basis' orthogonality, ~eps32 sqrt(yy / b2)) carry a
+            // relative error of ~eps32 yy / b2.  A second Gram-Schmidt pass with
+            // the exact norm is taken when that error could reach 1 % of the
+            // Ritz tolerance: yy / b2 > 4 for tight tolerances (<= 2.4e-5), up to
+            // ~170 at the loosest (1e-3) of the inexact early eigen steps.
+            if (b2 < gs2_frac * yy) {
                 // heavy cancellation: second Gram-Schmidt pass with exact norm
                 __syncthreads();
                 for (int i = warp; i < j + 2; i += kEigWarps) {
@@ -894,12 +903,11 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     __shared__ double s_xs[kMaxOrder + 1];   // [0..d-1] block factors, [d] whole-vector factor
     if (warp == 0) {
         const double sgn = (!hopm_out && bn[d] < 0.0) ? -1.0 : 1.0;   // HOPM keeps g's sign
-        if (lane < d) s_xs[lane] = bn[lane] > 0.0 ? sgn / sqrt(bn[lane]) : 0.0;
-        if (lane == 0) {
-            double tot = 0.0;
-            for (int m = 0; m < d; ++m) tot += bn[m];
-            s_xs[d] = tot > 0.0 ? sgn / sqrt(tot) : 0.0;
-        }
+        double v = 0.0;   // lanes 0..d-1: block norms^2; lane d: their sum
+        if (lane < d) v = bn[lane];
+        if (lane == d)
+            for (int m = 0; m < d; ++m) v += bn[m];
+        if (lane <= d) s_xs[lane] = v > 0.0 ? sgn * rsqrt_nr(v) : 0.0;
     }
     __syncthreads();
     for (int q = r0 + tid; q < r1; q += kEigThreads) {

@@ -422,10 +422,10 @@ static __device__ RitzOut ritz_refine_fp64(const double* alpha, const double* be
     }
     num = warp_sum_d(num);
     den = warp_sum_d(den);
-    const double inv = 1.0 / sqrt(den);
+    const double inv = rsqrt_nr(den);
     for (int i = lane; i < k; i += 32) s_out[i] = (double)sv[i] * inv;
     RitzOut ro;
-    ro.theta = num / den;
+    ro.theta = num * (inv * inv);
     ro.resid = fabs(beta_k * (double)sv[k - 1]) * inv;
     return ro;
 }

@@ -122,3 +122,30 @@ def test_timing_aid_records_the_backward_write_and_adjoint_solve():
     assert (nw, na) == (2, 1)
     assert 0.0 < wms and 0.0 < ams and wms + ams <= e0.elapsed_time(e1)
     assert pkg.hoscf_profile_read(0, pkg.PROFILE_PASS_KERNEL)[0] == 0
+
+
+def test_timing_aid_records_every_eigen_step():
+    """Kind 3: one record per eigen step - a hoscf_eig_step call, and every
+    iteration of a solve (its eigen steps), each a positive duration within
+    the calls' wall time; the pass kernels stay under kind 0."""
+    pkg = P()
+    dims = (40, 30, 50)
+    T, _ = W.planted_cp(dims, [1.0], seed=13, noise_abs=0.05)
+    Tg = T.cuda()
+    u = torch.cat(W.unit_gaussian_vectors(dims, 14)).cuda()
+    H = pkg.hoscf_ttvc_blocks(Tg, u)
+    pkg.hoscf_profile_enable(0, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pkg.hoscf_eig_step(dims, H, u.double())
+    r = pkg.hoscf_solve(Tg, u, tol=1e-6)
+    e1.record()
+    pkg.hoscf_profile_enable(0, False)
+    torch.cuda.synchronize()
+    ne, ems = pkg.hoscf_profile_read(0, pkg.PROFILE_EIG_STEP)
+    npass, _ = pkg.hoscf_profile_read(0, pkg.PROFILE_PASS_KERNEL)
+    assert r.converged
+    assert npass == r.passes
+    assert ne == 1 + r.passes     # the certificate rides on an eigen-step launch at every pass
+    assert 0.0 < ems <= e0.elapsed_time(e1)
