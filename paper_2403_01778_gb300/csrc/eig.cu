@@ -972,6 +972,60 @@ __global__ void build_jr_kernel(const float* __restrict__ H, float* __restrict__
     }
 }
 
+// The same with 64 x 64 tiles and 16-byte loads and stores, for blocks whose
+// sides are multiples of 4 (every row of H and of Jr, and every tile column
+// offset, 16-byte aligned): each thread moves four float4 in and eight out,
+// the transposed copy through a [64][65] shared tile.
+__global__ void __launch_bounds__(256) build_jr_vec4_kernel(const float* __restrict__ H,
+                                                            float* __restrict__ Jr, JrBuildArgs a,
+                                                            unsigned* bar) {
+    __shared__ float tile[64][65];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && bar) *bar = 0u;   // for the next Lanczos launch
+    const int64_t tix = blockIdx.x;
+    int b = 0;
+    while (tix >= a.tstart[b + 1]) ++b;
+    const int m = a.bm[b], nn = a.bn[b];
+    const int64_t Im = a.dims[m], In = a.dims[nn];
+    const int64_t tj_count = (In + 63) / 64;
+    const int64_t loc = tix - a.tstart[b];
+    const int64_t i0 = (loc / tj_count) * 64, j0 = (loc % tj_count) * 64;
+    const int c4 = threadIdx.x & 15, r16 = threadIdx.x >> 4;   // float4 column, row within 16
+    const float* blk = H + a.boff[b];
+    const int64_t lenm = a.n - Im, lenn = a.n - In;
+    float* dst_direct = Jr + a.jroff[m] + (a.moff[nn] - Im);
+    float* dst_trans = Jr + a.jroff[nn] + a.moff[m];
+    const int64_t jj = j0 + 4 * c4;
+    float4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t i = i0 + r16 + 16 * k;
+        v[k] = (i < Im && jj < In) ? __ldcg(reinterpret_cast<const float4*>(blk + i * In + jj))
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = r16 + 16 * k;
+        const int64_t i = i0 + r;
+        if (i < Im && jj < In) *reinterpret_cast<float4*>(dst_direct + i * lenm + jj) = v[k];
+        tile[r][4 * c4 + 0] = v[k].x;
+        tile[r][4 * c4 + 1] = v[k].y;
+        tile[r][4 * c4 + 2] = v[k].z;
+        tile[r][4 * c4 + 3] = v[k].w;
+    }
+    __syncthreads();
+    const int64_t ii = i0 + 4 * c4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = r16 + 16 * k;   // row of the transposed tile: column j0 + r of the block
+        const int64_t j = j0 + r;
+        if (j < In && ii < Im) {
+            const float4 w = make_float4(tile[4 * c4 + 0][r], tile[4 * c4 + 1][r],
+                                         tile[4 * c4 + 2][r], tile[4 * c4 + 3][r]);
+            *reinterpret_cast<float4*>(dst_trans + j * lenn + ii) = w;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- small kernels
 // Per-mode norms of u (FP64) into out[0..d-1]; one CTA.
 __global__ void mode_norms_kernel(const float* __restrict__ u, int d, ModeInfoArr mi, double* out) {
@@ -1209,6 +1263,19 @@ cudaError_t launch_build_jr(const Shape& s, const float* H, float* Jr, unsigned*
             ++b;
         }
     a.nblk = b;
+    // 16-byte path: every dimension a multiple of 4 and both buffers aligned
+    bool v4 = ((reinterpret_cast<uintptr_t>(H) | reinterpret_cast<uintptr_t>(Jr)) & 15) == 0;
+    for (int k = 0; k < s.d; ++k) v4 = v4 && s.dims[k] % 4 == 0;
+    if (v4) {
+        int64_t t4 = 0;
+        for (int q = 0; q < b; ++q) {
+            a.tstart[q] = t4;
+            t4 += ((s.dims[a.bm[q]] + 63) / 64) * ((s.dims[a.bn[q]] + 63) / 64);
+        }
+        a.tstart[b] = t4;
+        build_jr_vec4_kernel<<<(unsigned)t4, 256, 0, st>>>(H, Jr, a, bar);
+        return cudaGetLastError();
+    }
     const int64_t tiles = a.tstart[b];
     build_jr_kernel<<<(unsigned)tiles, 256, 0, st>>>(H, Jr, a, bar);
     return cudaGetLastError();

@@ -54,14 +54,15 @@ static __device__ float extreme_eig(const float* al, const float* be2, int k, fl
 // zero minor taking the sign opposite to its predecessor's (the limit of the
 // pivot form's replacement of a zero pivot by a small negative one).
 // |p_i| <= (1 + sqrt 2)^i, so nothing overflows for KM <= 32; a pair of
-// minors that falls below 2^-32 is rescaled by 2^32 at once (the recurrence
-// is homogeneous in the pair), which keeps clustered spectra, whose minors
-// shrink by a small factor per step, clear of underflow.
+// minors below 2^-32 is rescaled by 2^32 at once (the recurrence is
+// homogeneous in the pair; branch-free), which keeps clustered spectra,
+// whose minors can shrink by many orders of magnitude per step, clear of
+// underflow.
 template <int KM>
 static __device__ __forceinline__ int sturm_count_poly(const float (&a)[KM], const float (&b2)[KM],
                                                        int k, float x) {
     float pp = 1.f, pc = a[0] - x;
-    bool nc = pc < 0.f || pc == 0.f;   // p_0 > 0
+    bool nc = pc <= 0.f;   // p_0 > 0
     int c = nc ? 1 : 0;
 #pragma unroll
     for (int i = 1; i < KM; ++i) {
@@ -72,21 +73,24 @@ static __device__ __forceinline__ int sturm_count_poly(const float (&a)[KM], con
             const bool nn = pn < 0.f || (pn == 0.f && !nc);
             c += nn != nc ? 1 : 0;
             nc = nn;
-            if (fmaxf(fabsf(pp), fabsf(pc)) < 0x1p-32f) {
-                pp *= 0x1p32f;
-                pc *= 0x1p32f;
-            }
+            const float f = fmaxf(fabsf(pp), fabsf(pc)) < 0x1p-32f ? 0x1p32f : 1.f;
+            pp *= f;
+            pc *= f;
         }
     }
     return c;
 }
 
-// extreme_eig for k <= KM with sturm_count_poly: the entries are scaled by
+// Both extreme eigenvalues for k <= KM with sturm_count_poly, one full warp:
+// lanes 0-15 bracket the largest, lanes 16-31 the smallest, 16 points each
+// per round, one whole-warp ballot per round; the entries are scaled by
 // scale = 2^-e (exact) so that the Gershgorin bound is below 1, the
-// multisection runs on [-1, 1] and the result is scaled back.
+// multisection runs on [-1, 1] until both brackets are small and the result
+// (the lane's end) is scaled back.
 template <int KM>
-static __device__ float extreme_eig_poly(const float* al, const float* be2, int k, float scale,
-                                         bool want_max, int sublane, unsigned halfmask) {
+static __device__ float extreme_eig_poly(const float* al, const float* be2, int k, float scale) {
+    const int lane = threadIdx.x & 31;
+    const bool upper = lane >= 16;
     float a[KM], b2[KM];
     const float s2 = scale * scale;
 #pragma unroll
@@ -95,19 +99,21 @@ static __device__ float extreme_eig_poly(const float* al, const float* be2, int 
         b2[i] = i < k - 1 ? be2[i] * s2 : 0.f;
     }
     float lo = -1.f, hi = 1.f;
-    for (int round = 0; round < 7; ++round) {
+    for (int round = 0; round < 8; ++round) {
         const float w = (hi - lo) * (1.f / 17.f);
-        const float x = lo + w * (float)(sublane + 1);
+        const float x = lo + w * (float)((lane & 15) + 1);
         const int c = sturm_count_poly<KM>(a, b2, k, x);
-        const bool hit = want_max ? (c == k) : (c >= 1);
-        const unsigned bal = __ballot_sync(halfmask, hit);
-        const unsigned mine = (halfmask == 0xffffu) ? bal : (bal >> 16);
+        // largest: first point with every eigenvalue below it; smallest:
+        // first point with one below it
+        const bool hit = upper ? (c >= 1) : (c == k);
+        const unsigned bal = __ballot_sync(HOSCF_FULLMASK, hit);
+        const unsigned mine = upper ? (bal >> 16) : (bal & 0xffffu);
         const int first = mine ? __ffs(mine) - 1 : 16;
         const float nlo = lo + w * (float)first;
         const float nhi = (first == 16) ? hi : lo + w * (float)(first + 1);
         lo = nlo;
         hi = nhi;
-        if (hi - lo <= 4.f * 1.2e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
+        if (__all_sync(HOSCF_FULLMASK, hi - lo <= 4.f * 1.2e-7f * fmaxf(fabsf(lo), fabsf(hi)))) break;
     }
     return 0.5f * (lo + hi) / scale;
 }
@@ -338,11 +344,11 @@ static __device__ RitzOut ritz_extreme_core(int k, double beta_k, float* scratch
         frexpf(bound, &e);
         const float scale = ldexpf(1.f, -e);
         if (k <= 8)
-            ext = extreme_eig_poly<8>(al, be2, k, scale, !upper, lane & 15, hm);
+            ext = extreme_eig_poly<8>(al, be2, k, scale);
         else if (k <= 16)
-            ext = extreme_eig_poly<16>(al, be2, k, scale, !upper, lane & 15, hm);
+            ext = extreme_eig_poly<16>(al, be2, k, scale);
         else
-            ext = extreme_eig_poly<32>(al, be2, k, scale, !upper, lane & 15, hm);
+            ext = extreme_eig_poly<32>(al, be2, k, scale);
     } else {
         ext = extreme_eig(al, be2, k, -bound, bound, !upper, lane & 15, hm, pivmin);
     }
