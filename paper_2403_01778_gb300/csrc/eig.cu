@@ -343,6 +343,43 @@ __device__ void reduce_partials_d(const double* pb, int ps, int G, int cnt, doub
     __syncthreads();
 }
 
+// CTA-wide sums of NV double-float values (every thread passes its own
+// partial; every thread gets the totals in FP64 in out[0..NV), a shared
+// array): a butterfly per warp, then thread v adds the warp sums of value v
+// in warp order.  The same values give the same sums in every CTA.
+template <int NV>
+__device__ void df_block_sum(float (&h)[NV], float (&l)[NV], double* out, float* scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float bh = __shfl_xor_sync(HOSCF_FULLMASK, h[v], o);
+            const float bl = __shfl_xor_sync(HOSCF_FULLMASK, l[v], o);
+            df_add(h[v], l[v], bh);
+            l[v] += bl;
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            scratch[(2 * v) * kEigWarps + warp] = h[v];
+            scratch[(2 * v + 1) * kEigWarps + warp] = l[v];
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < NV) {
+        const int v = threadIdx.x;
+        float th = 0.f, tl = 0.f;
+        for (int w = 0; w < kEigWarps; ++w) {
+            df_add(th, tl, scratch[(2 * v) * kEigWarps + w]);
+            tl += scratch[(2 * v + 1) * kEigWarps + w];
+        }
+        out[v] = (double)th + (double)tl;
+    }
+    __syncthreads();
+}
+
 // Convergence checks of the Ritz pair: every step early on (a good warm start
 // converges in a few steps), sparser later.
 __device__ __forceinline__ bool check_now(int k) {
@@ -432,19 +469,22 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     float* pf = reinterpret_cast<float*>(a.part);
     double* pdd = a.part + (size_t)2 * G * ps;   // after the two FP32 buffers (sized in doubles)
     auto pbuf = [&]() { return pf + (size_t)(phase & 1) * G * ps; };
-    const double sqrt_d = sqrt((double)a.d);
     // the current vector is exchanged as FP32 through a ping-pong buffer in
     // global memory (the V workspace): slot (j & 1)
     float* vx = reinterpret_cast<float*>(a.V);
     auto vslot = [&](int j) { return vx + (size_t)(j & 1) * ((n + 3) & ~3); };
 
-    // ---- start vector (unnormalised), FP32
-    for (int q = r0 + tid; q < r1; q += kEigThreads) {
-        const float v = a.x0 ? (float)a.x0[q] : (float)((double)a.u0[q] / sqrt_d);
-        Vl[q - r0] = v;
-        vslot(0)[q] = v;
+    // ---- start vector (unnormalised), FP32: every CTA reads the whole input
+    // itself (no exchange), u0 / sqrt(d) when no x0 is given (only the
+    // direction matters); my rows also start the basis
+    {
+        const float rsd = rsqrtf((float)a.d);
+        for (int i = tid; i < n; i += kEigThreads) {
+            const float v = a.x0 ? (float)__ldg(a.x0 + i) : __ldg(a.u0 + i) * rsd;
+            vf[i] = v;
+            if (i >= r0 && i < r1) Vl[i - r0] = v;
+        }
     }
-    if (!eig_sync(a, G, bar_epoch)) return;
 
     int k = 0;
     // the last off-diagonal beta_k: FP32 in every thread (FP64 only where a
@@ -456,7 +496,8 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     ro.resid = 0.0;
     bool done = false;
     bool hopm_out = false;
-    float wscale = 1.0f;   // normalisation of the published vector (first Lanczos vector only)
+    bool have_vec = true;    // vf already holds the next vector (x0; v1, formed by the start)
+    double r41_b0 = 0.0, r41_rho = 0.0;   // the start's b0 and rho, for eq. 4.1's residual
     // every CTA gets the whole vector of slot (jj & 1), scaled by ws; threads
     // t0 .. t0 + nt - 1 take part
     auto read_vec = [&](int jj, float ws, int t0, int nt) {
@@ -503,8 +544,8 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     float gs2_frac = 0.25f;   // second Gram-Schmidt pass when b2 < gs2_frac * yy (set at the start)
     for (int j = 0; j < a.mmax && !done; ++j) {
         if (!pre) {
-            read_vec(j, wscale, 0, kEigThreads);
-            wscale = 1.0f;
+            if (!have_vec) read_vec(j, 1.0f, 0, kEigThreads);
+            have_vec = false;
             __syncthreads();
             if (cache)
                 matvec_rows_cached(a, vf, r0, r1, cache, crow, Yl, vec4_mv);
@@ -534,91 +575,76 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 }
                 __syncthreads();
             }
-            double sxy = 0.0, sxx = 0.0, syy = 0.0;
+            // y = J x0: every CTA publishes its rows (and its ||Jr||^2 partial)
+            // and, after one grid barrier, forms the certificate and the first
+            // Lanczos vector over the whole vector itself - in double-float,
+            // identically in every CTA, so no second exchange is needed.
+            float* ydst = vslot(1);
             for (int q = tid; q < nr; q += kEigThreads) {
-                const double x = Vl[q], y = Yl[q];
-                sxy += x * y;
-                sxx += x * x;
-                syy += y * y;
+                ydst[r0 + q] = Yl[q];
+                if (a.hopm) xrow[q] = (double)Yl[q];
             }
-            // FP64 warp sums only in the warps that hold rows (FP64 instructions
-            // cost the same with no active data)
-            const int nwr = min(kEigWarps, (nr + 31) >> 5);
-            __shared__ double red[3][kEigWarps];
-            if (warp < nwr) {
-                sxy = warp_sum_d(sxy);
-                sxx = warp_sum_d(sxx);
-                syy = warp_sum_d(syy);
-                if (lane == 0) {
-                    red[0][warp] = sxy;
-                    red[1][warp] = sxx;
-                    red[2][warp] = syy;
-                }
-            }
-            __syncthreads();
-            if (tid < 3) {
-                double t = 0.0;
-                for (int w8 = 0; w8 < nwr; ++w8) t += red[tid][w8];
-                pdd[(size_t)c * 4 + tid] = t;
-            }
-            if (tid == 3) pdd[(size_t)c * 4 + 3] = hd[0];
+            if (tid == 0) pdd[(size_t)c * 4 + 3] = hd[0];
             if (!eig_sync(a, G, bar_epoch)) return;
-            reduce_partials_d(pdd, 4, G, 4, hd + 1, rp_d);   // hd[1..4]
+            __shared__ double s_df[3];
+            __shared__ float s_dfs[6 * kEigWarps];
+            {
+                // x.y, x.x, y.y (x = x0 in vf)
+                float hh[3] = {0.f, 0.f, 0.f}, ll[3] = {0.f, 0.f, 0.f};
+                for (int i = tid; i < n; i += kEigThreads) {
+                    const float xi = vf[i], yi = __ldcg(ydst + i);
+                    df_add_prod(hh[0], ll[0], xi, yi);
+                    df_add_prod(hh[1], ll[1], xi, xi);
+                    df_add_prod(hh[2], ll[2], yi, yi);
+                }
+                df_block_sum<3>(hh, ll, s_df, s_dfs);
+            }
             // FP64 scalar work once per CTA (FP64 is a narrow pipe on this
             // part), the results broadcast through shared memory; every CTA
             // computes the same values, so every decision below is uniform
             __shared__ double s_sc[4];   // rho, 1/|x0|, b0, r
+            __shared__ float s_f[4];     // rho split hi + lo, 1/|x0|, b0 (FP32)
             __shared__ int s_flag;       // 0 go on, 1 non-finite, 2 start point certified
-            __shared__ float s_b0f;
             if (tid == 0) {
-                const double xy = hd[1], xx = hd[2], yy = hd[3];
+                const double xy = s_df[0], xx = s_df[1], yy = s_df[2];
+                hd[2] = xx;   // |x0|^2, the scale of the solve modes' result
                 const bool bad = !(xx > 0.0) || !isfinite(xx) || !isfinite(yy);
                 s_flag = bad ? 1 : 0;
-                s_sc[0] = bad ? 0.0 : xy * rcp_nr(xx);
+                const double rho = bad ? 0.0 : xy * rcp_nr(xx);
+                s_sc[0] = rho;
                 s_sc[1] = bad ? 0.0 : rsqrt_nr(xx);
+                s_f[0] = (float)rho;
+                s_f[1] = (float)(rho - (double)s_f[0]);
+                s_f[2] = (float)s_sc[1];
             }
             __syncthreads();
             if (s_flag) {
                 if (tid == 0) atomicCAS(a.err, 0, (int)DEV_NONFINITE);
                 return;
             }
-            const double rho = s_sc[0], inv = s_sc[1];
-            // ||J v0 - rho v0||^2 = (yy - xy^2/xx) / xx, evaluated as a sum of
-            // squares to avoid cancellation; in the same sweep the Lanczos start
-            // v0 = x0/|x0|, w = J v0 - rho v0 (FP32).  w is published
-            // unnormalised with the partial sums, so the norm's reduction rides
-            // on the exchange barrier of the first Lanczos vector.
-            const float finv = (float)inv, frho = (float)rho;
-            float* wdst = vslot(1);
-            double sw = 0.0;
-            for (int q = tid; q < nr; q += kEigThreads) {
-                const float yq = Yl[q], vq = Vl[q];
-                const double w = ((double)yq - rho * (double)vq) * inv;
-                sw += w * w;
-                if (a.hopm) xrow[q] = (double)yq;
-                const float v = vq * finv;
-                const float wq = yq * finv - frho * v;
-                Vl[q] = v;
-                Yl[q] = wq;
-                wdst[r0 + q] = wq;
+            const double rho = s_sc[0];
+            // w = (y - rho x) / |x0| (the two FMAs leave only the final
+            // rounding, so cancellation costs nothing) and ||w||^2, the KKT
+            // residual's sum of squares; w replaces x0 in vf, v0 = x0 / |x0|
+            // replaces my rows of x0 in the basis
+            const float rho_h = s_f[0], rho_l = s_f[1], finv = s_f[2];
+            {
+                float hh[1] = {0.f}, ll[1] = {0.f};
+                for (int i = tid; i < n; i += kEigThreads) {
+                    const float xi = vf[i], yi = __ldcg(ydst + i);
+                    const float wi = fmaf(-rho_l, xi, fmaf(-rho_h, xi, yi)) * finv;
+                    df_add_prod(hh[0], ll[0], wi, wi);
+                    vf[i] = wi;
+                }
+                for (int q = tid; q < nr; q += kEigThreads) Vl[q] *= finv;
+                df_block_sum<1>(hh, ll, s_df, s_dfs);
             }
-            if (warp < nwr) {
-                sw = warp_sum_d(sw);
-                if (lane == 0) red[0][warp] = sw;
-            }
-            __syncthreads();
+            __shared__ float s_b0f;
             if (tid == 0) {
-                double t = 0.0;
-                for (int w8 = 0; w8 < nwr; ++w8) t += red[0][w8];
-                pdd[(size_t)(G + c) * 4] = t;
-            }
-            if (!eig_sync(a, G, bar_epoch)) return;
-            reduce_partials_d(pdd + (size_t)G * 4, 4, G, 1, hd + 5, rp_d);
-            if (tid == 0) {
-                const double h5 = fmax(hd[5], 0.0);
+                const double h5 = fmax(s_df[0], 0.0);
                 const double b0 = h5 > 0.0 ? h5 * rsqrt_nr(h5) : 0.0;
-                const double jfro = (hd[4] > 0.0 ? hd[4] * rsqrt_nr(hd[4]) : 0.0) * (double)a.scale;
-                const double r = (rho != 0.0) ? sqrt_d * b0 * rcp_nr(fabs(rho)) : INFINITY;
+                const double dd = (double)a.d;
+                const double r = (rho != 0.0) ? dd * rsqrt_nr(dd) * b0 * rcp_nr(fabs(rho)) : INFINITY;
                 s_sc[2] = b0;
                 s_sc[3] = r;
                 // inexact eigen steps: the Ritz tolerance follows the residual
@@ -630,20 +656,25 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                 if (c == 0) {
                     a.scal[SC_SIGMA] = rho;
                     a.scal[SC_KKT] = r;
-                    a.scal[SC_R41] = b0 * rcp_nr(jfro + fabs(rho));
-                    a.scal[SC_JFRO] = jfro;
                     a.scal[SC_CONVERGED] = 0.0;
                 }
             }
             __syncthreads();
             const double b0 = s_sc[2], tol_adapted = s_sc[0];
+            r41_b0 = b0;
+            r41_rho = rho;
             if (s_flag == 1) {
                 if (tid == 0) atomicCAS(a.err, 0, (int)DEV_NONFINITE);
                 return;
             }
             if (s_flag == 2) {
-                // the start point is certified: no eigen step
+                // the start point is certified: no eigen step; ||J||_F for the
+                // residual of eq. 4.1 from the CTAs' partials
+                reduce_partials_d(pdd + 3, 4, G, 1, hd + 4, rp_d);
                 if (c == 0 && tid == 0) {
+                    const double jfro = (hd[4] > 0.0 ? hd[4] * rsqrt_nr(hd[4]) : 0.0) * (double)a.scale;
+                    a.scal[SC_R41] = b0 * rcp_nr(jfro + fabs(rho));
+                    a.scal[SC_JFRO] = jfro;
                     a.scal[SC_CONVERGED] = 1.0;
                     a.scal[SC_LAMBDA] = rho;
                     a.scal[SC_STEPS] = 0.0;
@@ -670,7 +701,10 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             }
             beta_last = b0;
             beta_f = s_b0f;
-            wscale = 1.0f / beta_f;   // the published w is normalised when read
+            // v1 = w / b0, whole in vf for the next mat-vec, my rows in the basis
+            const float ib = 1.0f / beta_f;
+            for (int i = tid; i < n; i += kEigThreads) vf[i] *= ib;
+            have_vec = true;
             k = 1;
         } else {
             // partial dots over my rows: h_i = V[i].y (i <= j), yy, and with a
@@ -839,10 +873,9 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             if (spec) {
                 if (!grid_wait(a.bar, G, bar_epoch, a.err, a.timeout_ns)) return;
             } else if (j == 0) {
-                // the start block published w with its norm's partial sums and
-                // passed that exchange barrier already
-                const float inv = 1.0f / beta_f;
-                for (int q = tid; q < nr; q += kEigThreads) Vl[(size_t)R + q] = Yl[q] * inv;
+                // every CTA formed the whole v1 itself (the start block)
+                __syncthreads();
+                for (int q = tid; q < nr; q += kEigThreads) Vl[(size_t)R + q] = vf[r0 + q];
             } else {
                 const float inv = 1.0f / beta_f;
                 float* dst = vslot(j + 1);
@@ -893,10 +926,12 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             for (int q = lane; q < nr; q += 32) s += xval(q) * (double)Vl[q];
         }
         s = warp_sum_d(s);
-        if (lane == 0) pdd[(size_t)8 * G + (size_t)c * (kMaxOrder + 1) + i] = s;
+        if (lane == 0) pdd[(size_t)8 * G + (size_t)c * (kMaxOrder + 2) + i] = s;
     }
+    // [d + 1]: this CTA's ||Jr||^2 (for ||J||_F in eq. 4.1's residual)
+    if (tid == 0) pdd[(size_t)8 * G + (size_t)c * (kMaxOrder + 2) + d + 1] = hd[0];
     if (!eig_sync(a, G, bar_epoch)) return;
-    reduce_partials_d(pdd + (size_t)8 * G, kMaxOrder + 1, G, d + 1, hd + 6, rp_d);
+    reduce_partials_d(pdd + (size_t)8 * G, kMaxOrder + 2, G, d + 2, hd + 6, rp_d);
     // the scale factors once per CTA (lanes of warp 0), then one multiply per
     // entry: x_out = sgn x / |x|, u_out = sgn x_n / |x_n| per block
     const double* bn = hd + 6;
@@ -916,6 +951,10 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         if (a.u_out) a.u_out[q] = (float)(x * s_xs[mode_of(a, q)]);
     }
     if (c == 0 && tid == 0) {
+        const double j2 = hd[6 + d + 1];
+        const double jfro = (j2 > 0.0 ? j2 * rsqrt_nr(j2) : 0.0) * (double)a.scale;
+        a.scal[SC_R41] = r41_b0 * rcp_nr(jfro + fabs(r41_rho));
+        a.scal[SC_JFRO] = jfro;
         a.scal[SC_LAMBDA] = ro.theta;
         a.scal[SC_STEPS] = (double)k;
         a.scal[SC_RITZRES] = ro.resid;
