@@ -186,6 +186,94 @@ static __device__ void tridiag_inverse_iteration(const float* al, const float* b
     }
 }
 
+// The same for k <= KM with every array in registers (one thread, loops
+// unrolled over KM); the result is written to s[0..k).
+template <int KM>
+static __device__ void tridiag_inverse_iteration_reg(const float* al, const float* be, int k,
+                                                     float theta, float bound, float* s_out) {
+    const float eps = fmaxf(1.2e-7f * bound, 1e-30f);
+    float wa[KM], wb[KM], wc[KM], wd[KM], s[KM];
+    unsigned piv = 0u;
+#pragma unroll
+    for (int i = 0; i < KM; ++i) {
+        wa[i] = i < k ? al[i] - theta : 1.f;
+        wb[i] = i < k - 1 ? be[i] : 0.f;
+        wc[i] = 0.f;
+        wd[i] = 0.f;
+        s[i] = 1.f;
+    }
+#pragma unroll
+    for (int i = 0; i < KM - 1; ++i) {
+        if (i < k - 1) {
+            const float sub = be[i];   // element (i+1, i)
+            if (fabsf(wa[i]) >= fabsf(sub)) {
+                const float l = (wa[i] != 0.f) ? __fdividef(sub, wa[i]) : 0.f;
+                wd[i] = l;
+                wa[i + 1] -= l * wb[i];
+            } else {
+                piv |= 1u << i;
+                const float l = __fdividef(wa[i], sub);
+                wd[i] = l;
+                const float a_ip1 = wa[i + 1];
+                wa[i] = sub;
+                const float t = wb[i];
+                wb[i] = a_ip1;
+                wa[i + 1] = t - l * a_ip1;
+                if (i + 1 < KM - 1 && i < k - 2) {
+                    wc[i] = wb[i + 1];
+                    wb[i + 1] = -l * wb[i + 1];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < KM; ++i)
+        if (i < k && fabsf(wa[i]) <= eps) wa[i] = (wa[i] < 0.f) ? -eps : eps;
+    for (int it = 0; it < 2; ++it) {
+#pragma unroll
+        for (int i = 0; i < KM - 1; ++i) {
+            if (i < k - 1) {
+                if (piv & (1u << i)) {
+                    const float t = s[i];
+                    s[i] = s[i + 1];
+                    s[i + 1] = t - wd[i] * s[i];
+                } else {
+                    s[i + 1] -= wd[i] * s[i];
+                }
+            }
+        }
+#pragma unroll
+        for (int i = KM - 1; i >= 0; --i) {
+            if (i < k) {
+                float v = s[i];
+                if (i + 1 < KM && i + 1 < k) v -= wb[i] * s[i + 1];
+                if (i + 2 < KM && i + 2 < k) v -= wc[i] * s[i + 2];
+                s[i] = __fdividef(v, wa[i]);
+                if (fabsf(s[i]) > 1e30f) {   // rescale to stay finite
+#pragma unroll
+                    for (int t = 0; t < KM; ++t)
+                        if (t >= i && t < k) s[t] *= 1e-30f;
+                }
+            }
+        }
+        float mx = 0.f;
+#pragma unroll
+        for (int i = 0; i < KM; ++i)
+            if (i < k) mx = fmaxf(mx, fabsf(s[i]));
+        if (!(mx > 0.f) || !isfinite(mx)) {
+#pragma unroll
+            for (int i = 0; i < KM; ++i) s[i] = (i == 0) ? 1.f : 0.f;
+            mx = 1.f;
+        }
+        const float inv = 1.f / mx;
+#pragma unroll
+        for (int i = 0; i < KM; ++i) s[i] *= inv;
+    }
+#pragma unroll
+    for (int i = 0; i < KM; ++i)
+        if (i < k) s_out[i] = s[i];
+}
+
 // Solution z of (T - shift I) z = e_1 for the k x k tridiagonal T (FP32,
 // partial-pivot LU as above); returns |z_k| / ||z|| and writes z / ||z|| to
 // s_out (FP64).  One thread.
@@ -378,11 +466,14 @@ static __device__ RitzOut ritz_extreme_core(int k, double beta_k, float* scratch
         return ro;
     }
     if (lane == 0) {
-        if (k == 1) {
+        if (k == 1)
             sv[0] = 1.f;
-        } else {
+        else if (poly && k <= 8)
+            tridiag_inverse_iteration_reg<8>(al, be, k, theta32, bound, sv);
+        else if (poly && k <= 16)
+            tridiag_inverse_iteration_reg<16>(al, be, k, theta32, bound, sv);
+        else
             tridiag_inverse_iteration(al, be, k, theta32, bound, sv, wa, wb, wc, wd, piv);
-        }
     }
     __syncwarp();
     float ss = 0.f;
