@@ -248,7 +248,13 @@ hoscf_status eig_launch(hoscf_handle* h, const Layout& L, const float* H, const 
     hoscf_status ps = prof_slot(h, 3, &kev);
     if (ps) return ps;
     if (kev) cudaEventRecord(kev->begin, st);
-    cudaError_t e = launch_build_jr(L.s, H, Jr, reinterpret_cast<unsigned*>(h->ws + kOffBar), st);
+    // the Lanczos kernel's epoch-tagged buffers: [2][G][pstride] dot partials
+    // over the partial region, two basis-vector slots over the V region
+    const int64_t pstride = (int64_t)L.ep.mmax + 8 + kMaxOrder;
+    cudaError_t e = launch_build_jr(
+        L.s, H, Jr, reinterpret_cast<unsigned*>(h->ws + kOffBar),
+        reinterpret_cast<unsigned long long*>(eb + L.ep.off_part), 2 * (int64_t)L.ep.G * pstride,
+        reinterpret_cast<unsigned long long*>(eb + L.ep.off_V), 2 * ((L.s.n_tot + 3) & ~(int64_t)3), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "build_jr");
     LanczosLaunch ll;
     ll.Jr = Jr;

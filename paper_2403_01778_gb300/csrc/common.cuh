@@ -232,6 +232,23 @@ __device__ __forceinline__ double rcp_nr(double x) {
     return y;
 }
 
+// Double-float accumulation (hi + lo, ~46 significant bits) with FP32
+// instructions, for sums that need more than FP32 on parts where FP64 issues
+// slowly: (hi, lo) += a by Knuth's two-sum, += x y with the product's exact
+// error from an FMA.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float a) {
+    const float s = hi + a;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (a - bb);
+    hi = s;
+}
+
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float x, float y) {
+    const float p = x * y;
+    df_add(hi, lo, p);
+    lo += fmaf(x, y, -p);
+}
+
 // ------------------------------------------------------------------ grid barrier
 // Software barrier across the co-resident CTAs of a cooperative launch.
 // `*count` is zero when the launch starts (the launcher's preceding kernel

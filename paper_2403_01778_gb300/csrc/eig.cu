@@ -380,6 +380,90 @@ __device__ void df_block_sum(float (&h)[NV], float (&l)[NV], double* out, float*
     __syncthreads();
 }
 
+// Epoch-tagged publication for the per-step exchanges of the Lanczos kernel:
+// a 32-bit value and a 32-bit epoch in one 8-byte word, written with a single
+// relaxed store, so a reader that sees the expected epoch holds the matching
+// value (one single-copy-atomic access) - the data read is the wait, and no
+// release fence or arrival counter is needed.  Epochs start at 1 in every
+// launch (the J-row build zeroes the tagged buffers before it).
+__device__ __forceinline__ void tag_put(unsigned long long* p, float v, unsigned ep) {
+    const unsigned long long w = ((unsigned long long)ep << 32) | (unsigned long long)__float_as_uint(v);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long tag_ld(const unsigned long long* p) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
+}
+
+// Wait (bounded) until each of the N words w[u] = *p[u] (already loaded
+// once) carries epoch ep; the pending ones are reloaded together, so a round
+// costs one memory latency however many are pending.  Words with null
+// pointers count as ready.  On a give-up the error word is set and false
+// returned.
+template <int N>
+__device__ __forceinline__ bool tag_wait_all(const unsigned long long* const (&p)[N],
+                                             unsigned long long (&w)[N], unsigned ep, int* err,
+                                             uint64_t limit_ns) {
+    auto pending = [&]() {
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < N; ++u) any |= p[u] && (unsigned)(w[u] >> 32) != ep;
+        return any;
+    };
+    if (!pending()) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (unsigned rounds = 1;; ++rounds) {
+#pragma unroll
+        for (int u = 0; u < N; ++u)
+            if (p[u] && (unsigned)(w[u] >> 32) != ep) w[u] = tag_ld(p[u]);
+        if (!pending()) return true;
+        if ((rounds & 15u) == 0 && (*(volatile int*)err || global_timer_ns() - t0 > limit_ns)) {
+            atomicCAS(err, 0, (int)DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// reduce_partials over epoch-tagged partials: out[i] = sum_c value of pb[c *
+// ps + i] once every one carries epoch ep (same order as reduce_partials).
+// Returns false (CTA-uniform) when a wait gave up.
+__device__ bool reduce_partials_tagged(const unsigned long long* pb, int ps, int G, int cnt,
+                                       unsigned ep, float* out, float* scratch, int* err,
+                                       uint64_t limit_ns) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool ok = true;
+    for (int i0 = 0, h = 0; i0 < cnt; i0 += 32, h ^= 1) {
+        const int i = i0 + lane;
+        float s = 0.f;
+        if (i < cnt) {
+            for (int c0 = warp; c0 < G; c0 += 16 * kEigWarps) {
+                const unsigned long long* pp[16];
+                unsigned long long w[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int c = c0 + u * kEigWarps;
+                    pp[u] = c < G ? pb + (size_t)c * ps + i : nullptr;
+                    w[u] = pp[u] ? tag_ld(pp[u]) : 0ull;
+                }
+                if (ok) ok = tag_wait_all<16>(pp, w, ep, err, limit_ns);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) s += pp[u] ? __uint_as_float((unsigned)w[u]) : 0.f;
+            }
+        }
+        float* sc = scratch + h * (kEigWarps * 32);
+        sc[warp * 32 + lane] = s;
+        __syncthreads();
+        if (warp == 0 && i < cnt) {
+            float t = sc[lane];
+            for (int w2 = 1; w2 < kEigWarps; ++w2) t += sc[w2 * 32 + lane];
+            out[i] = t;
+        }
+    }
+    return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
 // Convergence checks of the Ritz pair: every step early on (a good warm start
 // converges in a few steps), sparser later.
 __device__ __forceinline__ bool check_now(int k) {
@@ -469,10 +553,16 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     float* pf = reinterpret_cast<float*>(a.part);
     double* pdd = a.part + (size_t)2 * G * ps;   // after the two FP32 buffers (sized in doubles)
     auto pbuf = [&]() { return pf + (size_t)(phase & 1) * G * ps; };
+    // epoch-tagged per-step exchanges (see tag_put): the dot partials in two
+    // alternating [G][ps] buffers over the partial region, the basis vectors
+    // in two alternating slots over the V workspace
+    unsigned long long* const tpart = reinterpret_cast<unsigned long long*>(a.part);
+    auto tpbuf = [&]() { return tpart + (size_t)(phase & 1) * G * ps; };
+    unsigned ep_dots = 0;
     // the current vector is exchanged as FP32 through a ping-pong buffer in
     // global memory (the V workspace): slot (j & 1)
-    float* vx = reinterpret_cast<float*>(a.V);
-    auto vslot = [&](int j) { return vx + (size_t)(j & 1) * ((n + 3) & ~3); };
+    unsigned long long* const tvec = reinterpret_cast<unsigned long long*>(a.V);
+    auto tslot = [&](int j) { return tvec + (size_t)(j & 1) * ((n + 3) & ~3); };
 
     // ---- start vector (unnormalised), FP32: every CTA reads the whole input
     // itself (no exchange), u0 / sqrt(d) when no x0 is given (only the
@@ -498,55 +588,37 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     bool hopm_out = false;
     bool have_vec = true;    // vf already holds the next vector (x0; v1, formed by the start)
     double r41_b0 = 0.0, r41_rho = 0.0;   // the start's b0 and rho, for eq. 4.1's residual
-    // every CTA gets the whole vector of slot (jj & 1), scaled by ws; threads
-    // t0 .. t0 + nt - 1 take part
-    auto read_vec = [&](int jj, float ws, int t0, int nt) {
-        const float* src = vslot(jj);
+    // every CTA gets the whole basis vector v_jj (published with epoch jj)
+    // into vf; threads t0 .. t0 + nt - 1 take part, eight words in flight
+    // each; false if a wait gave up
+    auto read_vec = [&](int jj, int t0, int nt) -> bool {
+        const unsigned long long* src = tslot(jj);
         const int t = tid - t0;
-        if (vec4) {
-            const float4* s4 = reinterpret_cast<const float4*>(src);
-            float4* d4 = reinterpret_cast<float4*>(vf);
-            const int n4 = n >> 2;
-            for (int q0 = t; q0 < n4; q0 += 4 * nt) {
-                float4 tv[4];
+        bool ok = true;
+        for (int q0 = t; q0 < n; q0 += 8 * nt) {
+            const unsigned long long* pp[8];
+            unsigned long long w[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (q0 + u * nt < n4) tv[u] = __ldcg(s4 + q0 + u * nt);
-                if (ws != 1.0f) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        tv[u] = make_float4(tv[u].x * ws, tv[u].y * ws, tv[u].z * ws, tv[u].w * ws);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (q0 + u * nt < n4) d4[q0 + u * nt] = tv[u];
+            for (int u = 0; u < 8; ++u) {
+                pp[u] = q0 + u * nt < n ? src + q0 + u * nt : nullptr;
+                w[u] = pp[u] ? tag_ld(pp[u]) : 0ull;
             }
-        } else {
-            for (int q0 = t; q0 < n; q0 += 8 * nt) {
-                float tv[8];
+            if (ok) ok = tag_wait_all<8>(pp, w, (unsigned)jj, a.err, a.timeout_ns);
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (q0 + u * nt < n) tv[u] = __ldcg(src + q0 + u * nt);
-                if (ws != 1.0f) {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) tv[u] *= ws;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (q0 + u * nt < n) vf[q0 + u * nt] = tv[u];
-            }
+            for (int u = 0; u < 8; ++u)
+                if (pp[u]) vf[q0 + u * nt] = __uint_as_float((unsigned)w[u]);
         }
+        return ok;
     };
     // set when warps 1..7 already read the next vector and formed its
     // mat-vec during the previous step's Ritz check (see below)
     bool pre = false;
-    __shared__ int s_okg;
     float gs2_frac = 0.25f;   // second Gram-Schmidt pass when b2 < gs2_frac * yy (set at the start)
     for (int j = 0; j < a.mmax && !done; ++j) {
         if (!pre) {
-            if (!have_vec) read_vec(j, 1.0f, 0, kEigThreads);
+            const bool okv = have_vec ? true : read_vec(j, 0, kEigThreads);
             have_vec = false;
-            __syncthreads();
+            if (!__syncthreads_and(okv ? 1 : 0)) return;   // an exchange wait gave up
             if (cache)
                 matvec_rows_cached(a, vf, r0, r1, cache, crow, Yl, vec4_mv);
             else
@@ -579,7 +651,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             // and, after one grid barrier, forms the certificate and the first
             // Lanczos vector over the whole vector itself - in double-float,
             // identically in every CTA, so no second exchange is needed.
-            float* ydst = vslot(1);
+            float* ydst = reinterpret_cast<float*>(a.Y);
             for (int q = tid; q < nr; q += kEigThreads) {
                 ydst[r0 + q] = Yl[q];
                 if (a.hopm) xrow[q] = (double)Yl[q];
@@ -724,10 +796,11 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                     for (int q = lo + lane; q < hi; q += 32) s = fmaf(a.proj_u[q], Yl[q - r0], s);
                 }
                 s = warp_sum(s);
-                if (lane == 0) pbuf()[(size_t)c * ps + i] = s;
+                if (lane == 0) tag_put(tpbuf() + (size_t)c * ps + i, s, ep_dots + 1);
             }
-            if (!eig_sync(a, G, bar_epoch)) return;
-            reduce_partials<float>(pbuf(), ps, G, cnt, hsum, rp_f);
+            ++ep_dots;
+            if (!reduce_partials_tagged(tpbuf(), ps, G, cnt, ep_dots, hsum, rp_f, a.err, a.timeout_ns))
+                return;
             ++phase;
             if (nproj) {
                 float mu2 = 0.f;
@@ -769,10 +842,12 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                         for (int q = lane; q < nr; q += 32) s = fmaf(Yl[q], Yl[q], s);
                     }
                     s = warp_sum(s);
-                    if (lane == 0) pbuf()[(size_t)c * ps + i] = s;
+                    if (lane == 0) tag_put(tpbuf() + (size_t)c * ps + i, s, ep_dots + 1);
                 }
-                if (!eig_sync(a, G, bar_epoch)) return;
-                reduce_partials<float>(pbuf(), ps, G, j + 2, hsum, rp_f);
+                ++ep_dots;
+                if (!reduce_partials_tagged(tpbuf(), ps, G, j + 2, ep_dots, hsum, rp_f, a.err,
+                                            a.timeout_ns))
+                    return;
                 ++phase;
                 float ssq2 = 0.f;
                 for (int i = 0; i <= j; ++i) ssq2 = fmaf(hsum[i], hsum[i], ssq2);
@@ -800,27 +875,26 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
         // convergence test on the largest-magnitude Ritz pair
         const bool last = (k == a.mmax) || (k == n) || !(beta_f > 1e-30f);
         const bool chk = check_now(k) || last;
-        // On a check step of a multi-CTA eigen step, the next basis vector is
-        // published and the exchange barrier entered before the check, so the
+        // The next basis vector goes out (epoch-tagged) before a check, so the
         // check (one warp, identical in every CTA) overlaps the other CTAs'
-        // arrivals; if it stops the iteration, every CTA leaves without waiting.
-        const bool spec = chk && !last && G > 1 && !a.rqi;
-        // with the rows cached, the check (warp 0) also overlaps the next
-        // step's exchange wait, vector read and mat-vec (warps 1..7)
-        const bool ovl = spec && k >= 2 && cache != nullptr;
-        if (spec) {
+        // progress; with the rows cached, warps 1..7 meanwhile read the next
+        // vector and form its mat-vec (kept unless the check stops).
+        const bool pub_early = chk && !last && !a.rqi;
+        const bool ovl = pub_early && k >= 2 && cache != nullptr;
+        auto publish = [&]() {
             const float inv = 1.0f / beta_f;
-            float* dst = vslot(j + 1);
+            unsigned long long* dst = tslot(j + 1);
             for (int q = tid; q < nr; q += kEigThreads) {
                 const float v = Yl[q] * inv;
                 Vl[(size_t)(j + 1) * R + q] = v;
-                dst[r0 + q] = v;
+                tag_put(dst + r0 + q, v, (unsigned)(j + 1));
             }
-            grid_arrive(a.bar, bar_epoch);
-        }
+        };
+        if (pub_early) publish();
         if (chk) {
             __shared__ RitzOut s_ro;
             __shared__ int s_acc;
+            bool okx = true;
             if (a.rqi) {
                 if (tid == 0) {
                     float* w = rscratch;
@@ -843,21 +917,16 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
                         s_acc = acc ? 1 : 0;
                     }
                 } else if (ovl) {
-                    // meanwhile warps 1..7 wait for the exchange, read the next
-                    // vector and form its mat-vec (discarded if the check stops)
-                    if (grid_wait_group(a.bar, G, bar_epoch, a.err, a.timeout_ns, 32, 2,
-                                        kEigThreads - 32, &s_okg)) {
-                        read_vec(j + 1, 1.0f, 32, kEigThreads - 32);
-                        asm volatile("bar.sync 2, %0;" ::"r"(kEigThreads - 32) : "memory");
-                        matvec_rows_cached(a, vf, r0, r1, cache, crow, Yl, vec4_mv, 1, kEigWarps - 1);
-                    }
+                    okx = read_vec(j + 1, 32, kEigThreads - 32);
+                    asm volatile("bar.sync 2, %0;" ::"r"(kEigThreads - 32) : "memory");
+                    matvec_rows_cached(a, vf, r0, r1, cache, crow, Yl, vec4_mv, 1, kEigWarps - 1);
                 }
             } else if (tid == 0) {
                 sv[0] = 1.0;
                 s_ro.theta = alpha[0];
                 s_ro.resid = beta_last;
             }
-            __syncthreads();
+            if (!__syncthreads_and(okx ? 1 : 0)) return;   // an exchange wait gave up
             ro = s_ro;
             if (!a.rqi && k >= 2) {
                 if (s_acc) done = true;
@@ -867,24 +936,14 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             }
         }
         if (ovl) {
-            if (!s_okg) return;   // the exchange wait gave up (the code is in the status word)
             pre = !done;
-        } else if (!done) {
-            if (spec) {
-                if (!grid_wait(a.bar, G, bar_epoch, a.err, a.timeout_ns)) return;
-            } else if (j == 0) {
+        } else if (!done && !pub_early) {
+            if (j == 0) {
                 // every CTA formed the whole v1 itself (the start block)
                 __syncthreads();
                 for (int q = tid; q < nr; q += kEigThreads) Vl[(size_t)R + q] = vf[r0 + q];
             } else {
-                const float inv = 1.0f / beta_f;
-                float* dst = vslot(j + 1);
-                for (int q = tid; q < nr; q += kEigThreads) {
-                    const float v = Yl[q] * inv;
-                    Vl[(size_t)(j + 1) * R + q] = v;
-                    dst[r0 + q] = v;
-                }
-                if (!eig_sync(a, G, bar_epoch)) return;
+                publish();   // the next read waits for it
             }
         }
     }
@@ -974,12 +1033,26 @@ struct JrBuildArgs {
     int64_t boff[kMaxBlocks + 1];
     int bm[kMaxBlocks], bn[kMaxBlocks];
     int64_t tstart[kMaxBlocks + 1];   // tile prefix
+    // the Lanczos kernel's epoch-tagged exchange buffers, cleared for the
+    // launch that follows (epochs start at 1)
+    unsigned long long* z0;
+    int64_t nz0;
+    unsigned long long* z1;
+    int64_t nz1;
 };
+
+__device__ __forceinline__ void clear_tagged(const JrBuildArgs& a) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = t; i < a.nz0; i += nt) a.z0[i] = 0ull;
+    for (int64_t i = t; i < a.nz1; i += nt) a.z1[i] = 0ull;
+}
 
 __global__ void build_jr_kernel(const float* __restrict__ H, float* __restrict__ Jr, JrBuildArgs a,
                                 unsigned* bar) {
     __shared__ float tile[32][33];
     if (blockIdx.x == 0 && threadIdx.x == 0 && bar) *bar = 0u;   // for the next Lanczos launch
+    clear_tagged(a);
     const int64_t tix = blockIdx.x;
     int b = 0;
     while (tix >= a.tstart[b + 1]) ++b;
@@ -1020,6 +1093,7 @@ __global__ void __launch_bounds__(256) build_jr_vec4_kernel(const float* __restr
                                                             unsigned* bar) {
     __shared__ float tile[64][65];
     if (blockIdx.x == 0 && threadIdx.x == 0 && bar) *bar = 0u;   // for the next Lanczos launch
+    clear_tagged(a);
     const int64_t tix = blockIdx.x;
     int b = 0;
     while (tix >= a.tstart[b + 1]) ++b;
@@ -1270,7 +1344,9 @@ bool make_eig_plan(const Shape& s, int nsm, int blocks_per_sm, int mmax, EigPlan
         return o;
     };
     e.off_jr = take(sizeof(float) * 2 * (size_t)s.P);
-    e.off_V = take(sizeof(double) * (size_t)(mmax + 1) * s.n_tot);
+    // the basis workspace also holds the two epoch-tagged vector slots
+    e.off_V = take(sizeof(double) * std::max((size_t)(mmax + 1) * s.n_tot,
+                                             (size_t)2 * ((s.n_tot + 3) & ~(int64_t)3)));
     e.off_Y = take(sizeof(double) * (size_t)s.n_tot);
     e.off_part = take(sizeof(double) * 2 * (size_t)e.G * (mmax + 8 + kMaxOrder) +
                       sizeof(double) * 40 * (size_t)e.G);
@@ -1284,9 +1360,14 @@ static void jr_offsets(const Shape& s, int64_t* jroff) {
 }
 
 cudaError_t launch_build_jr(const Shape& s, const float* H, float* Jr, unsigned* bar,
-                            cudaStream_t st) {
+                            unsigned long long* zero0, int64_t nzero0, unsigned long long* zero1,
+                            int64_t nzero1, cudaStream_t st) {
     JrBuildArgs a;
     memset(&a, 0, sizeof(a));
+    a.z0 = zero0;
+    a.nz0 = nzero0;
+    a.z1 = zero1;
+    a.nz1 = nzero1;
     a.d = s.d;
     a.n = s.n_tot;
     for (int k = 0; k < s.d; ++k) a.dims[k] = s.dims[k];

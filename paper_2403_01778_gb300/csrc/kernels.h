@@ -131,10 +131,12 @@ enum EigScal {
 };
 
 int lanczos_blocks_per_sm(int64_t n_tot);
-// Also zeroes the grid-barrier counter `bar` of the Lanczos launch that
-// follows on the same stream.
+// Also zeroes the grid-barrier counter `bar` and the nzero0 / nzero1 words
+// of the epoch-tagged exchange buffers of the Lanczos launch that follows on
+// the same stream.
 cudaError_t launch_build_jr(const Shape& s, const float* H, float* Jr, unsigned* bar,
-                            cudaStream_t st);
+                            unsigned long long* zero0, int64_t nzero0, unsigned long long* zero1,
+                            int64_t nzero1, cudaStream_t st);
 cudaError_t launch_lanczos(const Shape& s, const LanczosLaunch& l, cudaStream_t st);
 cudaError_t launch_mode_norms(const Shape& s, const float* u, double* out, cudaStream_t st);
 cudaError_t launch_scale_modes(const Shape& s, const float* u, const double* nrm2, float* out,

@@ -1353,6 +1353,13 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
     // for d == 3 these are H_{0,1} and H_{0,2} themselves
     float* y1 = s.d == 3 ? H + s.boff[block_index(3, 0, 1)] : reinterpret_cast<float*>(ws + p.off_y1);
     float* y2 = s.d == 3 ? H + s.boff[block_index(3, 0, 2)] : reinterpret_cast<float*>(ws + p.off_y2);
+    // for d >= 4 a single partial (one column tile for y1, one row band for
+    // y2) already is the sum, in the same [O][A] / [O][B] layout: the folds
+    // read it in place instead of a copy
+    const bool y1_direct = s.d > 3 && p.TB == 1;
+    const bool y2_direct = s.d > 3 && p.TA == 1;
+    if (y1_direct) y1 = a.y1p;
+    if (y2_direct) y2 = a.y2p;
     {
         ReduceArgs ra;
         ra.hp = a.hp;
@@ -1368,11 +1375,11 @@ hoscf_status run_ttvc(const Shape& s, const PassPlan& p, int dtype, const void* 
         ra.FB = p.FB;
         ra.y1p = a.y1p;
         ra.y1 = y1;
-        ra.n1 = s.O * s.A;
+        ra.n1 = y1_direct ? 0 : s.O * s.A;
         ra.np1 = p.TB;
         ra.y2p = a.y2p;
         ra.y2 = y2;
-        ra.n2 = s.O * s.B;
+        ra.n2 = y2_direct ? 0 : s.O * s.B;
         ra.np2 = p.TA;
         const int64_t units = p.TT * p.FA * (p.FB / 128) + (ra.n1 + 127) / 128 + (ra.n2 + 127) / 128;
         const int64_t g = std::min<int64_t>((units + 1) / 2, 16 * (int64_t)std::max(1, p.nsm));
