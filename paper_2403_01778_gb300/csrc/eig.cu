@@ -134,12 +134,14 @@ __device__ void matvec_rows(const EigArgs& a, const float* __restrict__ vf, int 
 
 // Copies this CTA's rows of Jr into the shared-memory cache (rows of one mode
 // are contiguous in Jr and in the cache, so each mode segment is one block
-// copy), all threads with four independent loads in flight, and adds the
-// squared entries to *sq (FP32 per thread, FP64 per CTA: ||Jr||_F^2).
+// copy).  Where source and destination share their 16-byte phase the middle
+// goes by cp.async (16 bytes, no register round trip, every copy of the
+// thread in flight at once) and is NOT waited for here: the caller overlaps
+// other loads, then calls fill_cache_wait.  Elsewhere the copy is done with
+// register loads, 16 in flight per thread.
 __device__ void fill_cache_rows(const EigArgs& a, int r0, int r1, float* cache,
-                                const int64_t* crow, double* sq) {
+                                const int64_t* crow) {
     constexpr int T = kEigThreads;
-    float s2a = 0.f, s2b = 0.f;
     for (int q = r0; q < r1;) {
         const int m = mode_of(a, q);
         const int qe = min(r1, (int)a.moff[m + 1]);
@@ -147,45 +149,54 @@ __device__ void fill_cache_rows(const EigArgs& a, int r0, int r1, float* cache,
         const float* __restrict__ src = a.Jr + a.jroff[m] + (int64_t)(q - a.moff[m]) * len;
         float* dst = cache + crow[q - r0];
         const int64_t cnt = (int64_t)(qe - q) * len;
-        // scalar head up to a 16-byte boundary of the source, 16-byte loads for
-        // the middle (the cache side keeps scalar stores: its alignment differs)
+        // scalar head up to a 16-byte boundary of the source, 16-byte copies
+        // for the middle, scalar tail
         const int64_t head = min(cnt, (int64_t)((16 - (reinterpret_cast<uintptr_t>(src) & 15)) & 15) / 4);
         const int64_t nv = (cnt - head) / 4;
-        for (int64_t i = threadIdx.x; i < head; i += T) {
-            const float h = __ldcg(src + i);
-            dst[i] = h;
-            s2a = fmaf(h, h, s2a);
-        }
+        for (int64_t i = threadIdx.x; i < head; i += T) dst[i] = __ldcg(src + i);
         const float4* __restrict__ src4 = reinterpret_cast<const float4*>(src + head);
         float* d4 = dst + head;
-        // batches of kFillBatch loads per thread, all issued before the stores
-        // (the fill is bound by L2 latency, not bandwidth)
-        constexpr int kFillBatch = 16;
-        for (int64_t v0 = threadIdx.x; v0 < nv; v0 += kFillBatch * T) {
-            float4 h[kFillBatch];
+        if ((reinterpret_cast<uintptr_t>(d4) & 15) == 0) {
+            for (int64_t v = threadIdx.x; v < nv; v += T) cp_async<16>(d4 + 4 * v, src4 + v, true);
+        } else {
+            constexpr int kFillBatch = 16;
+            for (int64_t v0 = threadIdx.x; v0 < nv; v0 += kFillBatch * T) {
+                float4 h[kFillBatch];
 #pragma unroll
-            for (int t = 0; t < kFillBatch; ++t)
-                if (v0 + t * T < nv) h[t] = __ldcg(src4 + v0 + t * T);
+                for (int t = 0; t < kFillBatch; ++t)
+                    if (v0 + t * T < nv) h[t] = __ldcg(src4 + v0 + t * T);
 #pragma unroll
-            for (int t = 0; t < kFillBatch; ++t) {
-                if (v0 + t * T < nv) {
-                    float* o = d4 + 4 * (v0 + t * T);
-                    o[0] = h[t].x;
-                    o[1] = h[t].y;
-                    o[2] = h[t].z;
-                    o[3] = h[t].w;
-                    s2a = fmaf(h[t].x, h[t].x, fmaf(h[t].y, h[t].y, s2a));
-                    s2b = fmaf(h[t].z, h[t].z, fmaf(h[t].w, h[t].w, s2b));
+                for (int t = 0; t < kFillBatch; ++t) {
+                    if (v0 + t * T < nv) {
+                        float* o = d4 + 4 * (v0 + t * T);
+                        o[0] = h[t].x;
+                        o[1] = h[t].y;
+                        o[2] = h[t].z;
+                        o[3] = h[t].w;
+                    }
                 }
             }
         }
-        for (int64_t i = head + 4 * nv + threadIdx.x; i < cnt; i += T) {
-            const float h = __ldcg(src + i);
-            dst[i] = h;
-            s2a = fmaf(h, h, s2a);
-        }
+        for (int64_t i = head + 4 * nv + threadIdx.x; i < cnt; i += T) dst[i] = __ldcg(src + i);
         q = qe;
     }
+}
+
+// Waits for the fill's copies, then adds the squared cached entries of this
+// CTA (nfl floats from the cache start, 16-byte aligned) to *sq (FP32 per
+// thread, FP64 per CTA: ||Jr||_F^2).
+__device__ void fill_cache_wait(const float* cache, int64_t nfl, double* sq) {
+    cp_async_wait_all();
+    __syncthreads();
+    float s2a = 0.f, s2b = 0.f;
+    const float4* c4 = reinterpret_cast<const float4*>(cache);
+    const int64_t n4 = (reinterpret_cast<uintptr_t>(cache) & 15) == 0 ? nfl / 4 : 0;
+    for (int64_t v = threadIdx.x; v < n4; v += kEigThreads) {
+        const float4 h = c4[v];
+        s2a = fmaf(h.x, h.x, fmaf(h.y, h.y, s2a));
+        s2b = fmaf(h.z, h.z, fmaf(h.w, h.w, s2b));
+    }
+    for (int64_t i = 4 * n4 + threadIdx.x; i < nfl; i += kEigThreads) s2a = fmaf(cache[i], cache[i], s2a);
     const float s2 = warp_sum(s2a + s2b);
     if ((threadIdx.x & 31) == 0) atomicAdd(sq, (double)s2);   // shared-memory scratch, per CTA
     __syncthreads();
@@ -541,7 +552,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
     // 16-byte mat-vec loads pay off on long rows only (>= 8 per lane); on
     // short ones the ragged lane split costs more than they save
     const bool vec4_mv = vec4 && min_len >= 1024;
-    if (cache) fill_cache_rows(a, r0, r1, cache, crow, &hd[0]);
+    if (cache) fill_cache_rows(a, r0, r1, cache, crow);   // completed below, after the start vector
     __shared__ double s_znorm;   // |z| of the last tridiagonal solve (solve modes)
     __shared__ double s_rp[2 * kEigWarps * 32];   // cross-warp sums of reduce_partials
     double* const rp_d = s_rp;
@@ -575,6 +586,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) lanczos_kernel(EigArgs a) {
             if (i >= r0 && i < r1) Vl[i - r0] = v;
         }
     }
+    if (cache) fill_cache_wait(cache, crow[nr], &hd[0]);
 
     int k = 0;
     // the last off-diagonal beta_k: FP32 in every thread (FP64 only where a
