@@ -11,7 +11,8 @@
 // Lanczos runs as one cooperative kernel over G CTAs: rows are split across
 // CTAs, every step does one mat-vec and one full (classical Gram-Schmidt)
 // reorthogonalisation against the whole basis (FP32 rows kept by each CTA),
-// with two grid barriers.
+// with two exchanges between CTAs (the dot products' partials, the next
+// basis vector), both as epoch-tagged words whose reads are the waits.
 // Scalars (dot products, the tridiagonal matrix, Ritz values) are reduced in
 // a fixed order and recomputed identically by every CTA, so all CTAs take the
 // same decisions without another barrier.
@@ -38,9 +39,10 @@ struct EigArgs {
     float scale;            // 1 / (d - 1)
     const double* x0;       // start vector (n), or NULL: start = u0 / sqrt(d)
     const float* u0;
-    double* V;              // (mmax + 1) x n
-    double* Y;              // n
-    double* part;           // 2 x G x pstride (two alternating reduction buffers)
+    double* V;              // workspace: the two epoch-tagged basis-vector slots
+    double* Y;              // n: the start's exchange of y = J x0 (as floats)
+    double* part;           // [2][G][pstride] epoch-tagged dot partials, then the
+                            // FP64 partials of the certificate and the final sums
     int pstride;
     double* scal;           // outputs (see EigScal)
     double* x_out;          // n or NULL

@@ -25,24 +25,29 @@ static __device__ __forceinline__ int sturm_count(const float* al, const float* 
     return c;
 }
 
-// Largest (want_max) or smallest eigenvalue by 16-way multisection on one
-// half-warp.  Returns the midpoint of the final bracket.
+// Both extreme eigenvalues by multisection with the pivot-form Sturm count,
+// one full warp: lanes 0-15 bracket the largest, lanes 16-31 the smallest,
+// 16 points each per round, one whole-warp ballot per round, until both
+// brackets are small.  Returns the midpoint of the lane's final bracket.
 static __device__ float extreme_eig(const float* al, const float* be2, int k, float lo, float hi,
-                             bool want_max, int sublane, unsigned halfmask, float pivmin) {
+                                    float pivmin) {
+    const int lane = threadIdx.x & 31;
+    const bool upper = lane >= 16;
     for (int round = 0; round < 7; ++round) {
-        const float x = lo + (hi - lo) * (float)(sublane + 1) / 17.f;
+        const float w = (hi - lo) * (1.f / 17.f);
+        const float x = lo + w * (float)((lane & 15) + 1);
         const int c = sturm_count(al, be2, k, x, pivmin);
-        // want_max: first shift with all k eigenvalues below it
-        const bool hit = want_max ? (c == k) : (c >= 1);
-        const unsigned bal = __ballot_sync(halfmask, hit);
-        const unsigned mine = (halfmask == 0xffffu) ? bal : (bal >> 16);
-        const int first = mine ? __ffs(mine) - 1 : 16;   // first hit shift index
-        const float w = (hi - lo) / 17.f;
+        // largest: first point with all k eigenvalues below it; smallest:
+        // first point with one below it
+        const bool hit = upper ? (c >= 1) : (c == k);
+        const unsigned bal = __ballot_sync(HOSCF_FULLMASK, hit);
+        const unsigned mine = upper ? (bal >> 16) : (bal & 0xffffu);
+        const int first = mine ? __ffs(mine) - 1 : 16;
         const float nlo = lo + w * (float)first;
         const float nhi = (first == 16) ? hi : lo + w * (float)(first + 1);
         lo = nlo;
         hi = nhi;
-        if (hi - lo <= 4.f * 1.2e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
+        if (__all_sync(HOSCF_FULLMASK, hi - lo <= 4.f * 1.2e-7f * fmaxf(fabsf(lo), fabsf(hi)))) break;
     }
     return 0.5f * (lo + hi);
 }
@@ -420,9 +425,7 @@ static __device__ RitzOut ritz_extreme_core(int k, double beta_k, float* scratch
     for (int o = 16; o > 0; o >>= 1) bound = fmaxf(bound, __shfl_xor_sync(HOSCF_FULLMASK, bound, o));
     bound = bound * 1.0001f + 1e-30f;
     const float pivmin = fmaxf(bound * 1e-30f, 1e-35f);
-    // half-warp 0: largest eigenvalue, half-warp 1: smallest
-    const bool upper = lane >= 16;
-    const unsigned hm = upper ? 0xffff0000u : 0x0000ffffu;
+    // lanes 0-15: largest eigenvalue, lanes 16-31: smallest
     float ext;
     if (k == 1) {
         ext = al[0];
@@ -438,7 +441,7 @@ static __device__ RitzOut ritz_extreme_core(int k, double beta_k, float* scratch
         else
             ext = extreme_eig_poly<32>(al, be2, k, scale);
     } else {
-        ext = extreme_eig(al, be2, k, -bound, bound, !upper, lane & 15, hm, pivmin);
+        ext = extreme_eig(al, be2, k, -bound, bound, pivmin);
     }
     const float tmax = __shfl_sync(HOSCF_FULLMASK, ext, 0);
     const float tmin = __shfl_sync(HOSCF_FULLMASK, ext, 16);
