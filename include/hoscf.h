@@ -212,9 +212,9 @@ hoscf_status hoscf_rqi_step(hoscf_handle* h, int order, const int64_t* dims, con
  * point with r = ||g - sigma u||_2 / |sigma| (g_n = A x_{k!=n} u^(k) from the
  * blocks, sigma = mean_n <u_n, g_n>; the KKT system 2.4) and stops there when
  * r <= tol; otherwise it takes the eigen step.  With opts->refine set, passes
- * run on T until r <= switch_tol, r stops decreasing, or r * (r / r_prev)
- * <= switch_tol (the next iterate is predicted to reach it), and on
- * `refine` (FP32) afterwards.
+ * run on T until r <= switch_tol, r sets no new low for 64 iterations (or
+ * half of max_iter is spent), or r * (r / r_prev) <= switch_tol (the next
+ * iterate is predicted to reach it), and on `refine` (FP32) afterwards.
  * Synchronous: returns when the outputs are final.  NOT_CONVERGED after
  * max_iter (outputs = last certified iterate), NONFINITE, TIMEOUT, EINVAL,
  * ENOMEM, ECUDA; EUNSUPPORTED for the ASVD variant on orders above 3.

@@ -612,6 +612,9 @@ static hoscf_status solve_core(hoscf_handle* h, const hoscf_tensor_desc* T, cons
     int iters = 0, passes = 0, passes_ref = 0, accepts = 0;
     double sigma = 0.0, resid = INFINITY, r41 = NAN;
     bool use_ref = false;
+    double lo_min = INFINITY;   // precision form: lowest residual so far and
+    int since_min = 0;          // the iterations since it was reached
+    constexpr int kStallIters = 64;
     hoscf_status result = HOSCF_NOT_CONVERGED;
     // three factor buffers (current point, eigen step, RQI candidate) and two
     // block buffers, so a rejected RQI step never costs a repeated pass
@@ -702,8 +705,18 @@ static hoscf_status solve_core(hoscf_handle* h, const hoscf_tensor_desc* T, cons
         // once more) - so that the pass at that iterate is already an FP32
         // pass.  The low-precision certificate itself has no floor (it
         // certifies the low-precision tensor, whose fixed point the iteration
-        // approaches), so a slow but steady decrease is progress, not a floor.
-        const bool stalled = Tr && !use_ref && iters > 0 && !(resid < prev_resid);
+        // approaches), so a slow decrease is progress, not a floor; the KKT
+        // residual need not fall monotonically either (slowly converging
+        // problems show humps of tens of iterations), so "stops decreasing"
+        // means no new lowest residual for kStallIters iterations - or half
+        // of max_iter spent, so that the FP32 passes keep their share.
+        if (resid < lo_min) {
+            lo_min = resid;
+            since_min = 0;
+        } else {
+            ++since_min;
+        }
+        const bool stalled = Tr && !use_ref && (since_min >= kStallIters || 2 * iters >= o.max_iter);
         const bool predicted = Tr && !use_ref && iters > 0 && prev_resid > 0.0 &&
                                std::isfinite(prev_resid) && resid * (resid / prev_resid) <= o.switch_tol;
         prev_resid = resid;
