@@ -95,6 +95,12 @@ typedef struct {
     int batch_faces;           /* hoscf_solve_batched: at most this many faces (T[o][:][:],
                                   o over the leading modes) staged and folded per group,
                                   1 .. 32 (0 = 32); chosen by the autotuner */
+    int switch_predict;        /* precision form: move to `refine` one pass early when the
+                                  next residual is predicted to reach switch_tol from
+                                  1 (default): the last contraction r_k / r_{k-1} - suits
+                                  problems whose first steps show their rate; 2: the
+                                  slower of the last two - suits a fast first step
+                                  followed by a slow tail; 0: no prediction */
 } hoscf_opts;
 
 typedef struct {
@@ -113,7 +119,7 @@ hoscf_status hoscf_destroy(hoscf_handle* h);
 const char* hoscf_last_error(const hoscf_handle* h);
 
 /* Defaults: tol 1e-6, max_iter 200, HOSCF, eig_tol 1e-10, eig_max_steps 64,
- * eig_adapt 1e-3, refine NULL, switch_tol 1e-3, timeout 2 s. */
+ * eig_adapt 1e-3, refine NULL, switch_tol 1e-3, timeout 2 s, switch_predict 1. */
 hoscf_status hoscf_opts_default(hoscf_opts* opts);
 
 /* Bytes of handle workspace a solve of this shape and dtype needs (host args). */
@@ -213,8 +219,8 @@ hoscf_status hoscf_rqi_step(hoscf_handle* h, int order, const int64_t* dims, con
  * blocks, sigma = mean_n <u_n, g_n>; the KKT system 2.4) and stops there when
  * r <= tol; otherwise it takes the eigen step.  With opts->refine set, passes
  * run on T until r <= switch_tol, r sets no new low for 64 iterations (or
- * half of max_iter is spent), or r * (r / r_prev) <= switch_tol (the next
- * iterate is predicted to reach it), and on `refine` (FP32) afterwards.
+ * half of max_iter is spent), or the next iterate is predicted to reach
+ * switch_tol (opts->switch_predict), and on `refine` (FP32) afterwards.
  * Synchronous: returns when the outputs are final.  NOT_CONVERGED after
  * max_iter (outputs = last certified iterate), NONFINITE, TIMEOUT, EINVAL,
  * ENOMEM, ECUDA; EUNSUPPORTED for the ASVD variant on orders above 3.

@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int), ("variant", c_int),
                 ("eig_tol", c_double), ("eig_max_steps", c_int), ("eig_adapt", c_double),
                 ("refine", ctypes.POINTER(TensorDesc)), ("switch_tol", c_double),
-                ("timeout_ns", c_int64), ("batch_threads", c_int), ("batch_faces", c_int)]
+                ("timeout_ns", c_int64), ("batch_threads", c_int), ("batch_faces", c_int),
+                ("switch_predict", c_int)]
 
 
 # int reduce(float* H, int64_t count, void* stream, void* user)

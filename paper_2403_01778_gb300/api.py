@@ -188,8 +188,11 @@ def hoscf_ttvc_blocks_static(T: torch.Tensor, u: torch.Tensor, H: torch.Tensor |
 
 
 def _opts(tol=None, max_iter=None, variant=None, eig_tol=None, eig_max_steps=None,
-          refine_desc=None, switch_tol=None, timeout_ns=None, eig_adapt=None) -> Opts:
+          refine_desc=None, switch_tol=None, timeout_ns=None, eig_adapt=None,
+          switch_predict=None) -> Opts:
     o = hoscf_opts_default()
+    if switch_predict is not None:
+        o.switch_predict = int(switch_predict)
     if eig_adapt is not None:
         o.eig_adapt = float(eig_adapt)
     if tol is not None:
@@ -283,7 +286,7 @@ class SolveResult:
 def hoscf_solve(T: torch.Tensor, u0: torch.Tensor, tol=1e-6, max_iter=200, variant="hoscf",
                 eig_tol=None, eig_max_steps=None, scales=None, refine: torch.Tensor | None = None,
                 switch_tol=None, timeout_ns=None, u_out: torch.Tensor | None = None,
-                eig_adapt=None, refine_scales=None, stream=None) -> SolveResult:
+                eig_adapt=None, refine_scales=None, stream=None, switch_predict=None) -> SolveResult:
     """HOSCF / iHOSCF (Algorithm 1, Sec. 4.4).  Synchronous."""
     d = _Desc(T, scales)
     u0 = u0.contiguous()
@@ -292,7 +295,7 @@ def hoscf_solve(T: torch.Tensor, u0: torch.Tensor, tol=1e-6, max_iter=200, varia
         raise ValueError("u0 must be float32 with sum(dims) entries")
     rd = _Desc(refine) if refine is not None else None
     o = _opts(tol, max_iter, variant, eig_tol, eig_max_steps,
-              rd.desc if rd is not None else None, switch_tol, timeout_ns, eig_adapt)
+              rd.desc if rd is not None else None, switch_tol, timeout_ns, eig_adapt, switch_predict)
     if u_out is None:
         u_out = torch.empty(n, device=T.device, dtype=torch.float32)
     sigma = ctypes.c_double()

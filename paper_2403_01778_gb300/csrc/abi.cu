@@ -371,6 +371,7 @@ hoscf_status hoscf_opts_default(hoscf_opts* o) {
     o->eig_adapt = 1e-3;
     o->refine = nullptr;
     o->switch_tol = 1e-3;
+    o->switch_predict = 1;
     o->timeout_ns = 2000000000;   // 2 s per bounded device wait
     o->batch_threads = 0;
     o->batch_faces = 0;
@@ -689,7 +690,7 @@ static hoscf_status solve_core(hoscf_handle* h, const hoscf_tensor_desc* T, cons
     };
 
     double sc[SC_COUNT], sk[SC_COUNT], sy[SC_COUNT];
-    double prev_resid = INFINITY;
+    double prev_resid = INFINITY, prev2_resid = INFINITY;
     st = do_pass(ucur, Hcur);
     if (st) return st;
     while (true) {
@@ -717,8 +718,18 @@ static hoscf_status solve_core(hoscf_handle* h, const hoscf_tensor_desc* T, cons
             ++since_min;
         }
         const bool stalled = Tr && !use_ref && (since_min >= kStallIters || 2 * iters >= o.max_iter);
-        const bool predicted = Tr && !use_ref && iters > 0 && prev_resid > 0.0 &&
-                               std::isfinite(prev_resid) && resid * (resid / prev_resid) <= o.switch_tol;
+        // the prediction applies the last contraction once more
+        // (switch_predict 1), or the slower of the last two (2), so that a
+        // single fast first step on a slowly converging problem does not end
+        // the narrow passes early
+        bool predicted = false;
+        if (Tr && !use_ref && o.switch_predict == 1 && iters > 0 && prev_resid > 0.0 &&
+            std::isfinite(prev_resid))
+            predicted = resid * (resid / prev_resid) <= o.switch_tol;
+        if (Tr && !use_ref && o.switch_predict == 2 && iters > 1 && prev_resid > 0.0 &&
+            prev2_resid > 0.0 && std::isfinite(prev2_resid))
+            predicted = resid * std::max(resid / prev_resid, prev_resid / prev2_resid) <= o.switch_tol;
+        prev2_resid = prev_resid;
         prev_resid = resid;
         if (Tr && !use_ref &&
             (resid <= o.switch_tol || stalled || predicted || sc[SC_CONVERGED] != 0.0)) {

@@ -59,6 +59,7 @@ def test_opts_default_values(lib):
     assert (o.tol, o.max_iter, o.variant) == (1e-6, 200, 0)
     assert (o.eig_tol, o.eig_max_steps, o.eig_adapt) == (1e-10, 64, 1e-3)
     assert not o.refine and o.switch_tol == 1e-3 and o.timeout_ns == 2_000_000_000
+    assert o.switch_predict == 1
 
 
 def test_null_and_invalid_arguments_are_rejected_on_the_host(lib):

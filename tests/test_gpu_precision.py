@@ -114,10 +114,11 @@ def test_slowly_converging_solve_keeps_the_narrow_copy_until_switch_tol():
     """T = u o u o u o u + 0.3 sum over the six placements of v o v among
     u's (v orthogonal to u): the blocks at the solution keep a strong second
     singular value, so HOSCF converges slowly and steadily (the residual
-    falls by ~15 % per iteration, never halving).  The narrow-copy passes
-    continue until the residual nears switch_tol - a slow decrease is
-    progress, not the storage format's floor - and the FP32 refinement then
-    reaches the tolerance, certified by the oracle's FP64 pass."""
+    falls by ~15 % per iteration, never halving).  With switch_predict 2 the
+    narrow-copy passes continue until the residual nears switch_tol - a slow
+    decrease is progress, not the storage format's floor - and the FP32
+    refinement then reaches the tolerance, certified by the oracle's FP64
+    pass."""
     import itertools
     dims = (24, 24, 24, 24)
     rng = np.random.default_rng(25)
@@ -135,7 +136,9 @@ def test_slowly_converging_solve_keeps_the_narrow_copy_until_switch_tol():
     Tg = T.cuda()
     to_switch = P().hoscf_solve(Tg, u0, tol=1e-3, max_iter=3000)     # FP32 passes down to 1e-3
     q, s = P().hoscf_quantize(Tg, "f16")
-    r = P().hoscf_solve(q, u0, refine=Tg, tol=1e-6, max_iter=3000, switch_tol=1e-3)
+    # the prediction from the slower of the last two contractions (a fast
+    # first step does not end the narrow passes)
+    r = P().hoscf_solve(q, u0, refine=Tg, tol=1e-6, max_iter=3000, switch_tol=1e-3, switch_predict=2)
     assert r.converged
     narrow = r.passes - r.passes_refine
     # the narrow copy carries the iteration down to switch_tol (the

@@ -72,6 +72,36 @@ def gaussian_tensor(dims, seed: int, device="cpu"):
                        dtype=torch.float32)
 
 
+def coupled_pair(dims, a: float, seed: int, noise_abs: float = 0.0, device="cpu"):
+    """u o ... o u plus a times every placement of v o v (two modes) among
+    the u's, v a unit vector orthogonal to u (one u, v per mode), plus
+    Gaussian noise of norm noise_abs - a tensor whose blocks at the best
+    rank-one point keep a second singular value of about a, so that HOSCF
+    converges slowly and steadily (about 15 % per iteration at a = 0.3, d = 4).
+    Returns T (float32)."""
+    import itertools
+    dims = [int(n) for n in dims]
+    d = len(dims)
+    g = _gen(seed, device)
+    us, vs = [], []
+    for n in dims:
+        u = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+        u /= u.norm()
+        v = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+        v -= (v @ u) * u
+        v /= v.norm()
+        us.append(u.to(torch.float32))
+        vs.append(v.to(torch.float32))
+    T = outer(us)
+    for pos in itertools.combinations(range(d), 2):
+        T.add_(outer([vs[k] if k in pos else us[k] for k in range(d)]), alpha=float(a))
+    if noise_abs:
+        E = torch.randn(*dims, generator=g, device=device, dtype=torch.float32)
+        E.mul_(float(noise_abs) / float(E.double().norm()))
+        T.add_(E)
+    return T
+
+
 def planted_cp(dims, weights, seed: int, noise_rel=None, noise_abs=None, device="cpu"):
     """Planted CP tensor plus scaled Gaussian noise.
 
