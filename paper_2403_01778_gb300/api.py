@@ -400,17 +400,57 @@ def hoscf_backward(T: torch.Tensor, u: torch.Tensor, sigma: float, grad_sigma: f
     return grad_T
 
 
+def _batch_descs(tensors):
+    """The descriptor array of a batch, filled field by field with numpy (a
+    Python object per tensor costs more than the whole launch at a thousand
+    tensors).  Returns (array, dims buffer to keep alive)."""
+    import numpy as np
+    cnt = len(tensors)
+    for T in tensors:
+        if not (T.is_cuda and T.is_contiguous() and T.dtype == torch.float32):
+            raise ValueError("batched tensors must be contiguous FP32 CUDA tensors")
+    shapes = [tuple(T.shape) for T in tensors]
+    if any(len(sh) not in (3, 4) for sh in shapes):
+        raise ValueError("batched tensors have order 3 or 4")
+    dims = np.array([sh + (0,) * (4 - len(sh)) for sh in shapes], dtype=np.int64).reshape(cnt, 4)
+    orders = np.array([len(sh) for sh in shapes], dtype=np.int32)
+    arr = (TensorDesc * cnt)()
+    rec = np.ndarray((cnt,), dtype=np.dtype({
+        "names": ["order", "dims", "dtype", "data", "scales"],
+        "formats": [np.int32, np.uint64, np.int32, np.uint64, np.uint64],
+        "offsets": [TensorDesc.order.offset, TensorDesc.dims.offset, TensorDesc.dtype.offset,
+                    TensorDesc.data.offset, TensorDesc.scales.offset],
+        "itemsize": ctypes.sizeof(TensorDesc)}), buffer=arr)
+    rec["order"] = orders
+    rec["dims"] = dims.ctypes.data + dims.strides[0] * np.arange(cnt, dtype=np.uint64)
+    rec["dtype"] = _lib.HOSCF_F32
+    rec["data"] = np.fromiter((T.data_ptr() for T in tensors), dtype=np.uint64, count=cnt)
+    rec["scales"] = 0
+    return arr, dims
+
+
 def hoscf_solve_batched(tensors, u0s, tol=1e-6, max_iter=200, eig_tol=None, timeout_ns=None,
                         batch_threads=None, batch_faces=None, stream=None):
     """Many small independent F32 tensors (orders 3-4) in one persistent,
-    graph-captured launch.  Returns (sigmas, factor tensors, infos, status)."""
+    graph-captured launch.  Returns (sigmas, factor tensors, infos, status);
+    the factor tensors are views of one buffer."""
+    import numpy as np
     cnt = len(tensors)
-    descs = [_Desc(T) for T in tensors]
-    arr = (TensorDesc * cnt)(*[dd.desc for dd in descs])
+    if cnt == 0 or len(u0s) != cnt:
+        raise ValueError("need one start vector per tensor, at least one tensor")
+    arr, dims_keep = _batch_descs(tensors)
     u0c = [u.contiguous() for u in u0s]
-    uo = [torch.empty_like(u) for u in u0c]
-    pin = (ctypes.c_void_p * cnt)(*[u.data_ptr() for u in u0c])
-    pout = (ctypes.c_void_p * cnt)(*[u.data_ptr() for u in uo])
+    ns = [u.numel() for u in u0c]
+    if ns != [sum(T.shape) for T in tensors]:
+        raise ValueError("each start vector holds sum(dims) entries")
+    flat = torch.empty(sum(ns), dtype=torch.float32, device=tensors[0].device)
+    uo = list(flat.split(ns))
+    offs = np.zeros(cnt, dtype=np.uint64)
+    np.cumsum(np.asarray(ns[:-1], dtype=np.uint64) * 4, out=offs[1:])
+    pin = (ctypes.c_void_p * cnt)()
+    np.ndarray((cnt,), dtype=np.uint64, buffer=pin)[:] = [u.data_ptr() for u in u0c]
+    pout = (ctypes.c_void_p * cnt)()
+    np.ndarray((cnt,), dtype=np.uint64, buffer=pout)[:] = flat.data_ptr() + offs
     sig = (ctypes.c_double * cnt)()
     infos = (Info * cnt)()
     o = _opts(tol, max_iter, None, eig_tol, None, None, None, timeout_ns)
@@ -422,8 +462,9 @@ def hoscf_solve_batched(tensors, u0s, tol=1e-6, max_iter=200, eig_tol=None, time
     h = handle(dev)
     st = _lib.load().hoscf_solve_batched(h, cnt, arr, pin, ctypes.byref(o), pout, sig, infos,
                                          _stream_ptr(stream))
+    del dims_keep
     _check(st, h, allow=(0, _lib.HOSCF_NOT_CONVERGED))
-    return [float(s) for s in sig], uo, [infos[i] for i in range(cnt)], st
+    return list(sig), uo, list(infos), st
 
 
 # ------------------------------------------------------------------ sharded form

@@ -30,6 +30,7 @@ namespace hoscf {
 
 constexpr int kBatchMaxOrder = 4;
 constexpr int kBatchLanczos = 32;
+constexpr int kBatchDfScratch = 2 * 5 * 32;   // cta_df_sum of up to 5 values
 
 struct BatchItem {
     const float* T;
@@ -83,27 +84,43 @@ __device__ __forceinline__ int bmode(const BShape& s, int q) {
     return m;
 }
 
-// CTA-wide sum (float), result returned to every thread.  red has >= 32 slots.
-__device__ __forceinline__ float cta_sum(float v, float* red) {
+// CTA-wide sums of NV double-float values (df_add: ~46 significant bits from
+// FP32 instructions - FP64 issues slowly on this part, so no thread of the
+// CTA does FP64 arithmetic here): a butterfly per warp, then thread v < NV
+// adds the warp sums of value v in warp order and writes the total (FP64) to
+// out[v] (shared); every thread may read out[] on return.  scratch holds
+// 2 NV x 32 floats.
+template <int NV>
+__device__ void cta_df_sum(float (&h)[NV], float (&l)[NV], double* out, float* scratch) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float bh = __shfl_xor_sync(HOSCF_FULLMASK, h[v], o);
+            const float bl = __shfl_xor_sync(HOSCF_FULLMASK, l[v], o);
+            df_add(h[v], l[v], bh);
+            l[v] += bl;
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            scratch[(2 * v) * 32 + warp] = h[v];
+            scratch[(2 * v + 1) * 32 + warp] = l[v];
+        }
+    }
     __syncthreads();
-    if (lane == 0) red[warp] = v;
+    if ((int)threadIdx.x < NV) {
+        const int v = threadIdx.x;
+        float th = 0.f, tl = 0.f;
+        for (int w = 0; w < nw; ++w) {
+            df_add(th, tl, scratch[(2 * v) * 32 + w]);
+            tl += scratch[(2 * v + 1) * 32 + w];
+        }
+        out[v] = (double)th + (double)tl;
+    }
     __syncthreads();
-    float t = 0.f;
-    for (int w = 0; w < nw; ++w) t += red[w];
-    return t;
-}
-
-__device__ __forceinline__ double cta_sum_d(double v, double* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum_d(v);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += red[w];
-    return t;
 }
 
 // All blocks of one tensor into H (shared memory), one pass over T.  Faces
@@ -135,11 +152,10 @@ __device__ void batch_blocks(const BShape& s, const float* __restrict__ T, const
     const int gb = tid % B, gg = tid / B;
     for (int i = tid; i < s.P; i += nt) H[i] = 0.f;
     float* Hf = H + s.boff[bidx(d, d - 2, d - 1)];
-    auto outer_w = [&](int o) {
-        if (d == 3) return u[o];
-        const int a0 = o / s.dims[1], a1 = o - a0 * s.dims[1];
-        return u[a0] * u[s.moff[1] + a1];
-    };
+    // per group (double-buffered by group parity): the faces' outer weights
+    // w_k and, for d = 4, their outer indices (i0, i1)
+    __shared__ float s_wk[2][32];
+    __shared__ int s_i0[2][32], s_i1[2][32];
     auto stage = [&](int g) {
         const int o0 = g * K, kk = min(K, O - o0);
         const float* src = T + (size_t)o0 * F;
@@ -160,20 +176,48 @@ __device__ void batch_blocks(const BShape& s, const float* __restrict__ T, const
         } else {
             cp_async_wait_group<0>();
         }
+        const int o0 = g * K, kk = min(K, O - o0);
+        const int par = g & 1;
+        if (tid < kk) {
+            const int o = o0 + tid;
+            if (d == 3) {
+                s_wk[par][tid] = u[o];
+            } else {
+                const int i0 = o / s.dims[1], i1 = o - i0 * s.dims[1];
+                s_i0[par][tid] = i0;
+                s_i1[par][tid] = i1;
+                s_wk[par][tid] = u[i0] * u[s.moff[1] + i1];
+            }
+        }
         __syncthreads();               // everyone's copies of group g are visible (and H zeroed)
         const float* fb = faces + (size_t)(g & 1) * fstride;
-        const int o0 = g * K, kk = min(K, O - o0);
+        const float* wk = s_wk[par];
         for (int f = tid; f < F; f += nt) {
             float h = Hf[f];
-            for (int k = 0; k < kk; ++k) h = fmaf(outer_w(o0 + k), fb[k * F + f], h);
+            for (int k = 0; k < kk; ++k) h = fmaf(wk[k], fb[k * F + f], h);
             Hf[f] = h;
         }
-        for (int row = warp; row < kk * A; row += nw) {
-            const float* fr = fb + (size_t)row * B;     // face row (k, a): k * F + a * B
-            float t = 0.f;
-            for (int b = lane; b < B; b += 32) t = fmaf(fr[b], uB[b], t);
-            t = warp_sum(t);
-            if (lane == 0) y1[row] = t;
+        if (B <= 32) {
+            // short rows: one thread per row, walking its columns from a
+            // row-dependent start (the rows of a warp then hit distinct banks)
+            for (int row = tid; row < kk * A; row += nt) {
+                const float* fr = fb + (size_t)row * B;     // face row (k, a): k * F + a * B
+                int b = row % B;
+                float t = 0.f;
+                for (int c = 0; c < B; ++c) {
+                    t = fmaf(fr[b], uB[b], t);
+                    b = (b + 1 == B) ? 0 : b + 1;
+                }
+                y1[row] = t;
+            }
+        } else {
+            for (int row = warp; row < kk * A; row += nw) {
+                const float* fr = fb + (size_t)row * B;
+                float t = 0.f;
+                for (int b = lane; b < B; b += 32) t = fmaf(fr[b], uB[b], t);
+                t = warp_sum(t);
+                if (lane == 0) y1[row] = t;
+            }
         }
         if (kk == 1) {
             if (gg < ng) {
@@ -195,8 +239,9 @@ __device__ void batch_blocks(const BShape& s, const float* __restrict__ T, const
             for (int b = tid; b < B; b += nt) {
                 float t = 0.f;
                 for (int q = 0; q < ng; ++q) t += part[q * B + b];
-                y2[b] = t;   // read below only by the thread that wrote it
+                y2[b] = t;   // order 3: read below only by the thread that wrote it
             }
+            if (d == 4) __syncthreads();   // order 4: read below by other threads
         }
         if (d == 3) {
             // H01[o][a] = y1_k[a], H02[o][b] = y2_k[b]
@@ -204,21 +249,24 @@ __device__ void batch_blocks(const BShape& s, const float* __restrict__ T, const
             for (int kb = tid; kb < kk * B; kb += nt) H[s.boff[1] + (size_t)o0 * B + kb] = y2[kb];
         } else {
             // rows i0 = o / I_1, i1 = o % I_1 of H02, H12 (from y1) and H03, H13
-            // (from y2); a thread owns one column and walks the group's faces in order
-            for (int a = tid; a < A; a += nt)
+            // (from y2); a thread owns one column of one of the four blocks
+            // and walks the group's faces in order
+            const int* gi0 = s_i0[par];
+            const int* gi1 = s_i1[par];
+            for (int e = tid; e < 2 * (A + B); e += nt) {
+                const int which = e < 2 * A ? (e < A ? 0 : 1) : (e < 2 * A + B ? 2 : 3);
+                const int len = which < 2 ? A : B;
+                const int col = e - (which == 0 ? 0 : which == 1 ? A : which == 2 ? 2 * A : 2 * A + B);
+                const float* yy = which < 2 ? y1 : y2;
+                float* Hb = H + s.boff[bidx(4, (which & 1) ? 1 : 0, which < 2 ? 2 : 3)] + col;
                 for (int k = 0; k < kk; ++k) {
-                    const int o = o0 + k, i0 = o / s.dims[1], i1 = o - i0 * s.dims[1];
-                    const float yv = y1[k * A + a];
-                    H[s.boff[bidx(4, 0, 2)] + i0 * A + a] = fmaf(u[s.moff[1] + i1], yv, H[s.boff[bidx(4, 0, 2)] + i0 * A + a]);
-                    H[s.boff[bidx(4, 1, 2)] + i1 * A + a] = fmaf(u[i0], yv, H[s.boff[bidx(4, 1, 2)] + i1 * A + a]);
+                    const int i0 = gi0[k], i1 = gi1[k];
+                    // H0n rows i0 take u_1[i1]; H1n rows i1 take u_0[i0]
+                    const int rowi = (which & 1) ? i1 : i0;
+                    const float wu = (which & 1) ? u[i0] : u[s.moff[1] + i1];
+                    Hb[(size_t)rowi * len] = fmaf(wu, yy[k * len + col], Hb[(size_t)rowi * len]);
                 }
-            for (int b = tid; b < B; b += nt)
-                for (int k = 0; k < kk; ++k) {
-                    const int o = o0 + k, i0 = o / s.dims[1], i1 = o - i0 * s.dims[1];
-                    const float yv = y2[k * B + b];
-                    H[s.boff[bidx(4, 0, 3)] + i0 * B + b] = fmaf(u[s.moff[1] + i1], yv, H[s.boff[bidx(4, 0, 3)] + i0 * B + b]);
-                    H[s.boff[bidx(4, 1, 3)] + i1 * B + b] = fmaf(u[i0], yv, H[s.boff[bidx(4, 1, 3)] + i1 * B + b]);
-                }
+            }
             // H01[i0][i1] = r_o = <y1_k, uA>, one warp per face
             for (int k = warp; k < kk; k += nw) {
                 float r = 0.f;
@@ -269,12 +317,16 @@ struct BatchSmem {
     float* y2;     // AB_max
     float* w;      // n
     float* red;    // 64
-    double* dred;  // 64
+    double* dred;  // 64: [0, 8) sums of cta_df_sum, [8, 12) FP64 scalars of thread 0
     double* alpha; // kMaxLanczos
     double* beta;  // kMaxLanczos
     double* sv;    // kMaxLanczos
     float* hs;     // kMaxLanczos + 8
     float* rscratch;   // 9 kMaxLanczos
+    float* dfs;    // kBatchDfScratch: scratch of cta_df_sum
+    float* fsc;    // 8: FP32 scalars of thread 0, broadcast
+    float* svh;    // kBatchLanczos: the Ritz vector's coefficients, hi part
+    float* svl;    // kBatchLanczos: and lo part (double-float)
 };
 
 __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
@@ -290,7 +342,11 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
         S.red = fp;
         S.hs = S.red + 64;
         S.rscratch = S.hs + kMaxLanczos + 8;
-        S.u = S.rscratch + 9 * kMaxLanczos;
+        S.dfs = S.rscratch + 9 * kMaxLanczos;
+        S.fsc = S.dfs + kBatchDfScratch;
+        S.svh = S.fsc + 8;
+        S.svl = S.svh + kBatchLanczos;
+        S.u = S.svl + kBatchLanczos;
         S.w = S.u + ((a.n_max + 3) & ~3);
         S.y1 = S.w + ((a.n_max + 3) & ~3);
         S.y2 = S.y1 + batch_ycap(a.AB_max);
@@ -327,84 +383,131 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
             sh.P = off;
         }
         const int d = sh.d, n = sh.n;
-        const double sqrt_d = sqrt((double)d);
+        // FP64 arithmetic only in thread 0 (or one warp): every scalar is
+        // formed there and broadcast through shared memory (S.dred[8..12),
+        // S.fsc, s_ctl); the sums are double-float (cta_df_sum)
+        __shared__ int s_ctl;
         int status = 0;
         // normalise the initial guess per block
-        for (int m = 0; m < d; ++m) {
-            double ss = 0.0;
-            for (int q = sh.moff[m] + tid; q < sh.moff[m + 1]; q += nt) ss += (double)it.u0[q] * it.u0[q];
-            ss = cta_sum_d(ss, S.dred);
-            const double inv = (ss > 0.0 && isfinite(ss)) ? 1.0 / sqrt(ss) : 0.0;
-            if (!(ss > 0.0) || !isfinite(ss)) status = 5;
-            for (int q = sh.moff[m] + tid; q < sh.moff[m + 1]; q += nt) S.u[q] = (float)(it.u0[q] * inv);
+        {
+            float hh[kBatchMaxOrder] = {0.f, 0.f, 0.f, 0.f}, ll[kBatchMaxOrder] = {0.f, 0.f, 0.f, 0.f};
+            for (int q = tid; q < n; q += nt) {
+                const int m = bmode(sh, q);
+                const float x = it.u0[q];
+#pragma unroll
+                for (int v = 0; v < kBatchMaxOrder; ++v)
+                    if (v == m) df_add_prod(hh[v], ll[v], x, x);
+            }
+            cta_df_sum<kBatchMaxOrder>(hh, ll, S.dred, S.dfs);
+            if (tid == 0) {
+                int st = 0;
+                for (int m = 0; m < d; ++m) {
+                    const double ss = S.dred[m];
+                    const bool ok = ss > 0.0 && isfinite(ss);
+                    S.fsc[4 + m] = ok ? (float)rsqrt_nr(ss) : 0.f;
+                    if (!ok) st = 5;
+                }
+                s_ctl = st;
+            }
+            __syncthreads();
+            status = s_ctl;
+            for (int q = tid; q < n; q += nt) S.u[q] = it.u0[q] * S.fsc[4 + bmode(sh, q)];
         }
         __syncthreads();
         int iters = 0, passes = 0;
-        double sigma = 0.0, resid = INFINITY;
+        double sigma = 0.0, resid = INFINITY;   // thread 0's values are the results
+        // x = u / sqrt(d) (the scale of x is immaterial to rho and the
+        // relative residual; sqrt(d) enters the residual below)
+        const float xs = d == 4 ? 0.5f : 0.577350269f;
         while (status == 0) {
             batch_blocks(sh, it.T, S.u, S.H, S.face, (a.F_max + 3) & ~3, S.y1, S.y2, batch_ycap(a.AB_max),
                          S.part, S.red, a.faces);
             ++passes;
-            // ---- certificate at x = u / sqrt(d): rho = x^T J x, KKT residual
+            // ---- certificate at x: rho = x^T J x / x^T x, KKT residual (eq. 2.4)
             float* V = S.face;   // (mmax+1) x n basis
             float* Y = S.w;
-            for (int q = tid; q < n; q += nt) V[q] = (float)((double)S.u[q] / sqrt_d);
+            for (int q = tid; q < n; q += nt) V[q] = S.u[q] * xs;
             __syncthreads();
             batch_matvec(sh, S.H, V, Y);
             __syncthreads();
-            double sxy = 0.0, sxx = 0.0;
-            for (int q = tid; q < n; q += nt) {
-                sxy += (double)V[q] * Y[q];
-                sxx += (double)V[q] * V[q];
+            {
+                float hh[2] = {0.f, 0.f}, ll[2] = {0.f, 0.f};
+                for (int q = tid; q < n; q += nt) {
+                    df_add_prod(hh[0], ll[0], V[q], Y[q]);
+                    df_add_prod(hh[1], ll[1], V[q], V[q]);
+                }
+                cta_df_sum<2>(hh, ll, S.dred, S.dfs);
             }
-            sxy = cta_sum_d(sxy, S.dred);
-            sxx = cta_sum_d(sxx, S.dred);
-            const double rho = sxy / sxx;
-            const double inv = 1.0 / sqrt(sxx);
-            double sw = 0.0;
-            for (int q = tid; q < n; q += nt) {
-                const double wv = ((double)Y[q] - rho * (double)V[q]) * inv;
-                sw += wv * wv;
+            if (tid == 0) {
+                const double xy = S.dred[0], xx = S.dred[1];
+                const bool bad = !(xx > 0.0) || !isfinite(xx) || !isfinite(xy);
+                const double rho = bad ? 0.0 : xy * rcp_nr(xx);
+                S.dred[8] = rho;
+                S.fsc[0] = (float)rho;
+                S.fsc[1] = (float)(rho - (double)S.fsc[0]);
+                S.fsc[2] = bad ? 0.f : (float)rsqrt_nr(xx);
+                s_ctl = bad ? 1 : 0;
             }
-            sw = cta_sum_d(sw, S.dred);
-            const double b0 = sqrt(sw);
-            sigma = rho;
-            resid = (rho != 0.0) ? sqrt_d * b0 / fabs(rho) : INFINITY;
-            if (!isfinite(rho) || !isfinite(b0)) {
-                status = 5;
-                break;
+            __syncthreads();
+            // w = (y - rho x) / |x| (rho split hi + lo: the two FMAs leave only
+            // the final rounding, so the cancellation costs nothing), which is
+            // the first Lanczos residual; v0 = x / |x|
+            {
+                const float rho_h = S.fsc[0], rho_l = S.fsc[1], finv = S.fsc[2];
+                float hh[1] = {0.f}, ll[1] = {0.f};
+                for (int q = tid; q < n; q += nt) {
+                    const float x = V[q];
+                    const float w = fmaf(-rho_l, x, fmaf(-rho_h, x, Y[q])) * finv;
+                    df_add_prod(hh[0], ll[0], w, w);
+                    Y[q] = w;
+                    V[q] = x * finv;
+                }
+                cta_df_sum<1>(hh, ll, S.dred, S.dfs);
             }
-            if (resid <= a.tol) break;
-            if (iters >= a.max_iter) {
-                status = 4;
-                break;
+            if (tid == 0) {
+                const double rho = S.dred[8];
+                const double sw = fmax(S.dred[0], 0.0);
+                const double b0 = sw > 0.0 ? sw * rsqrt_nr(sw) : 0.0;
+                const double sqrt_d = d == 4 ? 2.0 : 1.7320508075688772;
+                sigma = rho;
+                resid = (rho != 0.0) ? sqrt_d * b0 * rcp_nr(fabs(rho)) : INFINITY;
+                int st = 0;
+                if (s_ctl || !isfinite(rho) || !isfinite(b0))
+                    st = 5;
+                else if (resid <= a.tol)
+                    st = 1;
+                else if (iters >= a.max_iter)
+                    st = 4;
+                s_ctl = st;
+                // inexact eigen steps: the Ritz tolerance follows the residual
+                double etol = a.eig_tol;
+                if (a.eig_adapt > 0.0) etol = fmax(etol, fmin(1e-3, a.eig_adapt * resid));
+                S.dred[9] = etol;
+                S.alpha[0] = rho;
+                S.beta[0] = (double)(float)b0;
+                S.fsc[3] = (float)b0;
+            }
+            __syncthreads();
+            {
+                const int st = s_ctl;
+                if (st == 1) break;
+                if (st) {
+                    status = st;
+                    break;
+                }
             }
             ++iters;
             // ---- Lanczos for the largest-magnitude eigenpair (warm start at x)
-            double etol = a.eig_tol;
-            if (a.eig_adapt > 0.0) etol = fmax(etol, fmin(1e-3, a.eig_adapt * resid));
-            const float finv = (float)inv, frho = (float)rho;
-            for (int q = tid; q < n; q += nt) {
-                V[q] *= finv;
-                Y[q] = Y[q] * finv - frho * V[q];
-            }
-            if (tid == 0) {
-                S.alpha[0] = rho;
-                S.beta[0] = b0;
-            }
-            __syncthreads();
-            double beta_last = b0;
+            const double etol = S.dred[9];
+            float beta_f = S.fsc[3];
             int k = 1;
-            RitzOut ro;
-            ro.theta = rho;
-            ro.resid = b0;
             bool done = false;
             const int mmax = min(a.mmax, n);
             for (int j = 1; !done; ++j) {
                 // V[j] = w / beta ; y = J V[j]
-                const bool last_basis = (j >= mmax) || !(beta_last > 1e-30);
+                const bool last_basis = (j >= mmax) || !(beta_f > 1e-30f);
                 if (!last_basis) {
-                    const float ib = (float)(1.0 / beta_last);
+                    const float ib = 1.f / beta_f;
                     for (int q = tid; q < n; q += nt) V[(size_t)j * n + q] = Y[q] * ib;
                     __syncthreads();
                     batch_matvec(sh, S.H, V + (size_t)j * n, Y);
@@ -433,35 +536,24 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
                         }
                         if (tid == 0) S.alpha[j] = (pass2 == 0 ? 0.0 : S.alpha[j]) + S.hs[j];
                         __syncthreads();
-                        if (pass2 == 0) {
-                            if (b2 >= 0.25f * yy) {
-                                beta_last = sqrt(fmax((double)b2, 0.0));
-                                break;
-                            }
-                        } else {
-                            beta_last = sqrt(fmax((double)b2, 0.0));
-                        }
+                        beta_f = sqrtf(fmaxf(b2, 0.f));
+                        if (pass2 == 0 && b2 >= 0.25f * yy) break;
                     }
-                    if (tid == 0) S.beta[j] = beta_last;
+                    if (tid == 0) S.beta[j] = beta_f;
                     k = j + 1;
                     __syncthreads();
                 }
-                const bool last = last_basis || k >= mmax || !(beta_last > 1e-30);
+                const bool last = last_basis || k >= mmax || !(beta_f > 1e-30f);
                 if (k >= 2 && (k <= 6 || (k & 1) == 0 || last)) {
                     // FP32 pair to decide; the FP64 refinement only once accepted
-                    __shared__ RitzOut s_ro;
                     __shared__ int s_acc;
                     if (warp == 0) {
-                        RitzOut rr = ritz_extreme_fp32(S.alpha, S.beta, k, beta_last, S.rscratch, etol, last);
+                        RitzOut rr = ritz_extreme_fp32(S.alpha, S.beta, k, beta_f, S.rscratch, etol, last);
                         const bool acc = rr.resid <= etol * fabs(rr.theta) || last;
-                        if (acc) rr = ritz_refine_fp64(S.alpha, S.beta, k, beta_last, S.sv, S.rscratch);
-                        if (lane == 0) {
-                            s_ro = rr;
-                            s_acc = acc ? 1 : 0;
-                        }
+                        if (acc) ritz_refine_fp64(S.alpha, S.beta, k, beta_f, S.sv, S.rscratch);
+                        if (lane == 0) s_acc = acc ? 1 : 0;
                     }
                     __syncthreads();
-                    ro = s_ro;
                     if (s_acc) done = true;
                 } else if (last) {
                     if (tid == 0) S.sv[0] = 1.0;
@@ -469,22 +561,46 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
                     done = true;
                 }
             }
-            // Ritz vector, sign-aligned with x, blocks normalised (lines 6-9)
-            double dot = 0.0;
-            for (int q = tid; q < n; q += nt) {
-                double x = 0.0;
-                for (int i = 0; i < k; ++i) x += S.sv[i] * (double)V[(size_t)i * n + q];
-                Y[q] = (float)x;
-                dot += x * (double)V[q];
+            // Ritz vector x = V s (double-float coefficients and sums), sign-
+            // aligned with x, blocks normalised (Alg. 1 lines 6-9)
+            if (tid < k) {
+                const double sv = S.sv[tid];
+                const float h = (float)sv;
+                S.svh[tid] = h;
+                S.svl[tid] = (float)(sv - (double)h);
             }
-            dot = cta_sum_d(dot, S.dred);
-            const float sgn = dot < 0.0 ? -1.f : 1.f;
-            for (int m = 0; m < d; ++m) {
-                double ss = 0.0;
-                for (int q = sh.moff[m] + tid; q < sh.moff[m + 1]; q += nt) ss += (double)Y[q] * Y[q];
-                ss = cta_sum_d(ss, S.dred);
-                const float ib = ss > 0.0 ? (float)(1.0 / sqrt(ss)) : 0.f;
-                for (int q = sh.moff[m] + tid; q < sh.moff[m + 1]; q += nt) S.u[q] = sgn * Y[q] * ib;
+            __syncthreads();
+            {
+                float hh[kBatchMaxOrder + 1] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                float ll[kBatchMaxOrder + 1] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int q = tid; q < n; q += nt) {
+                    float xh = 0.f, xl = 0.f;
+                    for (int i = 0; i < k; ++i) {
+                        const float v = V[(size_t)i * n + q];
+                        df_add_prod(xh, xl, S.svh[i], v);
+                        xl = fmaf(S.svl[i], v, xl);
+                    }
+                    const float x = xh + xl;
+                    Y[q] = x;
+                    const int m = bmode(sh, q);
+#pragma unroll
+                    for (int v = 0; v < kBatchMaxOrder; ++v)
+                        if (v == m) df_add_prod(hh[v], ll[v], x, x);
+                    df_add_prod(hh[kBatchMaxOrder], ll[kBatchMaxOrder], x, V[q]);
+                }
+                cta_df_sum<kBatchMaxOrder + 1>(hh, ll, S.dred, S.dfs);
+            }
+            if (tid == 0) {
+                for (int m = 0; m < d; ++m) {
+                    const double ss = S.dred[m];
+                    S.fsc[4 + m] = ss > 0.0 ? (float)rsqrt_nr(ss) : 0.f;
+                }
+                S.fsc[3] = S.dred[kBatchMaxOrder] < 0.0 ? -1.f : 1.f;
+            }
+            __syncthreads();
+            {
+                const float sgn = S.fsc[3];
+                for (int q = tid; q < n; q += nt) S.u[q] = sgn * Y[q] * S.fsc[4 + bmode(sh, q)];
             }
             __syncthreads();
         }
@@ -493,16 +609,26 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
         if (tid == 0) s_flip = (sigma < 0.0) ? 1 : 0;
         __syncthreads();
         for (int m = 1; m < d; ++m) {
-            // largest |u| entry of mode m (lowest index on ties) made positive
-            if (tid == 0) {
+            // largest |u| entry of mode m (lowest index on ties) made positive:
+            // a lane scan in index order, then a warp arg-max
+            if (warp == 0) {
                 float best = -1.f;
-                int bi = 0;
-                for (int q = sh.moff[m]; q < sh.moff[m + 1]; ++q)
+                int bi = sh.moff[m];
+                for (int q = sh.moff[m] + lane; q < sh.moff[m + 1]; q += 32)
                     if (fabsf(S.u[q]) > best) {
                         best = fabsf(S.u[q]);
                         bi = q;
                     }
-                S.red[0] = (S.u[bi] < 0.f) ? 1.f : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ob = __shfl_xor_sync(HOSCF_FULLMASK, best, o);
+                    const int oi = __shfl_xor_sync(HOSCF_FULLMASK, bi, o);
+                    if (ob > best || (ob == best && oi < bi)) {
+                        best = ob;
+                        bi = oi;
+                    }
+                }
+                if (lane == 0) S.red[0] = (S.u[bi] < 0.f) ? 1.f : 0.f;
             }
             __syncthreads();
             if (S.red[0] != 0.f) {
@@ -533,7 +659,8 @@ __global__ void __launch_bounds__(1024) batched_hoscf_kernel(BatchArgs a) {
 static size_t batch_smem(int n_max, int P_max, int F_max, int AB_max, int mmax) {
     const int basis = std::max(2 * ((F_max + 3) & ~3), (mmax + 1) * n_max);
     return sizeof(double) * (64 + 3 * kMaxLanczos) +
-           sizeof(float) * (64 + kMaxLanczos + 8 + 9 * kMaxLanczos + 2 * ((n_max + 3) & ~3) +
+           sizeof(float) * (64 + kMaxLanczos + 8 + 9 * kMaxLanczos + kBatchDfScratch + 8 +
+                            2 * kBatchLanczos + 2 * ((n_max + 3) & ~3) +
                             2 * batch_ycap(AB_max) + ((P_max + 3) & ~3) + ((basis + 3) & ~3) + 1024) +
            64;
 }

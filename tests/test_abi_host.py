@@ -214,3 +214,41 @@ def test_reference_arm_times_the_oracle_step_on_the_host(capsys):
     assert line["e2e"] == {"value": line["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["steps"] == 2 and line["warmup"] == 1
+
+
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor: shape, dtype, contiguity and an address."""
+
+    def __init__(self, shape, ptr):
+        self.shape = torch.Size(shape)
+        self.dtype = torch.float32
+        self.is_cuda = True
+        self._ptr = ptr
+
+    def is_contiguous(self):
+        return True
+
+    def dim(self):
+        return len(self.shape)
+
+    def data_ptr(self):
+        return self._ptr
+
+
+def test_batch_descriptors_are_filled_as_the_c_struct_expects():
+    """The batched call fills its descriptor array field by field with numpy:
+    every field lands where the C struct has it (order, dims pointer into a
+    kept buffer, dtype, data, no scales), and orders other than 3 and 4 are
+    rejected on the host."""
+    from paper_2403_01778_gb300 import _lib, api
+    ts = [_FakeDeviceTensor((3, 4, 5), 4096), _FakeDeviceTensor((6, 7, 8, 9), 8192),
+          _FakeDeviceTensor((9, 1, 2), 65536)]
+    arr, keep = api._batch_descs(ts)
+    for d, t in zip(arr, ts):
+        assert d.order == len(t.shape)
+        assert [d.dims[k] for k in range(d.order)] == list(t.shape)
+        assert d.dtype == _lib.HOSCF_F32 and d.data == t.data_ptr() and not d.scales
+    with pytest.raises(ValueError):
+        api._batch_descs([_FakeDeviceTensor((2, 3), 16)])
+    with pytest.raises(ValueError):
+        api._batch_descs([_FakeDeviceTensor((2, 3, 4, 5, 6), 16)])
