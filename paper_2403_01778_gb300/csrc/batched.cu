@@ -31,6 +31,7 @@ namespace hoscf {
 constexpr int kBatchMaxOrder = 4;
 constexpr int kBatchLanczos = 32;
 constexpr int kBatchDfScratch = 2 * 5 * 32;   // cta_df_sum of up to 5 values
+constexpr int kBatchMinStage = 4096;          // floats per staging slot, at least
 
 struct BatchItem {
     const float* T;
@@ -60,7 +61,8 @@ struct BatchArgs {
     double eig_tol;
     double eig_adapt;
     int mmax;
-    int n_max, P_max, F_max, AB_max;
+    int n_max, P_max, AB_max;
+    int F_max;             // floats per staging slot (>= the largest face)
     int faces;             // at most this many faces per staged group (1 .. 32)
 };
 
@@ -168,9 +170,23 @@ __device__ void batch_blocks(const BShape& s, const float* __restrict__ T, const
         }
         cp_async_commit();
     };
+    // L2 prefetch of the groups PD ahead of the one being staged (the staging
+    // ring holds two groups; the prefetch keeps ~128 KB more on the way, so
+    // each copy finds its lines in L2 rather than waiting out the DRAM latency)
+    const int gbytes = K * F * (int)sizeof(float);
+    const int PD = max(1, min(8, (128 << 10) / max(gbytes, 1)));
+    auto prefetch = [&](int g) {
+        if (g >= ngrp) return;
+        const int o0 = g * K, kk = min(K, O - o0);
+        const char* src = reinterpret_cast<const char*>(T + (size_t)o0 * F);
+        const int bytes = kk * F * (int)sizeof(float);
+        for (int off = tid * 128; off < bytes; off += nt * 128) prefetch_l2(src + off);
+    };
+    for (int g = 1; g <= PD; ++g) prefetch(g);
     stage(0);
     for (int g = 0; g < ngrp; ++g) {
         if (g + 1 < ngrp) {
+            prefetch(g + 1 + PD);
             stage(g + 1);
             cp_async_wait_group<1>();   // this thread's copies of group g have landed
         } else {
@@ -192,31 +208,75 @@ __device__ void batch_blocks(const BShape& s, const float* __restrict__ T, const
         __syncthreads();               // everyone's copies of group g are visible (and H zeroed)
         const float* fb = faces + (size_t)(g & 1) * fstride;
         const float* wk = s_wk[par];
-        for (int f = tid; f < F; f += nt) {
-            float h = Hf[f];
-            for (int k = 0; k < kk; ++k) h = fmaf(wk[k], fb[k * F + f], h);
-            Hf[f] = h;
-        }
-        if (B <= 32) {
-            // short rows: one thread per row, walking its columns from a
-            // row-dependent start (the rows of a warp then hit distinct banks)
-            for (int row = tid; row < kk * A; row += nt) {
-                const float* fr = fb + (size_t)row * B;     // face row (k, a): k * F + a * B
-                int b = row % B;
-                float t = 0.f;
-                for (int c = 0; c < B; ++c) {
-                    t = fmaf(fr[b], uB[b], t);
-                    b = (b + 1 == B) ? 0 : b + 1;
+        if (B > 32 && B <= 128) {
+            // one warp per face row a: its face-block entries (lane l holds
+            // columns l + 32 c) stay in registers over the group's faces, and
+            // each face's row sum y1[k][a] comes from the same loads; the
+            // sums run in the same order as the separate loops below
+            float ub[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int b = lane + 32 * c;
+                ub[c] = b < B ? uB[b] : 0.f;
+            }
+            for (int a = warp; a < A; a += nw) {
+                float* hr = Hf + (size_t)a * B;
+                float h[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int b = lane + 32 * c;
+                    h[c] = b < B ? hr[b] : 0.f;
                 }
-                y1[row] = t;
+                for (int k = 0; k < kk; ++k) {
+                    const float* fr = fb + (size_t)k * F + (size_t)a * B;
+                    const float w = wk[k];
+                    float t = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int b = lane + 32 * c;
+                        if (b < B) {
+                            const float x = fr[b];
+                            h[c] = fmaf(w, x, h[c]);
+                            t = fmaf(x, ub[c], t);
+                        }
+                    }
+                    t = warp_sum(t);
+                    if (lane == 0) y1[k * A + a] = t;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int b = lane + 32 * c;
+                    if (b < B) hr[b] = h[c];
+                }
             }
         } else {
-            for (int row = warp; row < kk * A; row += nw) {
-                const float* fr = fb + (size_t)row * B;
-                float t = 0.f;
-                for (int b = lane; b < B; b += 32) t = fmaf(fr[b], uB[b], t);
-                t = warp_sum(t);
-                if (lane == 0) y1[row] = t;
+            for (int f = tid; f < F; f += nt) {
+                float h = Hf[f];
+                for (int k = 0; k < kk; ++k) h = fmaf(wk[k], fb[k * F + f], h);
+                Hf[f] = h;
+            }
+            if (B <= 32) {
+                // short rows: one thread per row (rows B floats apart: distinct
+                // banks for odd B; for even B each walks its row from column
+                // row mod B)
+                for (int row = tid; row < kk * A; row += nt) {
+                    const float* fr = fb + (size_t)row * B;     // face row (k, a): k * F + a * B
+                    int b = (B & 1) ? 0 : row % B;
+                    float t = 0.f;
+                    for (int c = 0; c < B; ++c) {
+                        t = fmaf(fr[b], uB[b], t);
+                        b = (b + 1 == B) ? 0 : b + 1;
+                    }
+                    y1[row] = t;
+                }
+            } else {
+                for (int row = warp; row < kk * A; row += nw) {
+                    const float* fr = fb + (size_t)row * B;
+                    float t = 0.f;
+                    for (int b = lane; b < B; b += 32) t = fmaf(fr[b], uB[b], t);
+                    t = warp_sum(t);
+                    if (lane == 0) y1[row] = t;
+                }
             }
         }
         if (kk == 1) {
@@ -295,8 +355,15 @@ __device__ void batch_matvec(const BShape& s, const float* H, const float* v, fl
             const float* vn = v + s.moff[nn];
             const int In = s.dims[nn];
             if (nn > m) {
+                // row i of H_{m,nn}: the threads of a warp read rows In
+                // floats apart - distinct banks for odd In; for even In each
+                // walks its row from column i mod In (row stride In + 1)
                 const float* row = H + s.boff[bidx(s.d, m, nn)] + (size_t)i * In;
-                for (int j = 0; j < In; ++j) acc = fmaf(row[j], vn[j], acc);
+                int j = (In & 1) ? 0 : i % In;
+                for (int c = 0; c < In; ++c) {
+                    acc = fmaf(row[j], vn[j], acc);
+                    j = (j + 1 == In) ? 0 : j + 1;
+                }
             } else {
                 const int Im = s.dims[m];
                 const float* blk = H + s.boff[bidx(s.d, nn, m)];
@@ -717,7 +784,14 @@ hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* con
         sizes[(size_t)t] = N;
     }
     const int mmax = std::min(kBatchLanczos, std::max(2, o.eig_max_steps));
-    const size_t smem = batch_smem(n_max, P_max, F_max, AB_max, mmax);
+    // each of the two staging slots holds at least kBatchMinStage floats when
+    // that fits, so batches of small faces stage many faces per group
+    int F_stage = std::max(F_max, kBatchMinStage);
+    size_t smem = batch_smem(n_max, P_max, F_stage, AB_max, mmax);
+    if (smem > 220 * 1024) {
+        F_stage = F_max;
+        smem = batch_smem(n_max, P_max, F_stage, AB_max, mmax);
+    }
     if (smem > 220 * 1024) {
         err.code = HOSCF_EUNSUPPORTED;
         snprintf(err.msg, sizeof(err.msg), "batch tensors too large for one CTA (%zu bytes)", smem);
@@ -748,6 +822,7 @@ hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* con
     memcpy(hp + o_order, order.data(), sizeof(int) * count);
     memset(hp + o_cnt, 0, 256);
     BatchArgs a;
+    memset(&a, 0, sizeof(a));   // padding too: the graph key hashes these bytes
     a.items = reinterpret_cast<BatchItem*>(ws + o_items);
     a.order = reinterpret_cast<int*>(ws + o_order);
     a.out = reinterpret_cast<BatchOut*>(ws + o_out);
@@ -761,7 +836,7 @@ hoscf_status run_batched(int count, const hoscf_tensor_desc* T, const float* con
     a.faces = o.batch_faces > 0 ? std::min(32, o.batch_faces) : 32;
     a.n_max = n_max;
     a.P_max = P_max;
-    a.F_max = F_max;
+    a.F_max = F_stage;
     a.AB_max = AB_max;
     cudaError_t e = allow_max_dynamic_smem(batched_hoscf_kernel);
     int per_sm = 1;
