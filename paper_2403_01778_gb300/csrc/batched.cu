@@ -127,13 +127,15 @@ __device__ void cta_df_sum(float (&h)[NV], float (&l)[NV], double* out, float* s
 
 // All blocks of one tensor into H (shared memory), one pass over T.  Faces
 // T[o][:][:] arrive in groups of K consecutive outer indices (K faces fill
-// one staging buffer, at most 32), double-buffered in shared memory by
+// one staging slot, at most 32), double-buffered in shared memory by
 // cp.async (group g + 1 lands while group g is folded; 16-byte copies when
 // the group is 16-byte aligned, else 4-byte), two CTA barriers per group.
 // Per group: the face block H_{d-2,d-1} += sum_k w_k T_k (each entry owned
-// by one thread, faces in order); the row sums y1_k[a] = T_k[a][:] . u_B by
-// one warp per row; the column sums y2_k[b] = u_A . T_k[:][b] by one thread
-// per (k, b), or - one big face per group - by groups of threads over
+// by one thread - or, for rows of 33-128, by one lane of the warp that also
+// forms the row's sums - faces in order); the row sums y1_k[a] =
+// T_k[a][:] . u_B by one warp per row (one thread per row for rows of at
+// most 32); the column sums y2_k[b] = u_A . T_k[:][b] by one thread per
+// (k, b), or - one big face per group - by groups of threads over
 // interleaved rows, added in group order.  Every block entry is updated by
 // one thread in face order: the blocks are deterministic.
 __device__ void batch_blocks(const BShape& s, const float* __restrict__ T, const float* u, float* H,
