@@ -96,7 +96,7 @@ def test_autograd_function():
     loss = 0.5 * sigma + (w * u).sum()
     loss.backward()
     u64 = [v.astype(np.float64) for v in np.split(u.detach().cpu().numpy(), np.cumsum(dims)[:-1])]
-    ref, _, _ = oracle.adjoint(T.numpy().astype(np.float64), u64, float(sigma), 0.5,
+    ref, _, _ = oracle.adjoint(T.numpy().astype(np.float64), u64, float(sigma.detach()), 0.5,
                                oracle.split(w.cpu().numpy().astype(np.float64), list(dims)))
     assert rel(Tg.grad.double().cpu().numpy(), ref) <= 1e-5
 
