@@ -252,3 +252,15 @@ def test_batch_descriptors_are_filled_as_the_c_struct_expects():
         api._batch_descs([_FakeDeviceTensor((2, 3), 16)])
     with pytest.raises(ValueError):
         api._batch_descs([_FakeDeviceTensor((2, 3, 4, 5, 6), 16)])
+
+
+def test_batched_binding_rejects_bad_input_on_the_host():
+    """hoscf_solve_batched checks counts, placement and start-vector lengths
+    before it touches the library or a device."""
+    import paper_2403_01778_gb300 as P
+    with pytest.raises(ValueError):
+        P.hoscf_solve_batched([], [])                                   # empty batch
+    with pytest.raises(ValueError):
+        P.hoscf_solve_batched([torch.zeros(3, 4, 5)], [])               # one start per tensor
+    with pytest.raises(ValueError):
+        P.hoscf_solve_batched([torch.zeros(3, 4, 5)], [torch.zeros(12)])   # host tensor
